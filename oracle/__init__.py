@@ -1,0 +1,32 @@
+"""CPU oracle for the exact-diagonalization hot path (TEST INFRASTRUCTURE ONLY).
+
+This package is a plain, slow, FP64 restatement of what the method computes.
+Only the test-suite, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import it; the product path (the CUDA library and its Python
+binding) never does, and fails loudly when its extension is missing.
+
+Modules
+-------
+``fock``      Fock basis of a sector (Sec. 2.3, Sec. 6.3), fermionic signs
+              (Sec. 2.3), per-spin hopping matrices, the diagonal and the
+              sector Hamiltonian split of Eq. Hdecomp / Eq. Hbuild (Sec. 2.4),
+              the factorised product of Sec. 3.2 without MPI.
+``fullfock``  Independent checkers: the whole Fock space built from
+              Jordan-Wigner operator matrices (Eq. Ham1, Ns <= 6) and a
+              sector Hamiltonian built state by state with the full mode
+              ordering (no spin factorisation).
+``lanczos``   Plain Lanczos without re-orthogonalisation (Sec. 6.6), the
+              lowest eigenpair of the tridiagonal matrix by Sturm bisection and
+              inverse iteration, the second pass for the ground-state vector
+              and an FP64 Rayleigh-quotient polish.
+``gf``        Impurity Green's function from c^+|gs> and c|gs> Lanczos chains
+              and continued fractions (Sec. 6.8, Eq. KLgf), plus the exact
+              Lehmann sum from dense eigenvectors for small sectors.
+
+Every function cites the passage of the paper it follows.  Pins (tests under
+``tests/test_oracle_*.py``) tie each function to something other than itself:
+binomial dimensions, brute force, closed forms and symmetry invariants.
+Parity unpinned: the individual Lanczos coefficients after loss of
+orthogonality (rounding dependent); only E0, G(i w_n) and residuals are
+compared.
+"""

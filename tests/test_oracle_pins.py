@@ -1,0 +1,296 @@
+"""Pins of the CPU oracle against things other than itself (no GPU).
+
+Each test ties one oracle function to brute force, a closed form, a symmetry
+of the model or a library routine, so that a dropped term, a wrong sign or
+index, or a transposed operand fails at least one of them.
+"""
+import itertools
+import math
+import os
+
+import numpy as np
+import pytest
+import scipy.linalg as sla
+
+from oracle import fock, fullfock, gf, lanczos
+from workloads import (SplitMix64, make_model, splitmix64_uniform_array,
+                       workload_ns8, ImpurityModel)
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _golden_ints(name):
+    with open(os.path.join(GOLDEN, name)) as f:
+        return [line.split() for line in f if line.strip() and not line.startswith("#")]
+
+
+# ---------------------------------------------------------------- generator
+
+def test_splitmix64_published_outputs():
+    want = [int(x[0]) for x in _golden_ints("splitmix64_seed1234567.txt")]
+    r = SplitMix64(1234567)
+    assert [r.next_u64() for _ in range(5)] == want
+    u = splitmix64_uniform_array(1234567, 5)
+    assert np.array_equal(u, np.array([(w >> 11) * 2.0 ** -53 for w in want]))
+
+
+# ---------------------------------------------------------------- a1: LUTs
+
+@pytest.mark.parametrize("ns", range(1, 15))
+def test_sector_map_counts_and_order(ns):
+    for n in range(ns + 1):
+        m = fock.build_sector_map(ns, n)
+        assert len(m) == math.comb(ns, n)
+        assert np.all(np.diff(m) > 0)
+        assert all(bin(int(x)).count("1") == n for x in m)
+
+
+@pytest.mark.parametrize("ns,n", [(8, 4), (10, 3), (12, 6), (14, 7), (16, 8), (18, 9)])
+def test_rank_is_colex_combinatorial_number(ns, n):
+    """rank(I) = sum_k C(p_k, k) over the set bits p_1 < ... < p_n equals the
+    position in the ascending map (Sec. 6.3); checked for every state."""
+    m = fock.build_sector_map(ns, n)
+    for idx in range(0, len(m), max(1, len(m) // 3000)):
+        I = int(m[idx])
+        pos = [p for p in range(ns) if (I >> p) & 1]
+        r = sum(math.comb(p, k + 1) for k, p in enumerate(pos))
+        assert r == idx
+        assert fock.binary_search(m, I) == idx
+    assert fock.binary_search(m, (1 << ns) - 1 if n != ns else 0) == -1 or n in (0, ns)
+
+
+def test_rank_matches_itertools_colex_small():
+    ns, n = 9, 4
+    combos = sorted(itertools.combinations(range(ns), n), key=lambda c: sum(1 << p for p in c))
+    m = fock.build_sector_map(ns, n)
+    assert [sum(1 << p for p in c) for c in combos] == [int(x) for x in m]
+
+
+def test_workload_sector_dimensions():
+    rows = _golden_ints("sector_dimensions.txt")
+    for ns, nup, ndw, d in rows:
+        ns, nup, ndw, d = int(ns), int(nup), int(ndw), int(d)
+        assert math.comb(ns, nup) * math.comb(ns, ndw) == d
+    for ns, nup, ndw, d in rows[:2]:
+        assert len(fock.build_sector_map(int(ns), int(nup))) ** 2 == int(d)
+
+
+# ---------------------------------------------------------------- a2: H
+
+def _small_models():
+    return [
+        make_model(1, 5, U=2.7, e_d=-1.1, seed=11),
+        make_model(2, 2, U=3.1, Jh=0.6, seed=12),
+        make_model(3, 1, U=2.2, Jh=0.3, seed=13),
+    ]
+
+
+def _spin_asym(model, seed):
+    r = np.random.default_rng(seed)
+    return ImpurityModel(norb=model.norb, nbath=model.nbath, U=model.U, Ust=model.Ust,
+                         Jh=model.Jh, e_imp=model.e_imp + r.normal(0, .2, (2, model.norb)),
+                         e_bath=model.e_bath + r.normal(0, .2, model.e_bath.shape),
+                         v_bath=model.v_bath * r.uniform(.5, 1.5, model.v_bath.shape))
+
+
+@pytest.mark.parametrize("mi", range(3))
+def test_sector_blocks_equal_jordan_wigner_fock_space(mi):
+    """Every sector block of the whole-Fock-space Hamiltonian built from
+    Jordan-Wigner operators equals the spin-factorised sector matrix."""
+    m = _spin_asym(_small_models()[mi], mi)
+    H = fullfock.fock_space_hamiltonian(m)
+    ns = m.ns
+    for nup in range(ns + 1):
+        for ndw in range(ns + 1):
+            idx = fullfock.sector_indices(ns, nup, ndw)
+            B = H[idx][:, idx].toarray()
+            A = fock.Sector(m, nup, ndw).hamiltonian().toarray()
+            assert np.abs(A - B).max() < 1e-13, (nup, ndw)
+    # sectors do not couple
+    n_up = np.array([bin(I & ((1 << ns) - 1)).count("1") for I in range(1 << 2 * ns)])
+    n_dw = np.array([bin(I >> ns).count("1") for I in range(1 << 2 * ns)])
+    Hc = H.tocoo()
+    assert np.all(n_up[Hc.row] == n_up[Hc.col]) and np.all(n_dw[Hc.row] == n_dw[Hc.col])
+
+
+def test_statewise_sector_matrix_ns8():
+    wl = workload_ns8()
+    m = _spin_asym(wl.model, 5)
+    for (nu, nd) in [(4, 4), (3, 5), (5, 2)]:
+        A = fock.Sector(m, nu, nd).hamiltonian()
+        B = fullfock.sector_hamiltonian_statewise(m, nu, nd)
+        assert abs(A - B).max() < 1e-13
+        assert abs(A - A.T).max() == 0.0
+
+
+def test_factorised_matvec_equals_explicit_matrix():
+    m = _spin_asym(make_model(2, 3, U=2.0, Jh=0.3, seed=7), 1)
+    s = fock.Sector(m, 3, 5)
+    v = np.random.default_rng(0).normal(size=s.dim)
+    B = fullfock.sector_hamiltonian_statewise(m, 3, 5)
+    assert np.abs(s.matvec(v) - B @ v).max() < 1e-12
+
+
+# ---------------------------------------------------------------- E0
+
+def _lanczos_e0(m, nup, ndw, tol=1e-12):
+    s = fock.Sector(m, nup, ndw)
+    r = lanczos.lanczos_ground(s.matvec, lanczos.start_vector(0x5EED, s.dim), tol=tol)
+    return r["e0"], s
+
+
+def test_e0_equals_dense_eigh_ns8():
+    wl = workload_ns8()
+    e0, s = _lanczos_e0(wl.model, 4, 4)
+    ex = np.linalg.eigvalsh(s.hamiltonian().toarray())[0]
+    assert abs(e0 - ex) <= 1e-12 * abs(ex)
+
+
+def _one_body(m, spin):
+    ns = m.ns
+    h = np.diag(fock.level_energies(m, spin))
+    for a in range(m.norb):
+        for nu in range(m.nbath):
+            i, j = fock.level_of_impurity(m, a), fock.level_of_bath(m, a, nu)
+            h[i, j] = h[j, i] = m.v_bath[spin, a, nu]
+    return h
+
+
+@pytest.mark.parametrize("norb,nbath,nup,ndw", [(1, 7, 4, 4), (1, 7, 3, 5), (2, 3, 4, 3), (3, 2, 4, 5)])
+def test_e0_u0_closed_form(norb, nbath, nup, ndw):
+    """U = U' = J = 0: E0 is the sum of the lowest N_up (N_dw) eigenvalues of
+    the Ns x Ns one-body matrix of each spin."""
+    m = _spin_asym(make_model(norb, nbath, U=0.0, Jh=0.0, e_d=0.13, seed=21), 3)
+    e0, _ = _lanczos_e0(m, nup, ndw)
+    eu = np.linalg.eigvalsh(_one_body(m, 0))
+    ed = np.linalg.eigvalsh(_one_body(m, 1))
+    ref = eu[:nup].sum() + ed[:ndw].sum()
+    assert abs(e0 - ref) <= 1e-11 * max(1, abs(ref))
+
+
+@pytest.mark.parametrize("norb,nbath,nup,ndw", [(1, 7, 4, 4), (2, 3, 4, 3), (3, 2, 5, 4)])
+def test_e0_atomic_limit(norb, nbath, nup, ndw):
+    """V = 0: minimise over impurity occupations the impurity energy plus the
+    lowest remaining bath levels of each spin."""
+    m0 = make_model(norb, nbath, U=2.5, Jh=0.4, seed=31)
+    m = ImpurityModel(norb=norb, nbath=nbath, U=m0.U, Ust=m0.Ust, Jh=m0.Jh, e_imp=m0.e_imp,
+                      e_bath=m0.e_bath, v_bath=np.zeros_like(m0.v_bath))
+    s = fock.Sector(m, nup, ndw)
+    e_min = np.inf
+    for mu in range(1 << norb):
+        for md in range(1 << norb):
+            ku, kd = bin(mu).count("1"), bin(md).count("1")
+            if ku > nup or kd > ndw or nup - ku > norb * nbath or ndw - kd > norb * nbath:
+                continue
+            e = 0.0
+            for a in range(norb):
+                nau, nad = (mu >> a) & 1, (md >> a) & 1
+                e += m.e_imp[0, a] * nau + m.e_imp[1, a] * nad + m.U * nau * nad
+                for b in range(norb):
+                    if b != a:
+                        e += m.Ust * nau * ((md >> b) & 1)
+                for b in range(a + 1, norb):
+                    e += (m.Ust - m.Jh) * (nau * ((mu >> b) & 1) + nad * ((md >> b) & 1))
+            e += np.sort(m.e_bath[0].ravel())[:nup - ku].sum()
+            e += np.sort(m.e_bath[1].ravel())[:ndw - kd].sum()
+            e_min = min(e_min, e)
+    assert abs(s.diagonal().min() - e_min) < 1e-12
+    assert abs(s.H_up).max() == 0 and abs(s.H_dw).max() == 0
+
+
+def test_twin_and_particle_hole_symmetry():
+    """Spin-symmetric model: E(N_up,N_dw) = E(N_dw,N_up).  The Ns=8 workload
+    is particle-hole symmetric (e_d = -U/2, bath grid symmetric about 0,
+    equal V): E(N_up,N_dw) = E(Ns-N_up, Ns-N_dw)."""
+    wl = workload_ns8()
+    m = wl.model
+    e35, _ = _lanczos_e0(m, 3, 5)
+    e53, _ = _lanczos_e0(m, 5, 3)
+    e53b, _ = _lanczos_e0(m, 5, 3)
+    assert abs(e35 - e53) < 1e-11
+    e34, _ = _lanczos_e0(m, 3, 4)
+    e54, _ = _lanczos_e0(m, 5, 4)
+    assert abs(e34 - e54) < 1e-11
+    assert e53 == e53b
+
+
+# ---------------------------------------------------------------- tridiagonal
+
+@pytest.mark.parametrize("k", [1, 2, 7, 64, 300])
+def test_tridiagonal_eigenpair_against_lapack(k):
+    r = np.random.default_rng(k)
+    a = r.normal(size=k)
+    b = np.concatenate([[0.0], np.abs(r.normal(size=k - 1)) + 0.05])
+    th = lanczos.tridiag_lowest(a, b)
+    w, V = sla.eigh_tridiagonal(a, b[1:])
+    assert abs(th - w[0]) <= 1e-13 * max(1, abs(w[0]))
+    y = lanczos.tridiag_vector(a, b, th)
+    ref = V[:, 0] * np.sign(V[int(np.argmax(np.abs(V[:, 0]))), 0])
+    assert np.abs(y - ref).max() < 1e-9
+
+
+def test_ground_vector_residual_and_dense_ns8():
+    wl = workload_ns8()
+    s = fock.Sector(wl.model, 4, 4)
+    r = lanczos.ground_state(s.matvec, s.dim)
+    e, res = lanczos.rayleigh_residual(s.matvec, r["psi"])
+    assert res < 1e-10
+    E, U = np.linalg.eigh(s.hamiltonian().toarray())
+    assert abs(abs(U[:, 0] @ r["psi"]) - 1.0) < 1e-12
+
+
+# ---------------------------------------------------------------- a7: c, c^+
+
+@pytest.mark.parametrize("spin", [0, 1])
+@pytest.mark.parametrize("create", [+1, -1])
+def test_creation_annihilation_against_jordan_wigner(spin, create):
+    m = _spin_asym(make_model(2, 2, U=1.0, Jh=0.2, seed=41), 9)
+    ns = m.ns
+    nup, ndw = 3, 2
+    src = fullfock.sector_indices(ns, nup, ndw)
+    psi = np.random.default_rng(1).normal(size=len(src))
+    c = fullfock.jordan_wigner_annihilators(2 * ns)
+    full = np.zeros(1 << 2 * ns)
+    full[src] = psi
+    for orb in range(m.norb):
+        mode = fock.level_of_impurity(m, orb) + spin * ns
+        op = c[mode].T if create > 0 else c[mode]
+        out_full = op @ full
+        phi, (nu2, nd2) = gf._apply(m, psi, nup, ndw, orb, spin, create)
+        dst = fullfock.sector_indices(ns, nu2, nd2)
+        assert np.abs(out_full[dst] - phi).max() == 0.0
+        assert np.abs(np.delete(out_full, dst)).max() == 0.0
+
+
+# ---------------------------------------------------------------- a8: G(iw)
+
+def test_gf_u0_closed_form():
+    """U = 0: G_{dd}(i w) = [(i w - h)^-1]_{dd} with h the one-body matrix;
+    the chain breaks down within Ns steps so the continued fraction is exact."""
+    m = _spin_asym(make_model(1, 7, U=0.0, e_d=0.05, seed=51), 4)
+    s = fock.Sector(m, 4, 4)
+    r = lanczos.ground_state(s.matvec, s.dim)
+    wn = gf.matsubara(100.0, 64)
+    for spin in (0, 1):
+        G = gf.impurity_gf(m, 4, 4, r["psi"], r["e0"], 0, spin, nmats=64)
+        h = _one_body(m, spin)
+        ref = np.array([np.linalg.inv(1j * w * np.eye(m.ns) - h)[0, 0] for w in wn])
+        assert np.abs(G - ref).max() < 1e-9
+
+
+def test_gf_lehmann_symmetry_and_sum_rule_ns8():
+    wl = workload_ns8()
+    m = wl.model
+    s = fock.Sector(m, 4, 4)
+    r = lanczos.ground_state(s.matvec, s.dim)
+    G, parts = gf.impurity_gf(m, 4, 4, r["psi"], r["e0"], 0, 0, return_parts=True)
+    Gx, e0x = gf.lehmann_gf_dense(m, 4, 4, 0, 0)
+    assert abs(r["e0"] - e0x) < 1e-12 * abs(e0x)
+    assert np.abs(G - Gx).max() < 1e-10
+    assert np.abs(G.real).max() < 1e-10          # particle-hole symmetry
+    assert abs(parts[1][0] + parts[-1][0] - 1.0) < 1e-12   # <c c^+ + c^+ c> = 1
+    wn = gf.matsubara(0.01, 4)                   # far tail: i w G -> 1
+    Gt = gf.impurity_gf(m, 4, 4, r["psi"], r["e0"], 0, 0, beta=0.01, nmats=4)
+    assert np.abs(1j * wn * Gt - 1.0).max() < 1e-3
+    Gd = gf.impurity_gf(m, 4, 4, r["psi"], r["e0"], 0, 1)
+    assert np.abs(G - Gd).max() < 1e-10          # spin symmetry at N_up = N_dw
