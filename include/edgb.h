@@ -1,0 +1,264 @@
+/*
+ * edgb.h — C ABI of the GB300 exact-diagonalisation hot path.
+ *
+ * The library computes, on one GPU, the Lanczos ground state and the impurity
+ * Green's function of a density-density Anderson impurity model in one
+ * (N_up, N_dw) Fock sector, following A. Amaricci et al., "EDIpack: a parallel
+ * exact diagonalization package for quantum impurity problems":
+ *
+ *   - the model is Eq. Ham1 with J_X = J_P = 0, diagonal H^loc and bath h, and
+ *     a "normal" bath (each impurity orbital has its own Nbath levels,
+ *     Ns = Norb (Nbath + 1), Sec. 2.1 and Sec. 6.4);
+ *   - the sector basis is the product of two ascending lists of Ns-bit strings
+ *     with N_up and N_dw set bits (Sec. 2.3, Sec. 6.3);
+ *   - the sector Hamiltonian has the split H = H_d + H_up x 1 + 1 x H_dw of
+ *     Eq. Hdecomp with the matrix elements of Eq. Hbuild (Sec. 2.4);
+ *   - the product w = H v is the serial form of Sec. 6.7 (diagonal, up part
+ *     along contiguous rows, down part along the strided axis, Sec. 3.2);
+ *   - the ground state comes from plain Lanczos without re-orthogonalisation
+ *     (Sec. 6.6); G(i w_n) from Lanczos chains and continued fractions
+ *     (Sec. 6.8, Eq. KLgf).
+ *
+ * Conventions (fixed by this header; the paper is 1-based):
+ *   - level a of a spin string is bit a.  Impurity orbital alpha is level
+ *     alpha (alpha < Norb); bath level nu of orbital alpha is level
+ *     Norb + alpha*Nbath + nu.
+ *   - sector index i = i_up + i_dw * D_up (0-based Eq. SectorIndxDecomp): a
+ *     sector vector is a row-major [D_dw][D_up] array (Eq. Vmatrix).
+ *   - fermionic signs use the mode order 1up..Ns up, 1dw..Ns dw (Sec. 2.3).
+ *   - spin index 0 = up, 1 = down.
+ *
+ * Memory and errors:
+ *   - every call returns an ed_status; nothing aborts or throws across the ABI.
+ *   - pointers named d_* are DEVICE pointers owned by the caller; host_* are
+ *     host pointers owned by the caller.  Model arrays are copied at the call.
+ *   - handles (ed_sector, ed_server) are owned by the library and released by
+ *     the matching *_free / *_destroy call.
+ *   - stream arguments are cudaStream_t values passed as void* (NULL = the
+ *     legacy default stream).  Calls that return host results synchronise the
+ *     stream before returning; ed_matvec is asynchronous.
+ *   - a CUDA error is reported as ED_ERR_CUDA and its text is available from
+ *     ed_last_error(); the device context stays usable unless the CUDA error
+ *     itself is sticky.
+ */
+#ifndef EDGB_H
+#define EDGB_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define EDGB_VERSION_MAJOR 1
+#define EDGB_VERSION_MINOR 0
+
+/* Largest supported values (strings are 32-bit; tables sized statically). */
+#define ED_MAX_NS 24
+#define ED_MAX_NORB 5
+#define ED_MAX_LANCZOS 1024
+
+typedef enum {
+  ED_OK = 0,
+  ED_PENDING = 1,            /* ed_poll: request not finished yet            */
+  ED_ERR_ARG = -1,           /* invalid argument (NULL, out of range, size)  */
+  ED_ERR_UNSUPPORTED = -2,   /* J_X or J_P != 0, Ns or Norb above the limits */
+  ED_ERR_OOM = -3,           /* device allocation failed                     */
+  ED_ERR_CUDA = -4,          /* a CUDA runtime call failed                   */
+  ED_ERR_TIMEOUT = -5,       /* a bounded wait ran out                       */
+  ED_ERR_NOT_CONVERGED = -6, /* Lanczos reached max_iter before tolerance    */
+  ED_ERR_BUSY = -7,          /* server queue full                            */
+  ED_ERR_NOT_FOUND = -8      /* unknown ticket                               */
+} ed_status;
+
+typedef enum {
+  ED_FP64 = 0,        /* FP64 vectors, matrix elements and accumulation          */
+  ED_FP32 = 1,        /* FP32 vectors and elements, FP32 row sums, FP64 scalars  */
+  ED_FP32_POLISH = 2  /* ED_FP32 Lanczos, then FP64 Lanczos steps from the FP32
+                         ground state (energy and vector reported in FP64)       */
+} ed_precision;
+
+/* Model parameters, Eq. Ham1 with J_X = J_P = 0 (host arrays, copied). */
+typedef struct {
+  int32_t norb;            /* impurity orbitals, 1..ED_MAX_NORB              */
+  int32_t nbath;           /* bath levels per orbital, >= 0                  */
+  double U;                /* intra-orbital U                                */
+  double Ust;              /* inter-orbital opposite-spin U'                 */
+  double Jh;               /* Hund J: same-spin inter-orbital term is U'-J   */
+  double Jx, Jp;           /* spin exchange / pair hopping: must be 0        */
+  const double *e_imp;     /* [2][norb]        impurity levels (H^loc diag)  */
+  const double *e_bath;    /* [2][norb][nbath] bath energies                 */
+  const double *v_bath;    /* [2][norb][nbath] hybridisations V^nu_{alpha s} */
+} ed_model;
+
+typedef struct ed_sector_s *ed_sector;
+
+typedef struct {
+  int32_t ns, norb, nbath, nup, ndw;
+  int64_t dim_up, dim_dw, dim;     /* D_up, D_dw, D = D_up * D_dw           */
+  int64_t nnz_up, nnz_dw;          /* stored entries of H_up and H_dw        */
+  int64_t device_bytes;            /* device memory held by the handle       */
+} ed_sector_info;
+
+/* Sector set-up (Sec. 6.3 build_sector, Sec. 2.4 / Eq. Hbuild): enumerates
+ * both spin bases on the device (ascending Ns-bit strings with N_sigma set
+ * bits, ranked by the combinatorial number system, which gives the same
+ * order as the paper's scan + binary search), and builds the per-spin CSR
+ * hopping matrices (columns sorted, FP64 and FP32 values) and the diagonal
+ * tables: E_sigma[i] (one-body energies + (U'-J) same-spin pairs) and
+ * W[m_up][m_dw] (U and U' terms over impurity occupation masks).
+ * Returns ED_ERR_ARG for nup/ndw outside 0..Ns, ED_ERR_UNSUPPORTED for
+ * Jx/Jp != 0 or Ns > ED_MAX_NS.  Synchronises `stream`. */
+ed_status ed_sector_build(const ed_model *model, int32_t nup, int32_t ndw,
+                          void *stream, ed_sector *out);
+ed_status ed_sector_get_info(ed_sector s, ed_sector_info *out);
+/* Test hook: copies spin `spin`'s tables to host arrays (each may be NULL):
+ * map[D_s] (uint32 strings, sector order), rowptr[D_s+1], col[nnz], val[nnz]
+ * (FP64), ediag[D_s] (FP64 E_sigma), imask[D_s] (impurity bits).  The W table
+ * ([2^norb][2^norb] FP64) is copied by ed_sector_copy_w. */
+ed_status ed_sector_copy_tables(ed_sector s, int32_t spin, uint32_t *host_map,
+                                int32_t *host_rowptr, int32_t *host_col,
+                                double *host_val, double *host_ediag,
+                                uint8_t *host_imask);
+ed_status ed_sector_copy_w(ed_sector s, double *host_w);
+ed_status ed_sector_free(ed_sector s);
+
+/* w = H v on the sector (Sec. 6.7 without MPI; Eq. Hbuild):
+ *   w[r,c] = (E_up[c] + E_dw[r] + W[m_up[c]][m_dw[r]]) v[r,c]
+ *          + sum_k H_up[c,k] v[r,k] + sum_k H_dw[r,k] v[k,c].
+ * d_v, d_w: device arrays of D elements, double for ED_FP64, float for
+ * ED_FP32 / ED_FP32_POLISH; must not overlap.  Asynchronous on `stream`. */
+ed_status ed_matvec(ed_sector s, ed_precision prec, const void *d_v, void *d_w,
+                    void *stream);
+
+typedef struct {
+  ed_precision precision;
+  int32_t max_iter;      /* first-pass Lanczos steps, <= ED_MAX_LANCZOS (0: 512) */
+  double tol;            /* stop when beta_{k+1}|y_k| <= tol*max(1,|theta|)      */
+                         /* (0: 1e-12 for FP64, 1e-6 for the FP32 modes)         */
+  uint64_t seed;         /* start vector: v0_i = u_i - 1/2, u_i = SplitMix64(seed)
+                            output i, sector order, then normalised               */
+  int32_t polish_steps;  /* FP64 Lanczos steps of ED_FP32_POLISH (0: 4)          */
+  int32_t want_vector;   /* 1: second pass, psi and its FP64 residual            */
+} ed_lanczos_opts;
+
+typedef struct {
+  double e0;                /* reported ground energy                          */
+  double e0_raw;            /* lowest Ritz value of the first (FP32/FP64) pass */
+  double residual;          /* ||H psi - e0 psi|| / ||psi|| in FP64 (vector)   */
+  double residual_estimate; /* beta_{k+1}|y_k| of the first pass               */
+  int32_t iterations;       /* first-pass steps k                              */
+  int32_t polish_iterations;
+  int32_t stop_reason;      /* 0 converged, 1 breakdown, 2 max_iter            */
+  int32_t matvecs;          /* total products performed                        */
+} ed_lanczos_result;
+
+/* Lanczos ground state of the sector (Sec. 6.6): plain Lanczos, Paige form,
+ * no re-orthogonalisation; lowest eigenpair of the tridiagonal matrix by
+ * Sturm multisection (FP64); second pass to form psi = sum_j y_j v_j.
+ * d_psi (nullable, requires want_vector) receives psi, normalised, in
+ * sector order: double for ED_FP64 / ED_FP32_POLISH, float for ED_FP32.
+ * Work vectors are allocated stream-ordered on the device and released
+ * before return.  Synchronises `stream`.  Returns ED_ERR_NOT_CONVERGED (with
+ * `res` filled) when max_iter is reached before the tolerance. */
+ed_status ed_lanczos_ground(ed_sector s, const ed_lanczos_opts *opts,
+                            ed_lanczos_result *res, void *d_psi, void *stream);
+
+typedef struct {
+  double weight_particle;  /* ||c^+ psi||^2                                    */
+  double weight_hole;      /* ||c psi||^2                                      */
+  int32_t steps_particle;  /* chain lengths actually used (breakdown stops)    */
+  int32_t steps_hole;
+} ed_gf_info;
+
+/* Impurity Green's function G_{orb,spin}(i w_n), w_n = (2n+1) pi / beta,
+ * n = 0..nmats-1, at T = 0 (Sec. 6.8, Eq. KLgf with "+" for fermions):
+ *   G = n+ [(z - T+)^-1]_00 at z = e0 + i w_n  -  n- [(z - T-)^-1]_00 at
+ *   z = e0 - i w_n,
+ * where T+- are the tridiagonal matrices of `nsteps`-step Lanczos chains
+ * started from c^+_{orb,spin} psi and c_{orb,spin} psi and n+- their squared
+ * norms.  d_psi is the normalised ground state of `s` in sector order
+ * (double for ED_FP64 / ED_FP32_POLISH, float for ED_FP32); chains run in
+ * the precision `prec` (ED_FP32_POLISH runs them in FP32).  The N+-1 sectors
+ * are built on first use and cached in `s`.  host_G receives 2*nmats doubles
+ * (re, im interleaved).  Synchronises `stream`. */
+ed_status ed_gf_lanczos(ed_sector s, ed_precision prec, const void *d_psi, double e0,
+                        int32_t orb, int32_t spin, int32_t nsteps, double beta,
+                        int32_t nmats, double *host_G, ed_gf_info *info,
+                        void *stream);
+
+/* One impurity solve: sector build, ground state, and G for every orbital and
+ * both spins (the down spin is copied from the up spin when N_up = N_dw and
+ * the model is spin symmetric, Sec. 6.6 twin symmetry).  host_G receives
+ * [2][norb][nmats] complex values as 2*2*norb*nmats doubles (may be NULL when
+ * nmats == 0). */
+typedef struct {
+  ed_lanczos_opts lanczos;
+  int32_t gf_steps;      /* lanc_ngfiter (0: 200)  */
+  int32_t nmats;         /* Matsubara points (>= 0) */
+  double beta;           /* inverse temperature setting the grid */
+  ed_precision gf_precision;
+} ed_solve_opts;
+
+typedef struct {
+  ed_lanczos_result ground;
+  double t_build_s, t_ground_s, t_gf_s;  /* wall time of each phase */
+} ed_solve_result;
+
+ed_status ed_solve(const ed_model *model, int32_t nup, int32_t ndw,
+                   const ed_solve_opts *opts, ed_solve_result *res,
+                   double *host_G, void *stream);
+
+/* ---------------------------------------------------------------- serving
+ * A request loop on a host thread: requests are admitted while their
+ * estimated device memory fits the budget and a slot is free, run
+ * concurrently on a pool of CUDA streams (continuous batching: a request
+ * that arrives while others run starts as soon as a slot and memory free
+ * up), and their results are kept until polled.  Results are bit-identical
+ * to ed_solve with the same request (deterministic reductions). */
+typedef struct ed_server_s *ed_server;
+
+typedef struct {
+  int32_t slots;               /* concurrent solves (streams), 0: 8           */
+  int64_t device_mem_budget;   /* bytes for admitted solves, 0: 50% of free   */
+  int32_t queue_capacity;      /* pending requests, 0: 65536                  */
+} ed_server_opts;
+
+typedef struct {
+  ed_model model;              /* arrays copied at submit                    */
+  int32_t nup, ndw;
+  ed_solve_opts opts;
+} ed_request;
+
+typedef struct {
+  ed_status status;            /* status of the solve                        */
+  double e0;
+  ed_lanczos_result ground;
+  int32_t norb, nmats;
+  double t_submit_s, t_start_s, t_done_s;  /* server clock (seconds)         */
+} ed_result;
+
+ed_status ed_server_create(const ed_server_opts *opts, ed_server *out);
+/* Copies the request; returns ED_ERR_BUSY when the queue is full and
+ * ED_ERR_OOM when the request alone exceeds the memory budget. */
+ed_status ed_submit(ed_server srv, const ed_request *req, uint64_t *ticket);
+/* Never blocks.  ED_PENDING while the request runs; otherwise fills `out`
+ * and, when host_G is not NULL, copies G ([2][norb][nmats] complex) and
+ * forgets the ticket. */
+ed_status ed_poll(ed_server srv, uint64_t ticket, ed_result *out, double *host_G);
+/* Blocks up to timeout_s seconds for the request; ED_ERR_TIMEOUT otherwise. */
+ed_status ed_wait(ed_server srv, uint64_t ticket, double timeout_s);
+ed_status ed_server_destroy(ed_server srv);
+/* Test hook: the next `count` admissions fail as if the device allocation
+ * had failed (the request completes with ED_ERR_OOM). */
+ed_status ed_server_inject_alloc_failure(ed_server srv, int32_t count);
+
+const char *ed_status_string(ed_status st);
+const char *ed_last_error(void);
+/* Number of kernels this library has launched in the calling process. */
+int64_t ed_kernel_launches(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* EDGB_H */

@@ -1,0 +1,384 @@
+"""Python binding of libedgb.so (include/edgb.h): argument marshalling only.
+
+Every step of the exact-diagonalisation path runs in the CUDA library; this
+module converts Python/NumPy/PyTorch arguments to the C structures, passes
+device pointers (``tensor.data_ptr()``) and CUDA streams
+(``torch.cuda.current_stream().cuda_stream``) through, and raises
+``EDError`` on a non-OK status.  There is no CPU fallback: when the library
+is missing, ``lib()`` raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libedgb.so")
+
+ED_OK, ED_PENDING = 0, 1
+ED_ERR_ARG, ED_ERR_UNSUPPORTED, ED_ERR_OOM, ED_ERR_CUDA = -1, -2, -3, -4
+ED_ERR_TIMEOUT, ED_ERR_NOT_CONVERGED, ED_ERR_BUSY, ED_ERR_NOT_FOUND = -5, -6, -7, -8
+FP64, FP32, FP32_POLISH = 0, 1, 2
+PRECISIONS = {"fp64": FP64, "fp32": FP32, "fp32_polish": FP32_POLISH}
+
+EXPORTED = [
+    "ed_sector_build", "ed_sector_get_info", "ed_sector_copy_tables", "ed_sector_copy_w",
+    "ed_sector_free", "ed_matvec", "ed_lanczos_ground", "ed_gf_lanczos", "ed_solve",
+    "ed_server_create", "ed_submit", "ed_poll", "ed_wait", "ed_server_destroy",
+    "ed_server_inject_alloc_failure", "ed_status_string", "ed_last_error", "ed_kernel_launches",
+]
+
+
+class EDError(RuntimeError):
+    def __init__(self, status, what=""):
+        self.status = status
+        msg = f"{what}: status {status}"
+        try:
+            L = lib()
+            msg += f" ({L.ed_status_string(status).decode()})"
+            last = L.ed_last_error().decode()
+            if last:
+                msg += f" — {last}"
+        except Exception:
+            pass
+        super().__init__(msg)
+
+
+# ----------------------------------------------------------------- structs
+
+DP = C.POINTER(C.c_double)
+
+
+class ed_model(C.Structure):
+    _fields_ = [("norb", C.c_int32), ("nbath", C.c_int32), ("U", C.c_double),
+                ("Ust", C.c_double), ("Jh", C.c_double), ("Jx", C.c_double),
+                ("Jp", C.c_double), ("e_imp", DP), ("e_bath", DP), ("v_bath", DP)]
+
+
+class ed_sector_info(C.Structure):
+    _fields_ = [("ns", C.c_int32), ("norb", C.c_int32), ("nbath", C.c_int32),
+                ("nup", C.c_int32), ("ndw", C.c_int32), ("dim_up", C.c_int64),
+                ("dim_dw", C.c_int64), ("dim", C.c_int64), ("nnz_up", C.c_int64),
+                ("nnz_dw", C.c_int64), ("device_bytes", C.c_int64)]
+
+
+class ed_lanczos_opts(C.Structure):
+    _fields_ = [("precision", C.c_int), ("max_iter", C.c_int32), ("tol", C.c_double),
+                ("seed", C.c_uint64), ("polish_steps", C.c_int32), ("want_vector", C.c_int32)]
+
+
+class ed_lanczos_result(C.Structure):
+    _fields_ = [("e0", C.c_double), ("e0_raw", C.c_double), ("residual", C.c_double),
+                ("residual_estimate", C.c_double), ("iterations", C.c_int32),
+                ("polish_iterations", C.c_int32), ("stop_reason", C.c_int32),
+                ("matvecs", C.c_int32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class ed_gf_info(C.Structure):
+    _fields_ = [("weight_particle", C.c_double), ("weight_hole", C.c_double),
+                ("steps_particle", C.c_int32), ("steps_hole", C.c_int32)]
+
+
+class ed_solve_opts(C.Structure):
+    _fields_ = [("lanczos", ed_lanczos_opts), ("gf_steps", C.c_int32), ("nmats", C.c_int32),
+                ("beta", C.c_double), ("gf_precision", C.c_int)]
+
+
+class ed_solve_result(C.Structure):
+    _fields_ = [("ground", ed_lanczos_result), ("t_build_s", C.c_double),
+                ("t_ground_s", C.c_double), ("t_gf_s", C.c_double)]
+
+
+class ed_server_opts(C.Structure):
+    _fields_ = [("slots", C.c_int32), ("device_mem_budget", C.c_int64),
+                ("queue_capacity", C.c_int32)]
+
+
+class ed_request(C.Structure):
+    _fields_ = [("model", ed_model), ("nup", C.c_int32), ("ndw", C.c_int32),
+                ("opts", ed_solve_opts)]
+
+
+class ed_result(C.Structure):
+    _fields_ = [("status", C.c_int), ("e0", C.c_double), ("ground", ed_lanczos_result),
+                ("norb", C.c_int32), ("nmats", C.c_int32), ("t_submit_s", C.c_double),
+                ("t_start_s", C.c_double), ("t_done_s", C.c_double)]
+
+
+# ----------------------------------------------------------------- loading
+
+_lib = None
+_lock = threading.Lock()
+
+
+def lib():
+    """The loaded CUDA library; raises when it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(
+                f"{LIB_PATH} is missing: build it with __graft_entry__.build() "
+                "(the exact-diagonalisation path has no CPU fallback)")
+        L = C.CDLL(LIB_PATH)
+        vp, i32, i64, u64 = C.c_void_p, C.c_int32, C.c_int64, C.c_uint64
+        sig = {
+            "ed_sector_build": [C.POINTER(ed_model), i32, i32, vp, C.POINTER(vp)],
+            "ed_sector_get_info": [vp, C.POINTER(ed_sector_info)],
+            "ed_sector_copy_tables": [vp, i32, vp, vp, vp, vp, vp, vp],
+            "ed_sector_copy_w": [vp, vp],
+            "ed_sector_free": [vp],
+            "ed_matvec": [vp, C.c_int, vp, vp, vp],
+            "ed_lanczos_ground": [vp, C.POINTER(ed_lanczos_opts), C.POINTER(ed_lanczos_result),
+                                  vp, vp],
+            "ed_gf_lanczos": [vp, C.c_int, vp, C.c_double, i32, i32, i32, C.c_double, i32, vp,
+                              C.POINTER(ed_gf_info), vp],
+            "ed_solve": [C.POINTER(ed_model), i32, i32, C.POINTER(ed_solve_opts),
+                         C.POINTER(ed_solve_result), vp, vp],
+            "ed_server_create": [C.POINTER(ed_server_opts), C.POINTER(vp)],
+            "ed_submit": [vp, C.POINTER(ed_request), C.POINTER(u64)],
+            "ed_poll": [vp, u64, C.POINTER(ed_result), vp],
+            "ed_wait": [vp, u64, C.c_double],
+            "ed_server_destroy": [vp],
+            "ed_server_inject_alloc_failure": [vp, i32],
+        }
+        for name, args in sig.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = C.c_int
+        L.ed_status_string.argtypes = [C.c_int]
+        L.ed_status_string.restype = C.c_char_p
+        L.ed_last_error.argtypes = []
+        L.ed_last_error.restype = C.c_char_p
+        L.ed_kernel_launches.argtypes = []
+        L.ed_kernel_launches.restype = i64
+        _lib = L
+        return L
+
+
+def _check(st, what):
+    if st != ED_OK:
+        raise EDError(st, what)
+
+
+def kernel_launches() -> int:
+    return int(lib().ed_kernel_launches())
+
+
+def _stream_ptr(stream=None):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+# ----------------------------------------------------------------- model
+
+class Model:
+    """ed_model with owned contiguous arrays (any object with the fields of
+    workloads.ImpurityModel)."""
+
+    def __init__(self, m):
+        self.norb, self.nbath = int(m.norb), int(m.nbath)
+        self.e_imp = np.ascontiguousarray(np.broadcast_to(m.e_imp, (2, self.norb)), dtype=np.float64)
+        self.e_bath = np.ascontiguousarray(
+            np.broadcast_to(m.e_bath, (2, self.norb, self.nbath)), dtype=np.float64)
+        self.v_bath = np.ascontiguousarray(
+            np.broadcast_to(m.v_bath, (2, self.norb, self.nbath)), dtype=np.float64)
+        self.c = ed_model(self.norb, self.nbath, float(m.U), float(m.Ust), float(m.Jh),
+                          float(getattr(m, "Jx", 0.0)), float(getattr(m, "Jp", 0.0)),
+                          self.e_imp.ctypes.data_as(DP), self.e_bath.ctypes.data_as(DP),
+                          self.v_bath.ctypes.data_as(DP))
+
+    @property
+    def ns(self):
+        return self.norb * (self.nbath + 1)
+
+
+def as_model(m) -> Model:
+    return m if isinstance(m, Model) else Model(m)
+
+
+# ----------------------------------------------------------------- sector
+
+class Sector:
+    """Owns an ed_sector handle (device LUTs, CSR and diagonal tables)."""
+
+    def __init__(self, model, nup, ndw, stream=None):
+        self.model = as_model(model)
+        h = C.c_void_p()
+        _check(lib().ed_sector_build(C.byref(self.model.c), int(nup), int(ndw),
+                                     C.c_void_p(_stream_ptr(stream)), C.byref(h)),
+               "ed_sector_build")
+        self.h = h
+        inf = ed_sector_info()
+        _check(lib().ed_sector_get_info(self.h, C.byref(inf)), "ed_sector_get_info")
+        self.info = {k: getattr(inf, k) for k, _ in inf._fields_}
+        self.nup, self.ndw = int(nup), int(ndw)
+        self.dim = self.info["dim"]
+        self.dim_up, self.dim_dw = self.info["dim_up"], self.info["dim_dw"]
+
+    def free(self):
+        if self.h:
+            _check(lib().ed_sector_free(self.h), "ed_sector_free")
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.free()
+
+    def tables(self, spin):
+        d = self.dim_up if spin == 0 else self.dim_dw
+        nnz = self.info["nnz_up"] if spin == 0 else self.info["nnz_dw"]
+        out = dict(map=np.zeros(d, np.uint32), rowptr=np.zeros(d + 1, np.int32),
+                   col=np.zeros(max(nnz, 1), np.int32), val=np.zeros(max(nnz, 1), np.float64),
+                   ediag=np.zeros(d, np.float64), imask=np.zeros(d, np.uint8))
+        _check(lib().ed_sector_copy_tables(
+            self.h, int(spin), out["map"].ctypes.data, out["rowptr"].ctypes.data,
+            out["col"].ctypes.data, out["val"].ctypes.data, out["ediag"].ctypes.data,
+            out["imask"].ctypes.data), "ed_sector_copy_tables")
+        out["col"], out["val"] = out["col"][:nnz], out["val"][:nnz]
+        return out
+
+    def wtable(self):
+        nm = 1 << self.model.norb
+        w = np.zeros((nm, nm))
+        _check(lib().ed_sector_copy_w(self.h, w.ctypes.data), "ed_sector_copy_w")
+        return w
+
+
+def _prec(p):
+    return PRECISIONS[p] if isinstance(p, str) else int(p)
+
+
+def matvec(sector: Sector, v, w, precision="fp64", stream=None):
+    """w = H v for device tensors (float64 for fp64, float32 otherwise)."""
+    _check(lib().ed_matvec(sector.h, _prec(precision), C.c_void_p(v.data_ptr()),
+                           C.c_void_p(w.data_ptr()), C.c_void_p(_stream_ptr(stream))),
+           "ed_matvec")
+
+
+def lanczos_ground(sector: Sector, precision="fp64", max_iter=0, tol=0.0, seed=0x5EED,
+                   polish_steps=0, psi=None, want_vector=None, stream=None, allow_maxit=False):
+    o = ed_lanczos_opts(_prec(precision), int(max_iter), float(tol), int(seed),
+                        int(polish_steps), int(bool(psi is not None) if want_vector is None
+                                               else bool(want_vector)))
+    r = ed_lanczos_result()
+    st = lib().ed_lanczos_ground(sector.h, C.byref(o), C.byref(r),
+                                 C.c_void_p(psi.data_ptr() if psi is not None else 0),
+                                 C.c_void_p(_stream_ptr(stream)))
+    if st == ED_ERR_NOT_CONVERGED and allow_maxit:
+        st = ED_OK
+    _check(st, "ed_lanczos_ground")
+    return r.as_dict()
+
+
+def gf_lanczos(sector: Sector, psi, e0, orb, spin, precision="fp64", nsteps=200, beta=100.0,
+               nmats=512, stream=None):
+    G = np.zeros(2 * nmats, dtype=np.float64)
+    info = ed_gf_info()
+    _check(lib().ed_gf_lanczos(sector.h, _prec(precision), C.c_void_p(psi.data_ptr()),
+                               float(e0), int(orb), int(spin), int(nsteps), float(beta),
+                               int(nmats), G.ctypes.data, C.byref(info),
+                               C.c_void_p(_stream_ptr(stream))), "ed_gf_lanczos")
+    return G.view(np.complex128), {k: getattr(info, k) for k, _ in info._fields_}
+
+
+def solve_opts(precision="fp32_polish", gf_precision=None, nmats=512, beta=100.0,
+               gf_steps=200, max_iter=0, tol=0.0, seed=0x5EED, polish_steps=0):
+    p = _prec(precision)
+    gp = _prec(gf_precision) if gf_precision is not None else (FP64 if p == FP64 else FP32)
+    return ed_solve_opts(ed_lanczos_opts(p, int(max_iter), float(tol), int(seed),
+                                         int(polish_steps), 0),
+                         int(gf_steps), int(nmats), float(beta), gp)
+
+
+def solve(model, nup, ndw, stream=None, **kw):
+    m = as_model(model)
+    o = solve_opts(**kw)
+    r = ed_solve_result()
+    G = np.zeros(2 * 2 * m.norb * max(o.nmats, 0), dtype=np.float64)
+    _check(lib().ed_solve(C.byref(m.c), int(nup), int(ndw), C.byref(o), C.byref(r),
+                          C.c_void_p(G.ctypes.data if o.nmats > 0 else 0),
+                          C.c_void_p(_stream_ptr(stream))), "ed_solve")
+    out = r.ground.as_dict()
+    out.update(t_build_s=r.t_build_s, t_ground_s=r.t_ground_s, t_gf_s=r.t_gf_s)
+    return out, G.view(np.complex128).reshape(2, m.norb, max(o.nmats, 0))
+
+
+class Server:
+    """Continuous-batching request loop (ed_server_*)."""
+
+    def __init__(self, slots=8, device_mem_budget=0, queue_capacity=0):
+        o = ed_server_opts(int(slots), int(device_mem_budget), int(queue_capacity))
+        h = C.c_void_p()
+        _check(lib().ed_server_create(C.byref(o), C.byref(h)), "ed_server_create")
+        self.h = h
+        self._keep = {}
+
+    def submit(self, model, nup, ndw, **kw):
+        m = as_model(model)
+        req = ed_request(m.c, int(nup), int(ndw), solve_opts(**kw))
+        t = C.c_uint64()
+        st = lib().ed_submit(self.h, C.byref(req), C.byref(t))
+        if st != ED_OK:
+            raise EDError(st, "ed_submit")
+        self._keep[t.value] = (m.norb, req.opts.nmats)
+        return t.value
+
+    def poll(self, ticket):
+        """None while pending; else (result dict, G[2][norb][nmats])."""
+        norb, nmats = self._keep.get(ticket, (1, 0))
+        r = ed_result()
+        G = np.zeros(2 * 2 * norb * max(nmats, 0) + 2, dtype=np.float64)
+        st = lib().ed_poll(self.h, C.c_uint64(ticket), C.byref(r), C.c_void_p(G.ctypes.data))
+        if st == ED_PENDING:
+            return None
+        _check(st, "ed_poll")
+        self._keep.pop(ticket, None)
+        out = r.ground.as_dict()
+        out.update(status=r.status, e0=r.e0, t_submit_s=r.t_submit_s, t_start_s=r.t_start_s,
+                   t_done_s=r.t_done_s)
+        return out, G[:-2].view(np.complex128).reshape(2, norb, max(nmats, 0))
+
+    def wait(self, ticket, timeout_s=60.0):
+        return lib().ed_wait(self.h, C.c_uint64(ticket), float(timeout_s))
+
+    def inject_alloc_failure(self, count):
+        _check(lib().ed_server_inject_alloc_failure(self.h, int(count)), "inject")
+
+    def close(self):
+        if self.h:
+            _check(lib().ed_server_destroy(self.h), "ed_server_destroy")
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,184 @@
+// Internal declarations of the GB300 exact-diagonalisation library.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "edgb.h"
+
+// ----------------------------------------------------------------- errors
+
+void ed_set_cuda_error(cudaError_t e, const char *what, const char *file, int line);
+void ed_set_error_msg(const char *msg);
+void ed_count_launches(int64_t n);
+
+#define ED_TRY_CUDA(call)                                                   \
+  do {                                                                      \
+    cudaError_t e__ = (call);                                               \
+    if (e__ != cudaSuccess) {                                               \
+      ed_set_cuda_error(e__, #call, __FILE__, __LINE__);                    \
+      return e__ == cudaErrorMemoryAllocation ? ED_ERR_OOM : ED_ERR_CUDA;   \
+    }                                                                       \
+  } while (0)
+
+#define ED_TRY(call)                          \
+  do {                                        \
+    ed_status st__ = (call);                  \
+    if (st__ != ED_OK) return st__;           \
+  } while (0)
+
+#define ED_LAUNCHED(n)                                                      \
+  do {                                                                      \
+    ed_count_launches(n);                                                   \
+    cudaError_t e__ = cudaGetLastError();                                   \
+    if (e__ != cudaSuccess) {                                               \
+      ed_set_cuda_error(e__, "kernel launch", __FILE__, __LINE__);          \
+      return ED_ERR_CUDA;                                                   \
+    }                                                                       \
+  } while (0)
+
+// ----------------------------------------------------------------- model
+
+// Level energies and hybridisations indexed by level (Sec. 2.1): level a < Norb
+// is impurity orbital a; level Norb + alpha*Nbath + nu is bath level nu of
+// orbital alpha.  Passed by value to the table-building kernels.
+struct ModelParams {
+  int norb, nbath, ns;
+  double eps[2][ED_MAX_NS];   // one-body level energies per spin
+  double V[2][ED_MAX_NS];     // V of the bath level (0 for impurity levels)
+  int orb_of_level[ED_MAX_NS];  // orbital alpha owning the level
+  double U, Ust, Jh;
+};
+
+// Per-spin basis and hopping tables of a sector (device pointers).
+struct SpinTables {
+  int n = 0;               // electrons of this spin
+  int64_t dim = 0;         // D_sigma
+  int64_t nnz = 0;
+  uint32_t *map = nullptr;     // [dim] Ns-bit strings, ascending
+  uint8_t *imask = nullptr;    // [dim] impurity occupation bits
+  double *ediag = nullptr;     // [dim] E_sigma (FP64)
+  float *ediag32 = nullptr;    // [dim] E_sigma rounded to FP32
+  int32_t *rowptr = nullptr;   // [dim+1]
+  int32_t *col = nullptr;      // [nnz] sorted per row
+  double *val = nullptr;       // [nnz]
+  float *val32 = nullptr;      // [nnz]
+};
+
+struct ed_sector_s {
+  ModelParams mp;
+  std::vector<double> e_imp, e_bath, v_bath;  // host copies (for neighbours)
+  double U = 0, Ust = 0, Jh = 0;
+  int nup = 0, ndw = 0;
+  int64_t dim = 0;
+  SpinTables sp[2];
+  double *W = nullptr;     // [2^norb][2^norb]
+  float *W32 = nullptr;
+  ed_sector nb[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};  // [spin][0:c,1:c+]
+  int64_t device_bytes = 0;
+  bool spin_symmetric = false;
+};
+
+// Binomial table C[n][k], n,k <= 32, in constant memory.  Built at compile
+// time (Pascal's rule) so every translation unit holds its own copy and no
+// upload or relocatable device code is needed.
+struct BinomTable {
+  uint64_t v[33][33];
+};
+constexpr BinomTable ed_make_binom() {
+  BinomTable t{};
+  for (int n = 0; n <= 32; ++n) {
+    t.v[n][0] = 1;
+    for (int k = 1; k <= n; ++k) t.v[n][k] = t.v[n - 1][k - 1] + (k <= n - 1 ? t.v[n - 1][k] : 0);
+  }
+  return t;
+}
+static __constant__ BinomTable c_binom_tab = ed_make_binom();
+#define c_binom (c_binom_tab.v)
+inline ed_status ed_upload_binomials() { return ED_OK; }
+
+__device__ __forceinline__ uint32_t ed_unrank(uint64_t r, int ns, int n) {
+  // Combinatorial number system: the r-th Ns-bit string with n set bits in
+  // ascending order has set bits p_1 < ... < p_n with r = sum_k C(p_k, k).
+  uint32_t I = 0;
+  for (int k = n; k >= 1; --k) {
+    int p = k - 1;
+    while (p + 1 < ns && c_binom[p + 1][k] <= r) ++p;
+    r -= c_binom[p][k];
+    I |= 1u << p;
+  }
+  return I;
+}
+
+__device__ __forceinline__ int64_t ed_rank(uint32_t I) {
+  int64_t r = 0;
+  int k = 0;
+  while (I) {
+    int p = __ffs(I) - 1;
+    ++k;
+    r += (int64_t)c_binom[p][k];
+    I &= I - 1;
+  }
+  return r;
+}
+
+// ----------------------------------------------------------------- kernels/launchers
+
+// sector.cu
+ed_status ed_build_sector_impl(const ModelParams &mp, double U, double Ust, double Jh,
+                               int nup, int ndw, cudaStream_t st, ed_sector s);
+ModelParams ed_model_params(const ed_model *m, ed_status *st);
+
+// matvec.cu
+template <typename T>
+struct HvTables {
+  int64_t dup, ddw;
+  const int32_t *rp_up, *col_up, *rp_dw, *col_dw;
+  const T *val_up, *val_dw, *e_up, *e_dw, *W;
+  const uint8_t *m_up, *m_dw;
+  int nmask;  // 2^norb
+};
+template <typename T>
+HvTables<T> ed_hv_tables(ed_sector s);
+
+// Lanczos device state (lanczos.cu).
+struct LanczosState {
+  int32_t j;          // completed steps
+  int32_t done;       // 0 running, 1 converged, 2 breakdown, 3 max_iter
+  int32_t maxit;
+  int32_t check_every;
+  double tol;
+  double tnorm;
+  double theta, rest;
+  double scale[3];    // logical vector = scale[b] * buffer b
+  double alpha[ED_MAX_LANCZOS];
+  double beta[ED_MAX_LANCZOS + 1];
+  double y[ED_MAX_LANCZOS];
+  double acc[4];      // scratch reductions
+};
+
+// Modes of the fused product kernel.
+enum { HV_PLAIN = 0, HV_LANCZOS = 1, HV_SECOND = 2 };
+
+template <typename T>
+ed_status ed_launch_hv(ed_sector s, const HvTables<T> &tb, int mode, const T *v, T *w,
+                       T *const *bufs, T *psi, LanczosState *state, double *part,
+                       int64_t *nparts, cudaStream_t st);
+
+int64_t ed_hv_num_parts(ed_sector s, int elem_size);
+template <typename T>
+ed_status ed_hv_prepare();
+
+// lanczos.cu
+int64_t ed_reduce_grid(int64_t n);
+template <typename T>
+ed_status ed_lanczos_chain(ed_sector s, T *const *bufs, LanczosState *st, double *part,
+                           double *part2, int64_t nparts_start, int nsteps, cudaStream_t cs,
+                           int32_t *h_flag);
+ed_status ed_lanczos_ground_impl(ed_sector s, const ed_lanczos_opts *o, ed_lanczos_result *res,
+                                 void *d_psi, cudaStream_t cs);
+
+// sector.cu
+ed_status ed_neighbor_sector(ed_sector s, int spin, int create, cudaStream_t st, ed_sector *out);

@@ -1,0 +1,852 @@
+// Lanczos ground state on the device (Sec. 6.6): plain Lanczos in the Paige
+// form without re-orthogonalisation, FP64 scalars, lowest Ritz pair of the
+// tridiagonal matrix by Sturm multisection, second pass for the ground-state
+// vector, and an FP64 polish for the FP32 modes.
+//
+// Per step j the host enqueues four kernels (captured in a CUDA graph and
+// replayed in chunks; every kernel exits at once when the device-side state
+// says the recurrence has stopped):
+//   k_hv<LANCZOS>   w1 = H v_j - beta_j v_{j-1}, block partials of <v_j, w1>
+//   k_alpha         alpha_j = sum of partials (fixed order)
+//   k_axpy_norm     w = w1 - alpha_j v_j, block partials of ||w||^2
+//   k_beta          beta_{j+1}, lazy scale of v_{j+1} = w / beta_{j+1},
+//                   Ritz value, residual estimate, stop test
+// Vectors rotate over three buffers (v_j in buffer j%3) and carry a lazy
+// scale factor so that no normalisation pass is needed.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "internal.cuh"
+
+constexpr int SCALAR_THREADS = 512;
+constexpr int AXPY_THREADS = 256;
+
+// ----------------------------------------------------------------- reductions
+
+__device__ __forceinline__ double warp_sum(double x) {
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+  return x;
+}
+
+// Deterministic sum of n partials by one CTA: thread t adds the strided
+// subsequence t, t+T, ... in order, then a fixed tree.
+__device__ double cta_sum_parts(const double *p, int64_t n, double *red) {
+  double s = 0.0;
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) s += p[i];
+  s = warp_sum(s);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) red[wid] = s;
+  __syncthreads();
+  double tot = 0.0;
+  if (threadIdx.x == 0) {
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) tot += red[k];
+    red[0] = tot;
+  }
+  __syncthreads();
+  tot = red[0];
+  __syncthreads();
+  return tot;
+}
+
+template <typename T>
+__device__ __forceinline__ T fmaT(T a, T b, T c);
+template <>
+__device__ __forceinline__ float fmaT<float>(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+template <>
+__device__ __forceinline__ double fmaT<double>(double a, double b, double c) {
+  return __fma_rn(a, b, c);
+}
+template <typename T>
+__device__ __forceinline__ T mulT(T a, T b);
+template <>
+__device__ __forceinline__ float mulT<float>(float a, float b) { return __fmul_rn(a, b); }
+template <>
+__device__ __forceinline__ double mulT<double>(double a, double b) { return __dmul_rn(a, b); }
+
+// ----------------------------------------------------------------- tridiagonal
+
+// Sturm count: eigenvalues of T_k below x = sign changes of the leading
+// principal minors p_i = det(T_i - x) (division-free recurrence, rescaled by
+// powers of two; an exact zero counts as a change, as a tiny negative pivot).
+__device__ int sturm_count(const double *a, const double *b, int k, double x) {
+  double pm = 1.0, p = a[0] - x;
+  int cnt = 0;
+  if (p <= 0.0) {
+    if (p == 0.0) p = -1e-300;
+    cnt = 1;
+  }
+  for (int i = 1; i < k; ++i) {
+    double pn = (a[i] - x) * p - b[i] * b[i] * pm;
+    if (pn == 0.0) pn = -copysign(1e-300, p);
+    if ((pn < 0.0) != (p < 0.0)) ++cnt;
+    pm = p;
+    p = pn;
+    double ap = fabs(p);
+    if (ap > 1e200 || ap < 1e-200) {
+      int e;
+      frexp(p, &e);
+      double f = ldexp(1.0, -e);
+      p *= f;
+      pm *= f;
+    }
+  }
+  return cnt;
+}
+
+// Squared last component of the normalised eigenvector of T_k for the
+// eigenvalue theta: -p_{k-1}(theta) / p_k'(theta).
+__device__ double last_component_sq(const double *a, const double *b, int k, double x) {
+  double pm = 1.0, p = a[0] - x;
+  double dpm = 0.0, dp = -1.0;
+  for (int i = 1; i < k; ++i) {
+    double pn = (a[i] - x) * p - b[i] * b[i] * pm;
+    double dpn = -p + (a[i] - x) * dp - b[i] * b[i] * dpm;
+    pm = p;
+    p = pn;
+    dpm = dp;
+    dp = dpn;
+    double m = fmax(fmax(fabs(p), fabs(pm)), fmax(fabs(dp), fabs(dpm)));
+    if (m > 1e200 || (m < 1e-200 && m > 0.0)) {
+      int e;
+      frexp(m, &e);
+      double f = ldexp(1.0, -e);
+      p *= f;
+      pm *= f;
+      dp *= f;
+      dpm *= f;
+    }
+  }
+  if (dp == 0.0) return 0.0;
+  double r = -pm / dp;
+  return r < 0.0 ? 0.0 : (r > 1.0 ? 1.0 : r);
+}
+
+// Ritz vector of T_k for theta by inverse iteration with the tridiagonal
+// (Thomas) solver: `sweeps` sweeps from a flat start, normalised, largest
+// entry positive.  One thread; `piv` holds k pivots, `y` k entries.
+__device__ void ritz_vector(const double *a, const double *b, int k, double th, int sweeps,
+                            double *piv, double *y) {
+  const double shift = th - 1e-13 * fmax(1.0, fabs(th));
+  piv[0] = a[0] - shift;
+  if (piv[0] == 0.0) piv[0] = 1e-300;
+  for (int i = 1; i < k; ++i) {
+    double m = b[i] / piv[i - 1];
+    double di = a[i] - shift - m * b[i];
+    piv[i] = di == 0.0 ? 1e-300 : di;
+  }
+  const double y0 = 1.0 / sqrt((double)k);
+  for (int i = 0; i < k; ++i) y[i] = y0;
+  for (int it = 0; it < sweeps; ++it) {
+    for (int i = 1; i < k; ++i) y[i] -= (b[i] / piv[i - 1]) * y[i - 1];
+    y[k - 1] = y[k - 1] / piv[k - 1];
+    for (int i = k - 2; i >= 0; --i) y[i] = (y[i] - b[i + 1] * y[i + 1]) / piv[i];
+    double s = 0.0;
+    for (int i = 0; i < k; ++i) s += y[i] * y[i];
+    s = 1.0 / sqrt(s);
+    for (int i = 0; i < k; ++i) y[i] *= s;
+  }
+  int im = 0;
+  for (int i = 1; i < k; ++i)
+    if (fabs(y[i]) > fabs(y[im])) im = i;
+  if (y[im] < 0.0)
+    for (int i = 0; i < k; ++i) y[i] = -y[i];
+}
+
+// Lowest eigenvalue of T_k by multisection: every thread evaluates the Sturm
+// count at one interior point; the bracket shrinks by blockDim+1 per round.
+__device__ double lowest_eigenvalue(const double *a, const double *b, int k, double hint_hi,
+                                    double hint_lo, double *sh) {
+  __shared__ int first;
+  __shared__ double blo, bhi;
+  if (threadIdx.x == 0) {
+    double lo = 1e300, hi = -1e300;
+    for (int i = 0; i < k; ++i) {
+      double rad = (i > 0 ? fabs(b[i]) : 0.0) + (i + 1 < k ? fabs(b[i + 1]) : 0.0);
+      lo = fmin(lo, a[i] - rad);
+      hi = fmax(hi, a[i] + rad);
+    }
+    blo = lo;
+    bhi = hi;
+  }
+  __syncthreads();
+  // warm bracket [hint_lo, hint_hi] when it provably contains the minimum
+  if (hint_hi < bhi && hint_lo > blo && hint_lo < hint_hi) {
+    __shared__ int ok;
+    if (threadIdx.x == 0) ok = (sturm_count(a, b, k, hint_lo) == 0 && sturm_count(a, b, k, hint_hi) >= 1);
+    __syncthreads();
+    if (ok && threadIdx.x == 0) {
+      blo = hint_lo;
+      bhi = hint_hi;
+    }
+    __syncthreads();
+  }
+  const int T = blockDim.x;
+  for (int round = 0; round < 64; ++round) {
+    double lo = blo, hi = bhi;
+    if (!(hi - lo > 4e-16 * fmax(1.0, fmax(fabs(lo), fabs(hi))))) break;
+    if (threadIdx.x == 0) first = T;
+    __syncthreads();
+    double x = lo + (hi - lo) * (double)(threadIdx.x + 1) / (double)(T + 1);
+    if (x > lo && x < hi && sturm_count(a, b, k, x) >= 1) atomicMin(&first, (int)threadIdx.x);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      int f = first;
+      double nlo = f == 0 ? lo : lo + (hi - lo) * (double)f / (double)(T + 1);
+      double nhi = f == T ? hi : lo + (hi - lo) * (double)(f + 1) / (double)(T + 1);
+      if (nlo == lo && nhi == hi) nhi = lo;  // no progress possible: stop
+      blo = nlo;
+      bhi = fmax(nhi, nlo);
+    }
+    __syncthreads();
+  }
+  double th = 0.5 * (blo + bhi);
+  __syncthreads();
+  return th;
+}
+
+// ----------------------------------------------------------------- kernels
+
+__global__ void k_alpha(LanczosState *st, const double *part, const int64_t nparts) {
+  __shared__ double red[SCALAR_THREADS / 32];
+  if (st->done) return;
+  double s = cta_sum_parts(part, nparts, red);
+  if (threadIdx.x == 0) st->alpha[st->j] = s;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(AXPY_THREADS) k_axpy_norm(LanczosState *st, T *b0, T *b1, T *b2,
+                                                            int64_t n, double *part) {
+  __shared__ double red[AXPY_THREADS / 32];
+  if (st->done) return;
+  const int j = st->j;
+  T *bufs[3] = {b0, b1, b2};
+  const T *v = bufs[j % 3];
+  T *w = bufs[(j + 1) % 3];
+  const T s = (T)st->scale[j % 3];
+  const T al = (T)st->alpha[j];
+  T acc = T(0);
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += stride) {
+    T x = fmaT<T>(-al, mulT<T>(v[i], s), w[i]);
+    w[i] = x;
+    acc = fmaT<T>(x, x, acc);
+  }
+  double d = warp_sum((double)acc);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) red[wid] = d;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double tot = 0.0;
+    for (int k = 0; k < AXPY_THREADS / 32; ++k) tot += red[k];
+    part[blockIdx.x] = tot;
+  }
+}
+
+// beta_{j+1}, scale, Ritz value and stop test.  `check` = 1 evaluates the
+// Ritz value every `check_every` steps (and always at the last step).
+__global__ void k_beta(LanczosState *st, const double *part, int64_t nparts) {
+  __shared__ double red[SCALAR_THREADS / 32];
+  __shared__ int stop;
+  __shared__ double s_piv[ED_MAX_LANCZOS];
+  if (st->done) return;
+  double s2 = cta_sum_parts(part, nparts, red);
+  const int j = st->j;
+  const double al = st->alpha[j];
+  const double be = sqrt(fmax(s2, 0.0));
+  if (threadIdx.x == 0) {
+    st->beta[j + 1] = be;
+    st->scale[(j + 1) % 3] = be > 0.0 ? 1.0 / be : 0.0;
+    st->tnorm = fmax(st->tnorm, fmax(fabs(al), be));
+    stop = 0;
+    if (be <= 1e-13 * st->tnorm) stop = 2;
+    else if (j + 1 >= st->maxit) stop = 3;
+  }
+  __syncthreads();
+  const int k = j + 1;
+  const bool want = st->tol > 0.0 && (stop != 0 || (k % st->check_every) == 0 || k <= 2);
+  if (want) {
+    double prev = st->theta;
+    double hi = (k > 1 && isfinite(prev)) ? prev : 1e300;
+    double dl = isfinite(st->acc[3]) ? fabs(st->acc[3]) : 0.0;
+    double lo = (k > 1 && isfinite(prev)) ? prev - fmax(8.0 * dl, 1e-9 * fmax(1.0, fabs(prev))) : -1e300;
+    double th = lowest_eigenvalue(st->alpha, st->beta, k, hi, lo, red);
+    if (threadIdx.x == 0) {
+      double y2 = last_component_sq(st->alpha, st->beta, k, th);
+      double rest = be * sqrt(y2);
+      // The polynomial formula loses relative accuracy once the Ritz value
+      // has converged; near convergence use inverse iteration instead.
+      if (rest < 1e-6 * fmax(1.0, fabs(th))) {
+        ritz_vector(st->alpha, st->beta, k, th, 3, s_piv, st->y);
+        rest = be * fabs(st->y[k - 1]);
+      }
+      st->acc[3] = isfinite(prev) ? th - prev : 1e300;
+      st->theta = th;
+      st->rest = rest;
+      if (stop == 0 && rest <= st->tol * fmax(1.0, fabs(th)) && k >= 2) stop = 1;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    if (stop) st->done = stop;
+    st->j = k;
+  }
+}
+
+// Start vector: element i = u_i - 1/2 with u_i the uniform double of output i
+// of a SplitMix64 stream seeded with `seed` (Steele, Lea, Flood 2014; top 53
+// bits times 2^-53), in sector order.  Partial sums of squares per CTA.
+__device__ __forceinline__ uint64_t splitmix64_at(uint64_t seed, uint64_t i) {
+  uint64_t z = seed + (i + 1ull) * 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(AXPY_THREADS) k_start_vector(T *v, int64_t n, uint64_t seed,
+                                                               double *part) {
+  __shared__ double red[AXPY_THREADS / 32];
+  T acc = T(0);
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += stride) {
+    double u = (double)(splitmix64_at(seed, (uint64_t)i) >> 11) * (1.0 / 9007199254740992.0);
+    T x = (T)(u - 0.5);
+    v[i] = x;
+    acc = fmaT<T>(x, x, acc);
+  }
+  double d = warp_sum((double)acc);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) red[wid] = d;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double tot = 0.0;
+    for (int k = 0; k < AXPY_THREADS / 32; ++k) tot += red[k];
+    part[blockIdx.x] = tot;
+  }
+}
+
+// Sum of squares of a vector (partials per CTA).
+template <typename T>
+__global__ void __launch_bounds__(AXPY_THREADS) k_norm2(const T *v, int64_t n, double *part) {
+  __shared__ double red[AXPY_THREADS / 32];
+  T acc = T(0);
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += stride)
+    acc = fmaT<T>(v[i], v[i], acc);
+  double d = warp_sum((double)acc);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) red[wid] = d;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double tot = 0.0;
+    for (int k = 0; k < AXPY_THREADS / 32; ++k) tot += red[k];
+    part[blockIdx.x] = tot;
+  }
+}
+
+// Initialise the recurrence state: v_0 = buffer 0 scaled by 1/||buffer 0||.
+__global__ void k_state_init(LanczosState *st, const double *part, int64_t nparts, int maxit,
+                             double tol, int check_every) {
+  __shared__ double red[SCALAR_THREADS / 32];
+  double s = cta_sum_parts(part, nparts, red);
+  if (threadIdx.x == 0) {
+    st->j = 0;
+    st->done = s > 0.0 ? 0 : 2;
+    st->maxit = maxit;
+    st->check_every = check_every;
+    st->tol = tol;
+    st->tnorm = 0.0;
+    st->theta = INFINITY;
+    st->rest = INFINITY;
+    st->scale[0] = s > 0.0 ? 1.0 / sqrt(s) : 0.0;
+    st->scale[1] = 0.0;
+    st->scale[2] = 0.0;
+    st->beta[0] = 0.0;
+    st->acc[0] = s;
+    st->acc[1] = st->acc[2] = 0.0;
+    st->acc[3] = INFINITY;
+  }
+}
+
+// Final Ritz vector of T_k (4 inverse-iteration sweeps), one thread.
+__global__ void k_tridiag_vector(LanczosState *st, int k) {
+  extern __shared__ double piv[];
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  ritz_vector(st->alpha, st->beta, k, st->theta, 4, piv, st->y);
+}
+
+// Second pass bookkeeping: v_{j+1} = w / beta_{j+1}.
+__global__ void k_second_advance(LanczosState *st) {
+  const int j = st->j;
+  const double be = st->beta[j + 1];
+  st->scale[(j + 1) % 3] = be > 0.0 ? 1.0 / be : 0.0;
+  st->j = j + 1;
+}
+
+// psi += y_j * scale * buf (last vector of the second pass).
+template <typename T>
+__global__ void k_psi_tail(const LanczosState *st, const T *b0, const T *b1, const T *b2, T *psi,
+                           int64_t n) {
+  const int j = st->j;
+  const T *bufs[3] = {b0, b1, b2};
+  const T *v = bufs[j % 3];
+  const T s = (T)st->scale[j % 3];
+  const T y = (T)st->y[j];
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += stride)
+    psi[i] = fmaT<T>(y, mulT<T>(v[i], s), psi[i]);
+}
+
+template <typename Ti, typename To>
+__global__ void k_scale_copy(const Ti *x, To *y, int64_t n, const double *part, int64_t nparts) {
+  __shared__ double red[AXPY_THREADS / 32];
+  __shared__ double sc;
+  double s = 0.0;
+  for (int64_t i = threadIdx.x; i < nparts; i += blockDim.x) s += part[i];
+  s = warp_sum(s);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) red[wid] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += red[k];
+    sc = t > 0.0 ? 1.0 / sqrt(t) : 0.0;
+  }
+  __syncthreads();
+  const double f = sc;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += stride)
+    y[i] = (To)((double)x[i] * f);
+}
+
+// Residual pieces of psi (normalised) and w = H psi: <psi,w>, ||w||^2,
+// ||psi||^2 per CTA (FP64).
+__global__ void __launch_bounds__(AXPY_THREADS) k_resid_parts(const double *psi, const double *w,
+                                                              int64_t n, double *part,
+                                                              int64_t nparts) {
+  __shared__ double red[3][AXPY_THREADS / 32];
+  double a = 0, b = 0, c = 0;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += stride) {
+    a = fma(psi[i], w[i], a);
+    b = fma(w[i], w[i], b);
+    c = fma(psi[i], psi[i], c);
+  }
+  a = warp_sum(a);
+  b = warp_sum(b);
+  c = warp_sum(c);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) {
+    red[0][wid] = a;
+    red[1][wid] = b;
+    red[2][wid] = c;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double ta = 0, tb = 0, tc = 0;
+    for (int k = 0; k < AXPY_THREADS / 32; ++k) {
+      ta += red[0][k];
+      tb += red[1][k];
+      tc += red[2][k];
+    }
+    part[blockIdx.x] = ta;
+    part[nparts + blockIdx.x] = tb;
+    part[2 * nparts + blockIdx.x] = tc;
+  }
+}
+
+__global__ void k_resid_final(const double *part, int64_t nparts, double *out) {
+  __shared__ double red[SCALAR_THREADS / 32];
+  double a = cta_sum_parts(part, nparts, red);
+  double b = cta_sum_parts(part + nparts, nparts, red);
+  double c = cta_sum_parts(part + 2 * nparts, nparts, red);
+  if (threadIdx.x == 0) {
+    double e = a / c;
+    // ||w - e psi||^2 = ||w||^2 - 2 e <psi,w> + e^2 ||psi||^2
+    double r2 = b - 2.0 * e * a + e * e * c;
+    out[0] = e;
+    out[1] = sqrt(fmax(r2, 0.0) / c);
+  }
+}
+
+// ----------------------------------------------------------------- host driver
+
+struct Workspace {
+  void *mem = nullptr;
+  cudaStream_t st = nullptr;
+  ed_status alloc(size_t bytes, cudaStream_t s) {
+    st = s;
+    cudaError_t e = cudaMallocAsync(&mem, std::max<size_t>(bytes, 256), s);
+    if (e != cudaSuccess) {
+      ed_set_cuda_error(e, "cudaMallocAsync(workspace)", __FILE__, __LINE__);
+      mem = nullptr;
+      return ED_ERR_OOM;
+    }
+    return ED_OK;
+  }
+  ~Workspace() {
+    if (mem) cudaFreeAsync(mem, st);
+  }
+};
+
+static int64_t reduce_grid(int64_t n) {
+  int64_t g = (n + AXPY_THREADS * 8 - 1) / (AXPY_THREADS * 8);
+  return std::max<int64_t>(1, std::min<int64_t>(g, 152 * 8));
+}
+
+static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// Library-private stream of the calling thread (one per device): CUDA graph
+// capture is not allowed on the legacy default stream, so the captured
+// Lanczos chunks run here, ordered after and before the caller's stream by
+// events.
+static cudaStream_t private_stream(ed_status *st) {
+  static thread_local cudaStream_t streams[64] = {nullptr};
+  int dev = 0;
+  *st = ED_OK;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev >= 64) {
+    *st = ED_ERR_CUDA;
+    return nullptr;
+  }
+  if (!streams[dev]) {
+    cudaError_t e = cudaStreamCreateWithFlags(&streams[dev], cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+      ed_set_cuda_error(e, "cudaStreamCreateWithFlags", __FILE__, __LINE__);
+      *st = ED_ERR_CUDA;
+      return nullptr;
+    }
+  }
+  return streams[dev];
+}
+
+struct StreamJoin {
+  cudaEvent_t ev = nullptr;
+  ~StreamJoin() {
+    if (ev) cudaEventDestroy(ev);
+  }
+  ed_status order(cudaStream_t from, cudaStream_t to) {
+    if (!ev) ED_TRY_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    ED_TRY_CUDA(cudaEventRecord(ev, from));
+    ED_TRY_CUDA(cudaStreamWaitEvent(to, ev, 0));
+    return ED_OK;
+  }
+};
+
+// Runs Lanczos steps until the device state stops: chunks of `chunk` steps,
+// each chunk one CUDA graph launch, then a 4-byte read of the stop flag.
+template <typename T>
+static ed_status run_steps(ed_sector s, const HvTables<T> &tb, T *const *bufs, LanczosState *st,
+                           double *part, double *part2, int64_t n, int maxit, cudaStream_t caller,
+                           int *steps_out, int32_t *h_flag) {
+  int64_t np1 = 0;
+  const int64_t g2 = reduce_grid(n);
+  int chunk = n < (1 << 20) ? 16 : 4;
+  chunk = std::min(chunk, std::max(1, maxit));
+  ed_status ps = ED_OK;
+  cudaStream_t cs = private_stream(&ps);
+  if (ps != ED_OK) return ps;
+  StreamJoin join;
+  ED_TRY(join.order(caller, cs));
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  ED_TRY(ed_hv_prepare<T>());
+  ED_TRY_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+  ed_status rs = ED_OK;
+  for (int it = 0; it < chunk && rs == ED_OK; ++it) {
+    rs = ed_launch_hv<T>(s, tb, HV_LANCZOS, nullptr, nullptr, bufs, nullptr, st, part, &np1, cs);
+    if (rs != ED_OK) break;
+    k_alpha<<<1, SCALAR_THREADS, 0, cs>>>(st, part, np1);
+    k_axpy_norm<T><<<(unsigned)g2, AXPY_THREADS, 0, cs>>>(st, bufs[0], bufs[1], bufs[2], n, part2);
+    k_beta<<<1, SCALAR_THREADS, 0, cs>>>(st, part2, g2);
+  }
+  cudaError_t ce = cudaStreamEndCapture(cs, &graph);
+  ed_count_launches(-(int64_t)chunk);  // the captured launches run inside the graph
+  if (rs != ED_OK) {
+    if (graph) cudaGraphDestroy(graph);
+    return rs;
+  }
+  ED_TRY_CUDA(ce);
+  ce = cudaGraphInstantiate(&exec, graph, 0);
+  cudaGraphDestroy(graph);
+  ED_TRY_CUDA(ce);
+  int launched = 0;
+  ed_status out = ED_OK;
+  while (launched < maxit) {
+    cudaError_t e = cudaGraphLaunch(exec, cs);
+    if (e != cudaSuccess) {
+      ed_set_cuda_error(e, "cudaGraphLaunch", __FILE__, __LINE__);
+      out = ED_ERR_CUDA;
+      break;
+    }
+    ed_count_launches(4 * chunk);
+    launched += chunk;
+    e = cudaMemcpyAsync(h_flag, &st->done, sizeof(int32_t), cudaMemcpyDeviceToHost, cs);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(cs);
+    if (e != cudaSuccess) {
+      ed_set_cuda_error(e, "Lanczos stop flag", __FILE__, __LINE__);
+      out = ED_ERR_CUDA;
+      break;
+    }
+    if (*h_flag) break;
+  }
+  cudaGraphExecDestroy(exec);
+  ed_status js = join.order(cs, caller);
+  if (out == ED_OK) out = js;
+  if (steps_out) *steps_out = launched;
+  return out;
+}
+
+// Second pass: rebuild v_0..v_{k-1} from the stored coefficients and
+// accumulate psi = sum_j y_j v_j.
+template <typename T>
+static ed_status second_pass(ed_sector s, const HvTables<T> &tb, T *const *bufs, T *psi,
+                             LanczosState *st, int k, int64_t n, cudaStream_t cs) {
+  ED_TRY_CUDA(cudaMemsetAsync(psi, 0, n * sizeof(T), cs));
+  for (int j = 0; j + 1 < k; ++j) {
+    ED_TRY(ed_launch_hv<T>(s, tb, HV_SECOND, nullptr, nullptr, bufs, psi, st, nullptr, nullptr, cs));
+    k_second_advance<<<1, 1, 0, cs>>>(st);
+    ED_LAUNCHED(1);
+  }
+  int64_t g = reduce_grid(n);
+  k_psi_tail<T><<<(unsigned)g, AXPY_THREADS, 0, cs>>>(st, bufs[0], bufs[1], bufs[2], psi, n);
+  ED_LAUNCHED(1);
+  return ED_OK;
+}
+
+struct PinnedFlag {
+  int32_t *p = nullptr;
+  PinnedFlag() { cudaMallocHost((void **)&p, 64); }
+  ~PinnedFlag() {
+    if (p) cudaFreeHost(p);
+  }
+};
+
+// One Lanczos solve in precision T on sector s, starting from either the
+// seeded vector or (start != nullptr) a given vector in precision T.
+template <typename T>
+static ed_status lanczos_solve(ed_sector s, int maxit, double tol, uint64_t seed, const T *start,
+                               bool want_vector, T *psi_out, LanczosState *h_state,
+                               cudaStream_t cs, int *matvecs) {
+  const int64_t n = s->dim;
+  const int64_t np1 = ed_hv_num_parts(s, (int)sizeof(T));
+  const int64_t g2 = reduce_grid(n);
+  const int64_t nparts = std::max<int64_t>(np1, 3 * g2);
+  size_t vb = align256(n * sizeof(T));
+  size_t bytes = 3 * vb + (want_vector ? vb : 0) + align256(sizeof(LanczosState)) +
+                 2 * align256(nparts * sizeof(double));
+  Workspace ws;
+  ED_TRY(ws.alloc(bytes, cs));
+  char *p = (char *)ws.mem;
+  T *bufs[3];
+  for (int b = 0; b < 3; ++b) {
+    bufs[b] = (T *)p;
+    p += vb;
+  }
+  T *psi = nullptr;
+  if (want_vector) {
+    psi = (T *)p;
+    p += vb;
+  }
+  LanczosState *st = (LanczosState *)p;
+  p += align256(sizeof(LanczosState));
+  double *part = (double *)p;
+  p += align256(nparts * sizeof(double));
+  double *part2 = (double *)p;
+
+  PinnedFlag flag;
+  const int check_every = n > (1 << 22) ? 1 : 4;
+  auto init = [&]() -> ed_status {
+    if (start) {
+      ED_TRY_CUDA(cudaMemcpyAsync(bufs[0], start, n * sizeof(T), cudaMemcpyDeviceToDevice, cs));
+      k_norm2<T><<<(unsigned)g2, AXPY_THREADS, 0, cs>>>(bufs[0], n, part);
+    } else {
+      k_start_vector<T><<<(unsigned)g2, AXPY_THREADS, 0, cs>>>(bufs[0], n, seed, part);
+    }
+    ED_LAUNCHED(1);
+    k_state_init<<<1, SCALAR_THREADS, 0, cs>>>(st, part, g2, maxit, tol, check_every);
+    ED_LAUNCHED(1);
+    return ED_OK;
+  };
+  ED_TRY(init());
+  HvTables<T> tb = ed_hv_tables<T>(s);
+  int launched = 0;
+  ED_TRY(run_steps<T>(s, tb, bufs, st, part, part2, n, maxit, cs, &launched, flag.p));
+  ED_TRY_CUDA(cudaMemcpyAsync(h_state, st, sizeof(LanczosState), cudaMemcpyDeviceToHost, cs));
+  ED_TRY_CUDA(cudaStreamSynchronize(cs));
+  const int k = h_state->j;
+  int mv = k;
+  if (want_vector && k > 0) {
+    k_tridiag_vector<<<1, 1, sizeof(double) * ED_MAX_LANCZOS, cs>>>(st, k);
+    ED_LAUNCHED(1);
+    // restart the recurrence bookkeeping for the second pass
+    ED_TRY(init());
+    ED_TRY(second_pass<T>(s, tb, bufs, psi, st, k, n, cs));
+    mv += k - 1;
+    // normalise psi into the output
+    k_norm2<T><<<(unsigned)g2, AXPY_THREADS, 0, cs>>>(psi, n, part2);
+    ED_LAUNCHED(1);
+    k_scale_copy<T, T><<<(unsigned)g2, AXPY_THREADS, 0, cs>>>(psi, psi_out, n, part2, g2);
+    ED_LAUNCHED(1);
+    ED_TRY_CUDA(cudaMemcpyAsync(h_state->y, st->y, sizeof(double) * k, cudaMemcpyDeviceToHost, cs));
+  }
+  ED_TRY_CUDA(cudaStreamSynchronize(cs));
+  if (matvecs) *matvecs += mv;
+  return ED_OK;
+}
+
+// FP64 residual of a normalised FP64 vector: returns (Rayleigh quotient,
+// ||H psi - e psi||).
+static ed_status fp64_residual(ed_sector s, const double *psi, double *e, double *r,
+                               cudaStream_t cs) {
+  const int64_t n = s->dim;
+  const int64_t g2 = reduce_grid(n);
+  size_t bytes = align256(n * sizeof(double)) + align256(3 * g2 * sizeof(double)) + 256;
+  Workspace ws;
+  ED_TRY(ws.alloc(bytes, cs));
+  double *w = (double *)ws.mem;
+  double *part = (double *)((char *)ws.mem + align256(n * sizeof(double)));
+  double *out = part + 3 * g2 + 8;
+  out = (double *)(((uintptr_t)out + 255) & ~(uintptr_t)255);
+  if ((char *)out + 16 > (char *)ws.mem + bytes) out = part + 3 * g2;
+  ED_TRY(ed_launch_hv<double>(s, ed_hv_tables<double>(s), HV_PLAIN, psi, w, nullptr, nullptr,
+                              nullptr, nullptr, nullptr, cs));
+  k_resid_parts<<<(unsigned)g2, AXPY_THREADS, 0, cs>>>(psi, w, n, part, g2);
+  ED_LAUNCHED(1);
+  k_resid_final<<<1, SCALAR_THREADS, 0, cs>>>(part, g2, out);
+  ED_LAUNCHED(1);
+  double h[2];
+  ED_TRY_CUDA(cudaMemcpyAsync(h, out, sizeof(h), cudaMemcpyDeviceToHost, cs));
+  ED_TRY_CUDA(cudaStreamSynchronize(cs));
+  *e = h[0];
+  *r = h[1];
+  return ED_OK;
+}
+
+static void fill_result(const LanczosState &h, ed_lanczos_result *res) {
+  res->e0_raw = h.theta;
+  res->e0 = h.theta;
+  res->residual_estimate = h.rest;
+  res->iterations = h.j;
+  res->stop_reason = h.done == 1 ? 0 : (h.done == 2 ? 1 : 2);
+}
+
+ed_status ed_lanczos_ground_impl(ed_sector s, const ed_lanczos_opts *o, ed_lanczos_result *res,
+                                 void *d_psi, cudaStream_t cs) {
+  memset(res, 0, sizeof(*res));
+  int maxit = o->max_iter > 0 ? o->max_iter : 512;
+  if (maxit > ED_MAX_LANCZOS) return ED_ERR_ARG;
+  const ed_precision prec = o->precision;
+  if (prec != ED_FP64 && prec != ED_FP32 && prec != ED_FP32_POLISH) return ED_ERR_ARG;
+  double tol = o->tol > 0 ? o->tol : (prec == ED_FP64 ? 1e-12 : 1e-6);
+  const bool want = o->want_vector != 0 || prec == ED_FP32_POLISH;
+  const int64_t n = s->dim;
+  if (n <= 0) return ED_ERR_ARG;
+  std::vector<char> hbuf(sizeof(LanczosState));
+  LanczosState *h = (LanczosState *)hbuf.data();
+  int mv = 0;
+  if (prec == ED_FP64) {
+    Workspace psi;
+    double *dpsi = (double *)d_psi;
+    if (want && !dpsi) {
+      ED_TRY(psi.alloc(n * sizeof(double), cs));
+      dpsi = (double *)psi.mem;
+    }
+    ED_TRY(lanczos_solve<double>(s, maxit, tol, o->seed, nullptr, want, dpsi, h, cs, &mv));
+    fill_result(*h, res);
+    if (want) {
+      double e, r;
+      ED_TRY(fp64_residual(s, dpsi, &e, &r, cs));
+      res->residual = r;
+      ++mv;
+    }
+  } else {
+    Workspace psi32;
+    float *fpsi = (prec == ED_FP32) ? (float *)d_psi : nullptr;
+    if (want && !fpsi) {
+      ED_TRY(psi32.alloc(n * sizeof(float), cs));
+      fpsi = (float *)psi32.mem;
+    }
+    ED_TRY(lanczos_solve<float>(s, maxit, tol, o->seed, nullptr, want, fpsi, h, cs, &mv));
+    fill_result(*h, res);
+    if (prec == ED_FP32_POLISH) {
+      // FP64 Lanczos restarted from the FP32 ground state (a6): a few FP64
+      // steps, their Ritz pair, and the FP64 residual of the result.
+      const int steps = o->polish_steps > 0 ? o->polish_steps : 4;
+      Workspace start, psi64;
+      ED_TRY(start.alloc(n * sizeof(double), cs));
+      double *dst = (double *)d_psi;
+      if (!dst) {
+        ED_TRY(psi64.alloc(n * sizeof(double), cs));
+        dst = (double *)psi64.mem;
+      }
+      const int64_t g2 = reduce_grid(n);
+      Workspace prt;
+      ED_TRY(prt.alloc(g2 * sizeof(double), cs));
+      k_norm2<float><<<(unsigned)g2, AXPY_THREADS, 0, cs>>>(fpsi, n, (double *)prt.mem);
+      ED_LAUNCHED(1);
+      k_scale_copy<float, double><<<(unsigned)g2, AXPY_THREADS, 0, cs>>>(
+          fpsi, (double *)start.mem, n, (double *)prt.mem, g2);
+      ED_LAUNCHED(1);
+      std::vector<char> h2buf(sizeof(LanczosState));
+      LanczosState *h2 = (LanczosState *)h2buf.data();
+      ED_TRY(lanczos_solve<double>(s, steps, 1e-300, 0, (const double *)start.mem, true, dst, h2,
+                                   cs, &mv));
+      res->e0 = h2->theta;
+      res->polish_iterations = h2->j;
+      double e, r;
+      ED_TRY(fp64_residual(s, dst, &e, &r, cs));
+      res->residual = r;
+      ++mv;
+    } else if (want) {
+      // report the FP64 residual of the FP32 vector
+      Workspace tmp;
+      ED_TRY(tmp.alloc(n * sizeof(double), cs));
+      const int64_t g2 = reduce_grid(n);
+      Workspace prt;
+      ED_TRY(prt.alloc(g2 * sizeof(double), cs));
+      k_norm2<float><<<(unsigned)g2, AXPY_THREADS, 0, cs>>>(fpsi, n, (double *)prt.mem);
+      ED_LAUNCHED(1);
+      k_scale_copy<float, double><<<(unsigned)g2, AXPY_THREADS, 0, cs>>>(
+          fpsi, (double *)tmp.mem, n, (double *)prt.mem, g2);
+      ED_LAUNCHED(1);
+      double e, r;
+      ED_TRY(fp64_residual(s, (const double *)tmp.mem, &e, &r, cs));
+      res->residual = r;
+      ++mv;
+    }
+  }
+  res->matvecs = mv;
+  if (res->stop_reason == 2) return ED_ERR_NOT_CONVERGED;
+  return ED_OK;
+}
+
+// ----------------------------------------------------------------- chains (GF)
+
+// A Lanczos chain of `nsteps` steps from a start vector (already in bufs[0]
+// with partial squares in `part`): coefficients left in the device state.
+template <typename T>
+ed_status ed_lanczos_chain(ed_sector s, T *const *bufs, LanczosState *st, double *part,
+                           double *part2, int64_t nparts_start, int nsteps, cudaStream_t cs,
+                           int32_t *h_flag) {
+  k_state_init<<<1, SCALAR_THREADS, 0, cs>>>(st, part, nparts_start, nsteps, 0.0, 1);
+  ED_LAUNCHED(1);
+  HvTables<T> tb = ed_hv_tables<T>(s);
+  int launched = 0;
+  return run_steps<T>(s, tb, bufs, st, part, part2, s->dim, nsteps, cs, &launched, h_flag);
+}
+
+template ed_status ed_lanczos_chain<float>(ed_sector, float *const *, LanczosState *, double *,
+                                           double *, int64_t, int, cudaStream_t, int32_t *);
+template ed_status ed_lanczos_chain<double>(ed_sector, double *const *, LanczosState *, double *,
+                                            double *, int64_t, int, cudaStream_t, int32_t *);
+
+int64_t ed_reduce_grid(int64_t n) { return reduce_grid(n); }
+
+extern "C" ed_status ed_lanczos_ground(ed_sector s, const ed_lanczos_opts *opts,
+                                       ed_lanczos_result *res, void *d_psi, void *stream) {
+  if (!s || !opts || !res) return ED_ERR_ARG;
+  return ed_lanczos_ground_impl(s, opts, res, d_psi, (cudaStream_t)stream);
+}

@@ -1,0 +1,371 @@
+// Sector set-up on the device: basis enumeration, ranks, per-spin CSR
+// hopping matrices and diagonal tables (Sec. 2.3-2.4, Sec. 6.3).
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+
+#include "internal.cuh"
+
+static uint64_t host_binom(int n, int k) {
+  if (k < 0 || k > n) return 0;
+  uint64_t r = 1;
+  for (int i = 1; i <= k; ++i) r = r * (uint64_t)(n - k + i) / (uint64_t)i;
+  return r;
+}
+
+ModelParams ed_model_params(const ed_model *m, ed_status *st) {
+  ModelParams mp;
+  memset(&mp, 0, sizeof(mp));
+  *st = ED_OK;
+  if (!m || m->norb < 1 || m->nbath < 0 || !m->e_imp || (m->nbath > 0 && (!m->e_bath || !m->v_bath))) {
+    *st = ED_ERR_ARG;
+    return mp;
+  }
+  if (m->norb > ED_MAX_NORB || m->norb * (m->nbath + 1) > ED_MAX_NS) {
+    *st = ED_ERR_UNSUPPORTED;
+    return mp;
+  }
+  if (m->Jx != 0.0 || m->Jp != 0.0) {
+    *st = ED_ERR_UNSUPPORTED;
+    return mp;
+  }
+  mp.norb = m->norb;
+  mp.nbath = m->nbath;
+  mp.ns = m->norb * (m->nbath + 1);
+  mp.U = m->U;
+  mp.Ust = m->Ust;
+  mp.Jh = m->Jh;
+  for (int s = 0; s < 2; ++s) {
+    for (int a = 0; a < m->norb; ++a) {
+      mp.eps[s][a] = m->e_imp[s * m->norb + a];
+      mp.V[s][a] = 0.0;
+      mp.orb_of_level[a] = a;
+      for (int nu = 0; nu < m->nbath; ++nu) {
+        int lev = m->norb + a * m->nbath + nu;
+        mp.eps[s][lev] = m->e_bath[(s * m->norb + a) * m->nbath + nu];
+        mp.V[s][lev] = m->v_bath[(s * m->norb + a) * m->nbath + nu];
+        mp.orb_of_level[lev] = a;
+      }
+    }
+  }
+  return mp;
+}
+
+// ----------------------------------------------------------------- kernels
+
+// One thread per basis state: the string (unrank), impurity mask, diagonal
+// energy E_sigma = sum_a eps_a n_a + (U'-J) sum_{alpha<beta} n_alpha n_beta.
+__global__ void k_spin_basis(ModelParams mp, int spin, int n, int64_t dim, uint32_t *map,
+                             uint8_t *imask, double *ediag, float *ediag32) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= dim) return;
+  uint32_t I = ed_unrank((uint64_t)i, mp.ns, n);
+  map[i] = I;
+  uint32_t m = I & ((1u << mp.norb) - 1u);
+  imask[i] = (uint8_t)m;
+  double e = 0.0;
+  for (int a = 0; a < mp.ns; ++a)
+    if ((I >> a) & 1u) e += mp.eps[spin][a];
+  int k = __popc(m);
+  e += (mp.Ust - mp.Jh) * (double)(k * (k - 1) / 2);
+  ediag[i] = e;
+  ediag32[i] = (float)e;
+}
+
+// Hops of one state: for each bath level b of orbital alpha, exactly one of
+// (impurity level alpha, b) occupied -> one matrix element of H_sigma.
+__device__ __forceinline__ int hop_count(const ModelParams &mp, uint32_t I) {
+  int c = 0;
+  for (int b = mp.norb; b < mp.ns; ++b) {
+    int d = mp.orb_of_level[b];
+    c += (int)(((I >> d) ^ (I >> b)) & 1u);
+  }
+  return c;
+}
+
+__global__ void k_row_counts(ModelParams mp, int64_t dim, const uint32_t *map, int32_t *cnt) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= dim) return;
+  cnt[i] = hop_count(mp, map[i]);
+}
+
+// Exclusive scan of the row counts into rowptr (one CTA, fixed order).
+__global__ void k_scan_rowptr(int64_t dim, const int32_t *cnt, int32_t *rowptr) {
+  __shared__ int32_t sums[1024];
+  const int T = blockDim.x;
+  const int t = threadIdx.x;
+  int64_t chunk = (dim + T - 1) / T;
+  int64_t lo = t * chunk, hi = min(dim, lo + chunk);
+  int32_t s = 0;
+  for (int64_t i = lo; i < hi; ++i) s += cnt[i];
+  sums[t] = s;
+  __syncthreads();
+  if (t == 0) {
+    int32_t run = 0;
+    for (int k = 0; k < T; ++k) {
+      int32_t x = sums[k];
+      sums[k] = run;
+      run += x;
+    }
+  }
+  __syncthreads();
+  int32_t run = sums[t];
+  for (int64_t i = lo; i < hi; ++i) {
+    rowptr[i] = run;
+    run += cnt[i];
+  }
+  if (hi == dim && lo < hi) rowptr[dim] = run;
+  if (dim == 0 && t == 0) rowptr[0] = 0;
+}
+
+// CSR fill: H_sigma[i, j] = V * (-1)^(occupied levels strictly between the
+// two levels) for J = I with the electron moved (Eq. Hbuild, Sec. 2.3 signs).
+__global__ void k_fill_csr(ModelParams mp, int spin, int64_t dim, const uint32_t *map,
+                           const int32_t *rowptr, int32_t *col, double *val, float *val32) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= dim) return;
+  uint32_t I = map[i];
+  int32_t cs[ED_MAX_NS];
+  double vs[ED_MAX_NS];
+  int m = 0;
+  for (int b = mp.norb; b < mp.ns; ++b) {
+    int d = mp.orb_of_level[b];
+    if ((((I >> d) ^ (I >> b)) & 1u) == 0u) continue;
+    uint32_t J = I ^ (1u << d) ^ (1u << b);
+    int lo = d < b ? d : b, hi = d < b ? b : d;
+    uint32_t between = ((1u << hi) - 1u) & ~((2u << lo) - 1u);
+    double sg = (__popc(I & between) & 1) ? -1.0 : 1.0;
+    int32_t c = (int32_t)ed_rank(J);
+    double v = sg * mp.V[spin][b];
+    // insertion keeps the row sorted by column
+    int p = m;
+    while (p > 0 && cs[p - 1] > c) {
+      cs[p] = cs[p - 1];
+      vs[p] = vs[p - 1];
+      --p;
+    }
+    cs[p] = c;
+    vs[p] = v;
+    ++m;
+  }
+  int32_t o = rowptr[i];
+  for (int k = 0; k < m; ++k) {
+    col[o + k] = cs[k];
+    val[o + k] = vs[k];
+    val32[o + k] = (float)vs[k];
+  }
+}
+
+// W[m_up][m_dw] = U sum_a n_a,up n_a,dw + U' sum_{a != b} n_a,up n_b,dw.
+__global__ void k_wtable(ModelParams mp, double *W, float *W32) {
+  int nm = 1 << mp.norb;
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nm * nm) return;
+  int mu = t / nm, md = t % nm;
+  double w = 0.0;
+  for (int a = 0; a < mp.norb; ++a)
+    for (int b = 0; b < mp.norb; ++b)
+      if (((mu >> a) & 1) && ((md >> b) & 1)) w += (a == b) ? mp.U : mp.Ust;
+  W[t] = w;
+  W32[t] = (float)w;
+}
+
+// ----------------------------------------------------------------- host
+
+template <typename P>
+static ed_status dalloc(ed_sector s, P **p, size_t count) {
+  size_t bytes = std::max<size_t>(count, 1) * sizeof(P);
+  cudaError_t e = cudaMalloc((void **)p, bytes);
+  if (e != cudaSuccess) {
+    ed_set_cuda_error(e, "cudaMalloc(sector table)", __FILE__, __LINE__);
+    return ED_ERR_OOM;
+  }
+  s->device_bytes += (int64_t)bytes;
+  return ED_OK;
+}
+
+static ed_status build_spin(ed_sector s, int spin, int n, cudaStream_t st) {
+  const ModelParams &mp = s->mp;
+  SpinTables &t = s->sp[spin];
+  t.n = n;
+  t.dim = (int64_t)host_binom(mp.ns, n);
+  // every bath level contributes 2*C(Ns-2, n-1) hops (exactly one of the two
+  // levels occupied)
+  t.nnz = (int64_t)mp.norb * mp.nbath * 2 * (int64_t)host_binom(mp.ns - 2, n - 1);
+  if (t.nnz >= (int64_t)INT32_MAX) return ED_ERR_UNSUPPORTED;
+  ED_TRY(dalloc(s, &t.map, t.dim));
+  ED_TRY(dalloc(s, &t.imask, t.dim));
+  ED_TRY(dalloc(s, &t.ediag, t.dim));
+  ED_TRY(dalloc(s, &t.ediag32, t.dim));
+  ED_TRY(dalloc(s, &t.rowptr, t.dim + 1));
+  ED_TRY(dalloc(s, &t.col, t.nnz));
+  ED_TRY(dalloc(s, &t.val, t.nnz));
+  ED_TRY(dalloc(s, &t.val32, t.nnz));
+  int32_t *cnt = nullptr;
+  ED_TRY_CUDA(cudaMallocAsync((void **)&cnt, std::max<int64_t>(t.dim, 1) * sizeof(int32_t), st));
+  int threads = 256;
+  int blocks = (int)((t.dim + threads - 1) / threads);
+  if (t.dim > 0) {
+    k_spin_basis<<<blocks, threads, 0, st>>>(mp, spin, n, t.dim, t.map, t.imask, t.ediag,
+                                             t.ediag32);
+    ED_LAUNCHED(1);
+    k_row_counts<<<blocks, threads, 0, st>>>(mp, t.dim, t.map, cnt);
+    ED_LAUNCHED(1);
+  }
+  k_scan_rowptr<<<1, 1024, 0, st>>>(t.dim, cnt, t.rowptr);
+  ED_LAUNCHED(1);
+  if (t.dim > 0) {
+    k_fill_csr<<<blocks, threads, 0, st>>>(mp, spin, t.dim, t.map, t.rowptr, t.col, t.val,
+                                           t.val32);
+    ED_LAUNCHED(1);
+  }
+  ED_TRY_CUDA(cudaFreeAsync(cnt, st));
+  return ED_OK;
+}
+
+ed_status ed_build_sector_impl(const ModelParams &mp, double U, double Ust, double Jh, int nup,
+                               int ndw, cudaStream_t st, ed_sector s) {
+  ED_TRY(ed_upload_binomials());
+  s->mp = mp;
+  s->U = U;
+  s->Ust = Ust;
+  s->Jh = Jh;
+  s->nup = nup;
+  s->ndw = ndw;
+  ED_TRY(build_spin(s, 0, nup, st));
+  ED_TRY(build_spin(s, 1, ndw, st));
+  s->dim = s->sp[0].dim * s->sp[1].dim;
+  int nm = 1 << mp.norb;
+  ED_TRY(dalloc(s, &s->W, nm * nm));
+  ED_TRY(dalloc(s, &s->W32, nm * nm));
+  k_wtable<<<(nm * nm + 63) / 64, 64, 0, st>>>(mp, s->W, s->W32);
+  ED_LAUNCHED(1);
+  bool sym = true;
+  for (int a = 0; a < mp.ns; ++a)
+    if (mp.eps[0][a] != mp.eps[1][a] || mp.V[0][a] != mp.V[1][a]) sym = false;
+  s->spin_symmetric = sym;
+  ED_TRY_CUDA(cudaStreamSynchronize(st));
+  return ED_OK;
+}
+
+static void free_spin(SpinTables &t) {
+  cudaFree(t.map);
+  cudaFree(t.imask);
+  cudaFree(t.ediag);
+  cudaFree(t.ediag32);
+  cudaFree(t.rowptr);
+  cudaFree(t.col);
+  cudaFree(t.val);
+  cudaFree(t.val32);
+  t = SpinTables();
+}
+
+static void sector_destroy(ed_sector s) {
+  if (!s) return;
+  for (int a = 0; a < 2; ++a)
+    for (int b = 0; b < 2; ++b) sector_destroy(s->nb[a][b]);
+  free_spin(s->sp[0]);
+  free_spin(s->sp[1]);
+  cudaFree(s->W);
+  cudaFree(s->W32);
+  delete s;
+}
+
+extern "C" ed_status ed_sector_build(const ed_model *model, int32_t nup, int32_t ndw,
+                                     void *stream, ed_sector *out) {
+  if (!out) return ED_ERR_ARG;
+  *out = nullptr;
+  ed_status st = ED_OK;
+  ModelParams mp = ed_model_params(model, &st);
+  if (st != ED_OK) return st;
+  if (nup < 0 || ndw < 0 || nup > mp.ns || ndw > mp.ns) return ED_ERR_ARG;
+  ed_sector s = new ed_sector_s();
+  s->e_imp.assign(model->e_imp, model->e_imp + 2 * model->norb);
+  size_t nb = (size_t)2 * model->norb * model->nbath;
+  if (nb) {
+    s->e_bath.assign(model->e_bath, model->e_bath + nb);
+    s->v_bath.assign(model->v_bath, model->v_bath + nb);
+  }
+  st = ed_build_sector_impl(mp, model->U, model->Ust, model->Jh, nup, ndw,
+                            (cudaStream_t)stream, s);
+  if (st != ED_OK) {
+    sector_destroy(s);
+    return st;
+  }
+  *out = s;
+  return ED_OK;
+}
+
+// Neighbour sector for the Green's function chains (cached in `s`).
+ed_status ed_neighbor_sector(ed_sector s, int spin, int create, cudaStream_t st, ed_sector *out) {
+  int slot = create > 0 ? 1 : 0;
+  if (s->nb[spin][slot]) {
+    *out = s->nb[spin][slot];
+    return ED_OK;
+  }
+  int nup = s->nup + (spin == 0 ? create : 0);
+  int ndw = s->ndw + (spin == 1 ? create : 0);
+  if (nup < 0 || ndw < 0 || nup > s->mp.ns || ndw > s->mp.ns) {
+    *out = nullptr;
+    return ED_OK;
+  }
+  ed_sector n = new ed_sector_s();
+  n->e_imp = s->e_imp;
+  n->e_bath = s->e_bath;
+  n->v_bath = s->v_bath;
+  ed_status r = ed_build_sector_impl(s->mp, s->U, s->Ust, s->Jh, nup, ndw, st, n);
+  if (r != ED_OK) {
+    sector_destroy(n);
+    return r;
+  }
+  s->nb[spin][slot] = n;
+  *out = n;
+  return ED_OK;
+}
+
+extern "C" ed_status ed_sector_get_info(ed_sector s, ed_sector_info *out) {
+  if (!s || !out) return ED_ERR_ARG;
+  out->ns = s->mp.ns;
+  out->norb = s->mp.norb;
+  out->nbath = s->mp.nbath;
+  out->nup = s->nup;
+  out->ndw = s->ndw;
+  out->dim_up = s->sp[0].dim;
+  out->dim_dw = s->sp[1].dim;
+  out->dim = s->dim;
+  out->nnz_up = s->sp[0].nnz;
+  out->nnz_dw = s->sp[1].nnz;
+  out->device_bytes = s->device_bytes;
+  return ED_OK;
+}
+
+extern "C" ed_status ed_sector_copy_tables(ed_sector s, int32_t spin, uint32_t *host_map,
+                                           int32_t *host_rowptr, int32_t *host_col,
+                                           double *host_val, double *host_ediag,
+                                           uint8_t *host_imask) {
+  if (!s || spin < 0 || spin > 1) return ED_ERR_ARG;
+  const SpinTables &t = s->sp[spin];
+  if (host_map) ED_TRY_CUDA(cudaMemcpy(host_map, t.map, t.dim * 4, cudaMemcpyDeviceToHost));
+  if (host_rowptr)
+    ED_TRY_CUDA(cudaMemcpy(host_rowptr, t.rowptr, (t.dim + 1) * 4, cudaMemcpyDeviceToHost));
+  if (host_col) ED_TRY_CUDA(cudaMemcpy(host_col, t.col, t.nnz * 4, cudaMemcpyDeviceToHost));
+  if (host_val) ED_TRY_CUDA(cudaMemcpy(host_val, t.val, t.nnz * 8, cudaMemcpyDeviceToHost));
+  if (host_ediag)
+    ED_TRY_CUDA(cudaMemcpy(host_ediag, t.ediag, t.dim * 8, cudaMemcpyDeviceToHost));
+  if (host_imask) ED_TRY_CUDA(cudaMemcpy(host_imask, t.imask, t.dim, cudaMemcpyDeviceToHost));
+  return ED_OK;
+}
+
+extern "C" ed_status ed_sector_copy_w(ed_sector s, double *host_w) {
+  if (!s || !host_w) return ED_ERR_ARG;
+  int nm = 1 << s->mp.norb;
+  ED_TRY_CUDA(cudaMemcpy(host_w, s->W, nm * nm * 8, cudaMemcpyDeviceToHost));
+  return ED_OK;
+}
+
+extern "C" ed_status ed_sector_free(ed_sector s) {
+  if (!s) return ED_ERR_ARG;
+  sector_destroy(s);
+  return ED_OK;
+}

@@ -1,0 +1,124 @@
+"""a4-a6 on the GPU: Lanczos ground state (FP64, FP32, FP32 + FP64 polish)
+against the oracle.
+
+Tolerances (relative to |E0|): FP64 <= 1e-10; raw FP32 <= 1e-6; FP32 after
+the FP64 polish <= 1e-10.  Degenerate and tiny sectors are checked against
+dense diagonalisation."""
+import json
+import os
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import fock
+from workloads import make_model, workload_ns8, workload_ns14, workload_ns16
+
+pytestmark = pytest.mark.gpu
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _gold(name):
+    with open(os.path.join(GOLD, name)) as f:
+        return json.load(f)
+
+
+def test_ns8_all_precisions(ed):
+    g = _gold("oracle_ns8.json")
+    wl = workload_ns8()
+    s = ed.Sector(wl.model, 4, 4)
+    ex = g["e0_dense"]
+    r64 = ed.lanczos_ground(s, "fp64")
+    assert abs(r64["e0"] - ex) <= 1e-10 * abs(ex)
+    assert r64["stop_reason"] == 0 and r64["iterations"] > 10
+    r32 = ed.lanczos_ground(s, "fp32")
+    assert abs(r32["e0"] - ex) <= 1e-6 * abs(ex)
+    rp = ed.lanczos_ground(s, "fp32_polish")
+    assert abs(rp["e0"] - ex) <= 1e-10 * abs(ex)
+    assert rp["residual"] < 1e-6 and rp["polish_iterations"] >= 2
+    s.free()
+
+
+def test_ns8_vector_matches_oracle(ed):
+    g = _gold("oracle_ns8.json")
+    s = ed.Sector(workload_ns8().model, 4, 4)
+    psi = torch.empty(s.dim, dtype=torch.float64, device="cuda")
+    r = ed.lanczos_ground(s, "fp64", psi=psi)
+    p = psi.cpu().numpy()
+    p *= np.sign(p[np.argmax(np.abs(p))])
+    idx = np.array(g["psi_index"])
+    assert np.abs(p[idx] - np.array(g["psi_value"])).max() < 1e-9
+    assert abs(np.linalg.norm(p) - 1) < 1e-12
+    assert r["residual"] < 1e-9
+    s.free()
+
+
+def test_ns14_fp64_and_polish(ed):
+    g = _gold("oracle_ns14.json")
+    wl = workload_ns14(0)
+    s = ed.Sector(wl.model, 7, 7)
+    e = g["e0"]
+    r64 = ed.lanczos_ground(s, "fp64")
+    assert abs(r64["e0"] - e) <= 1e-10 * abs(e)
+    rp = ed.lanczos_ground(s, "fp32_polish")
+    assert abs(rp["e0_raw"] - e) <= 1e-6 * abs(e)
+    assert abs(rp["e0"] - e) <= 1e-10 * abs(e)
+    psi = torch.empty(s.dim, dtype=torch.float64, device="cuda")
+    r = ed.lanczos_ground(s, "fp64", psi=psi)
+    p = psi.cpu().numpy()
+    p *= np.sign(p[np.argmax(np.abs(p))])
+    idx = np.array(g["psi_index"])
+    assert np.abs(p[idx] - np.array(g["psi_value"])).max() < 1e-8
+    s.free()
+
+
+def test_deterministic_and_twin(ed):
+    m = make_model(2, 3, U=2.5, Jh=0.4, seed=17)
+    a = ed.Sector(m, 3, 5)
+    b = ed.Sector(m, 5, 3)
+    r1 = ed.lanczos_ground(a, "fp32")
+    r2 = ed.lanczos_ground(a, "fp32")
+    assert r1["e0"] == r2["e0"] and r1["iterations"] == r2["iterations"]
+    rt = ed.lanczos_ground(b, "fp64")
+    r3 = ed.lanczos_ground(a, "fp64")
+    assert abs(rt["e0"] - r3["e0"]) <= 1e-11 * abs(r3["e0"])     # twin sectors
+    a.free()
+    b.free()
+
+
+CASES = [
+    (make_model(1, 0, U=1.3, e_d=-0.4), 1, 1),       # D = 1
+    (make_model(1, 0, U=1.3, e_d=-0.4), 1, 0),       # D = 1
+    (make_model(1, 2, U=2.0, seed=3), 0, 2),         # empty up spin: D = 3
+    (make_model(1, 3, U=2.0, seed=4), 4, 2),         # full up spin
+    (make_model(2, 1, U=2.0, Jh=0.3, seed=5), 2, 2), # D = 36
+    (make_model(3, 1, U=2.2, Jh=0.4, seed=6), 3, 3), # Norb=3, D = 400
+    (make_model(1, 7, U=0.0, e_d=0.0, e_bath=np.linspace(-1, 1, 7)[None], v_bath=np.full((1, 7), 0.5)), 4, 4),
+]
+
+
+@pytest.mark.parametrize("ci", range(len(CASES)))
+def test_small_and_degenerate_sectors(ed, ci):
+    m, nup, ndw = CASES[ci]
+    ref = fock.Sector(m, nup, ndw)
+    ex = np.linalg.eigvalsh(ref.hamiltonian().toarray())[0]
+    s = ed.Sector(m, nup, ndw)
+    r = ed.lanczos_ground(s, "fp64", allow_maxit=True)
+    assert abs(r["e0"] - ex) <= 1e-10 * max(1, abs(ex))
+    rp = ed.lanczos_ground(s, "fp32_polish", allow_maxit=True)
+    assert abs(rp["e0"] - ex) <= 1e-9 * max(1, abs(ex))
+    s.free()
+
+
+def test_ns16_fp32_polish_against_fp64_gpu(ed):
+    """Ns=16 (D = 165,636,900): FP32 + polish against the FP64 GPU path, with
+    the FP64 residual bound |E - lambda| <= ||r|| checked on both."""
+    wl = workload_ns16(0)
+    s = ed.Sector(wl.model, 8, 8)
+    r64 = ed.lanczos_ground(s, "fp64", want_vector=True)
+    rp = ed.lanczos_ground(s, "fp32_polish")
+    e = r64["e0"]
+    assert abs(rp["e0_raw"] - e) <= 1e-6 * abs(e)
+    assert abs(rp["e0"] - e) <= 1e-10 * abs(e)
+    assert r64["residual"] < 1e-6 and rp["residual"] < 1e-4
+    s.free()

@@ -1,0 +1,140 @@
+"""a3 on the GPU: w = H v through ed_matvec against the oracle's factorised
+product, element by element, FP64 and FP32, on sizes that span several CTAs,
+ragged last CTAs, the flattened and the row-loop paths, the shared-memory and
+the global-memory staging; plus sampled outputs at the full workload sizes.
+
+Tolerances: FP64 |dw| <= 1e-13 * (sum of |terms| bound) ; FP32 relative to the
+same bound <= 2e-6 (FP32 row sums of at most ~30 terms)."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import fock
+from workloads import (make_model, workload_ns8, workload_ns14, workload_ns16, workload_ns18,
+                       ImpurityModel)
+
+pytestmark = pytest.mark.gpu
+
+
+def _bound(ref_sector, v):
+    """Elementwise bound sum_k |H_ik| |v_k| (scale of the rounding error)."""
+    s = ref_sector
+    V = np.abs(v).reshape(s.dim_dw, s.dim_up)
+    B = np.abs(s.diagonal()) * V + (abs(s.H_up) @ V.T).T + abs(s.H_dw) @ V
+    return B.reshape(-1)
+
+
+SMALL = [
+    (workload_ns8().model, 4, 4),                              # D_up=70 < CTA: flattened
+    (make_model(2, 4, U=3.0, Jh=0.5, seed=6), 5, 4),           # Ns=10, D=252*210
+    (make_model(1, 11, U=2.5, e_d=-1.2, seed=7), 6, 5),        # Ns=12, D_up=924 row loop
+    (make_model(1, 16, U=2.0, e_d=-1.0, seed=8), 8, 1),        # Ns=17: D_up=24310, FP64 row
+                                                               # beyond shared memory
+    (make_model(3, 2, U=2.0, Jh=0.3, seed=9), 0, 9),           # empty up string, full down
+]
+
+
+@pytest.mark.parametrize("ci", range(len(SMALL)))
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_matvec_elementwise(ed, ci, prec):
+    m, nup, ndw = SMALL[ci]
+    ref = fock.Sector(m, nup, ndw)
+    s = ed.Sector(m, nup, ndw)
+    rng = np.random.default_rng(100 + ci)
+    v = rng.uniform(-1, 1, ref.dim)
+    want = ref.matvec(v)
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    vt = torch.tensor(v, dtype=dt, device="cuda")
+    wt = torch.full_like(vt, float("nan"))
+    ed.matvec(s, vt, wt, prec)
+    torch.cuda.synchronize()
+    got = wt.double().cpu().numpy()
+    if prec == "fp32":
+        # the FP32 path sees the input rounded to FP32 and FP32 matrix elements
+        v_used, tol = vt.double().cpu().numpy(), 4e-6
+    else:
+        v_used, tol = v, 1e-13
+    want = ref.matvec(v_used)
+    bnd = _bound(ref, v_used)
+    assert np.all(np.isfinite(got))
+    assert np.all(np.abs(got - want) <= tol * bnd)
+    s.free()
+
+
+def test_matvec_hermitian(ed):
+    m = make_model(2, 4, U=3.0, Jh=0.5, seed=6)
+    s = ed.Sector(m, 5, 5)
+    rng = np.random.default_rng(3)
+    x = torch.tensor(rng.normal(size=s.dim), device="cuda")
+    y = torch.tensor(rng.normal(size=s.dim), device="cuda")
+    hx, hy = torch.empty_like(x), torch.empty_like(y)
+    ed.matvec(s, x, hx)
+    ed.matvec(s, y, hy)
+    a, b = float(torch.dot(x, hy)), float(torch.dot(hx, y))
+    assert abs(a - b) <= 1e-12 * max(1, abs(a))
+
+
+def _sampled_reference(ref, v_host_fn, rows, cols):
+    """Oracle product at sampled (r, c) computed entry by entry from the
+    oracle's per-spin tables (Eq. Hbuild): needs only rows k of v."""
+    out = []
+    for r, c in zip(rows, cols):
+        d = ref.E_up[c] + ref.E_dw[r] + ref.W[ref.m_up[c], ref.m_dw[r]]
+        acc = d * v_host_fn(r, c)
+        hu = ref.H_up
+        for k in range(hu.indptr[c], hu.indptr[c + 1]):
+            acc += hu.data[k] * v_host_fn(r, hu.indices[k])
+        hd = ref.H_dw
+        for k in range(hd.indptr[r], hd.indptr[r + 1]):
+            acc += hd.data[k] * v_host_fn(hd.indices[k], c)
+        out.append(acc)
+    return np.array(out)
+
+
+def _lite_sector(model, nup, ndw):
+    """Oracle per-spin pieces only (no explicit sector matrix)."""
+    class S:
+        pass
+    S.map_up = fock.build_sector_map(model.ns, nup)
+    S.map_dw = S.map_up if ndw == nup else fock.build_sector_map(model.ns, ndw)
+    S.H_up = fock.spin_hopping_matrix(model, 0, nup, S.map_up)
+    S.H_dw = fock.spin_hopping_matrix(model, 1, ndw, S.map_dw)
+    S.E_up, S.m_up = fock.spin_diagonal(model, 0, nup, S.map_up)
+    S.E_dw, S.m_dw = fock.spin_diagonal(model, 1, ndw, S.map_dw)
+    S.W = fock.interaction_table(model)
+    return S
+
+
+@pytest.mark.parametrize("maker", [workload_ns14, workload_ns16, workload_ns18])
+def test_matvec_full_size_sampled(ed, maker):
+    """Full-size product in the launch configuration of the benchmark (FP32,
+    the input is a closed-form function of the index so the oracle can
+    evaluate any entry), checked on sampled outputs."""
+    wl = maker(0)
+    m = wl.model
+    s = ed.Sector(m, wl.nup, wl.ndw)
+    dup, ddw = s.dim_up, s.dim_dw
+    n = s.dim
+    # v[i] = sin(0.37 i) + cos(0.011 i) computed in FP64 then rounded to FP32
+    v = torch.empty(n, device="cuda", dtype=torch.float32)
+    step = 1 << 27
+    for o in range(0, n, step):
+        idx = torch.arange(o, min(n, o + step), device="cuda", dtype=torch.float64)
+        v[o:o + len(idx)] = (torch.sin(0.37 * idx) + torch.cos(0.011 * idx)).float()
+    del idx
+    w = torch.empty_like(v)
+    ed.matvec(s, v, w, "fp32")
+    torch.cuda.synchronize()
+    ref = _lite_sector(m, wl.nup, wl.ndw)
+
+    def vf(r, c):
+        i = int(r) * int(dup) + int(c)
+        return float(np.float32(np.sin(0.37 * i) + np.cos(0.011 * i)))
+    rng = np.random.default_rng(5)
+    rows = np.concatenate([[0, ddw - 1, ddw // 2], rng.integers(0, ddw, 40)])
+    cols = np.concatenate([[0, dup - 1, dup // 3], rng.integers(0, dup, 40)])
+    want = _sampled_reference(ref, vf, rows, cols)
+    flat = torch.tensor(rows.astype(np.int64) * dup + cols.astype(np.int64), device="cuda")
+    got = w[flat].double().cpu().numpy()
+    assert np.abs(got - want).max() <= 2e-5 * max(1.0, np.abs(want).max())
+    s.free()
