@@ -214,24 +214,10 @@ def run_ours(args):
     t_max = _max_over_ranks(dist, t_s)
     clk = clocks.stop()
 
-    # dominant kernel alone: the FP32 product on the full sector
-    s = E.Sector(m, wl.nup, wl.ndw, stream=stream)
-    v = torch.randn(D, dtype=torch.float32, device=dev)
-    w = torch.empty_like(v)
-    for _ in range(3):
-        E.matvec(s, v, w, "fp32", stream=stream)
-    reps = 20
-    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    durs = []
-    for _ in range(reps):
-        a.record(stream)
-        E.matvec(s, v, w, "fp32", stream=stream)
-        b.record(stream)
-        b.synchronize()
-        durs.append(a.elapsed_time(b))
-    mv_ms = statistics.median(durs)
-    del v, w
-    s.free()
+    # dominant kernel alone: the FP32 block-major product (the one inside
+    # the Lanczos steps) on the full sector
+    mv = time_products(E, wl, stream, dev, reps=20)
+    mv_ms = mv["blocked_fp32_ms"]
     hbm, src = _peaks()
     alg = 8.0 * D
     achieved = alg / (mv_ms / 1e3) / 1e9
@@ -295,12 +281,61 @@ def run_ours(args):
         "e0": last["e0"], "e0_raw": last["e0_raw"], "residual": last["residual"],
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm,
                      "unit": "GB/s", "frac": round(achieved / hbm, 4), "traffic": None,
-                     "kernel": "k_hv<float, HV_PLAIN> (ed_matvec)", "peak_source": src,
+                     "kernel": "k_hv<float, HV_PLAIN> block-major (ed_matvec_blocked)",
+                     "peak_source": src, "products_ms": mv,
                      "kernel_ms": round(mv_ms, 4), "algorithmic_bytes": int(alg)},
         "e2e": e2e, "gpu_launches": int(launches), "clocks": clk,
         "cpu_baseline": cpu, "serving": serving,
     }
     print(json.dumps(line))
+
+
+def time_products(E, wl, stream, dev, reps=20, which=("blocked_fp32", "sector_fp32")):
+    """Median CUDA-event time of single H.v launches on the full sector."""
+    import torch
+    m = wl.model
+    s = E.Sector(m, wl.nup, wl.ndw, stream=stream)
+    D = s.dim
+    out = {}
+    for name in which:
+        lay, prec = name.split("_")
+        dt = torch.float32 if prec == "fp32" else torch.float64
+        n = s.blocked_dim if lay == "blocked" else D    # block-major vectors are padded
+        v = torch.randn(n, dtype=dt, device=dev)
+        w = torch.empty_like(v)
+        f = E.matvec_blocked if lay == "blocked" else E.matvec
+        for _ in range(3):
+            f(s, v, w, prec, stream=stream)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        durs = []
+        for _ in range(reps):
+            a.record(stream)
+            f(s, v, w, prec, stream=stream)
+            b.record(stream)
+            b.synchronize()
+            durs.append(a.elapsed_time(b))
+        out[name + "_ms"] = round(statistics.median(durs), 4)
+        del v, w
+    s.free()
+    return out
+
+
+def run_matvec_only(args):
+    """Product kernels alone (used for kernel profiling)."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2105_06806_gb300 as E
+    torch.cuda.set_device(0)
+    wl = _workload(args.workload)
+    which = tuple(args.matvec_only.split(","))
+    r = time_products(E, wl, torch.cuda.current_stream(), torch.device("cuda", 0),
+                      reps=args.steps, which=which)
+    hbm, src = _peaks()
+    for k, v in list(r.items()):
+        elem = 8 if "fp64" in k else 4
+        r[k.replace("_ms", "_gbs")] = round(2 * elem * wl.dim / (v / 1e3) / 1e9, 1)
+    print(json.dumps({"workload": wl.name, "dim": wl.dim, "peak_gbs": hbm, **r}))
 
 
 def cpu_baseline(wl, budget_s):
@@ -433,7 +468,12 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--serving", type=int, default=0, help="requests of the serving stream")
     ap.add_argument("--serving-max-ns", type=int, default=12)
+    ap.add_argument("--matvec-only", default="",
+                    help="comma list of {blocked,sector}_{fp32,fp64}: time products only")
     args = ap.parse_args()
+    if args.matvec_only:
+        run_matvec_only(args)
+        return
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = max(args.warmup, 0)
     if args.impl == "reference":

@@ -98,6 +98,8 @@ typedef struct {
   int64_t dim_up, dim_dw, dim;     /* D_up, D_dw, D = D_up * D_dw           */
   int64_t nnz_up, nnz_dw;          /* stored entries of H_up and H_dw        */
   int64_t device_bytes;            /* device memory held by the handle       */
+  int64_t blocked_stride;          /* row length of block-major vectors      */
+  int64_t blocked_dim;             /* D_dw * blocked_stride                  */
 } ed_sector_info;
 
 /* Sector set-up (Sec. 6.3 build_sector, Sec. 2.4 / Eq. Hbuild): enumerates
@@ -126,10 +128,41 @@ ed_status ed_sector_free(ed_sector s);
 /* w = H v on the sector (Sec. 6.7 without MPI; Eq. Hbuild):
  *   w[r,c] = (E_up[c] + E_dw[r] + W[m_up[c]][m_dw[r]]) v[r,c]
  *          + sum_k H_up[c,k] v[r,k] + sum_k H_dw[r,k] v[k,c].
- * d_v, d_w: device arrays of D elements, double for ED_FP64, float for
- * ED_FP32 / ED_FP32_POLISH; must not overlap.  Asynchronous on `stream`. */
-ed_status ed_matvec(ed_sector s, ed_precision prec, const void *d_v, void *d_w,
+ * d_v, d_w: device arrays of n = D elements, double for ED_FP64, float for
+ * ED_FP32 / ED_FP32_POLISH; must not overlap.  ED_ERR_ARG when n != D.
+ * Asynchronous on `stream`. */
+ed_status ed_matvec(ed_sector s, ed_precision prec, const void *d_v, void *d_w, int64_t n,
                     void *stream);
+
+/* Block-major layout.  With a diagonal H^loc, a normal bath and the
+ * density-density interaction, each orbital group (impurity level alpha and
+ * its bath levels) conserves its number of spin-s electrons (the per-orbital
+ * quantum numbers of Sec. 2.2; H_sigma is a Kronecker sum over orbitals,
+ * Sec. 2.4).  In block-major order the states of each spin are grouped by
+ * the tuple of group occupations (tuples in lexicographic order; inside a
+ * block the mixed-radix index of the group strings, group 0 slowest, each
+ * group string in colex order), so H maps every (dw block, up block)
+ * rectangle of the [D_dw][D_up] array to itself.  The library's Lanczos
+ * vectors live in this order; inputs and outputs of the calls below that
+ * say "sector order" are converted at the boundary.
+ *
+ * Block-major vectors are [D_dw][blocked_stride] arrays: every up block is
+ * padded to a multiple of 4 columns (16-byte aligned row segments) and the
+ * padding entries are zero (ed_sector_info gives blocked_stride and
+ * blocked_dim = D_dw * blocked_stride).
+ *
+ * ed_matvec_blocked: w = H v with v, w block-major vectors of
+ * n = blocked_dim elements (same element types as ed_matvec); the padding
+ * of w is not written.  ed_sector_permute: converts between a sector-order
+ * D-vector and a block-major vector (to_blocked = 1: sector -> blocked,
+ * padding written as zero); n_in / n_out are the element counts of the two
+ * arrays; d_in and d_out must not overlap.  Both return ED_ERR_ARG when a
+ * count does not match the layout, and are asynchronous. */
+ed_status ed_matvec_blocked(ed_sector s, ed_precision prec, const void *d_v, void *d_w,
+                            int64_t n, void *stream);
+ed_status ed_sector_permute(ed_sector s, ed_precision prec, int32_t to_blocked,
+                            const void *d_in, int64_t n_in, void *d_out, int64_t n_out,
+                            void *stream);
 
 typedef struct {
   ed_precision precision;

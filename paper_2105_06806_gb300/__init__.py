@@ -26,7 +26,7 @@ PRECISIONS = {"fp64": FP64, "fp32": FP32, "fp32_polish": FP32_POLISH}
 
 EXPORTED = [
     "ed_sector_build", "ed_sector_get_info", "ed_sector_copy_tables", "ed_sector_copy_w",
-    "ed_sector_free", "ed_matvec", "ed_lanczos_ground", "ed_gf_lanczos", "ed_solve",
+    "ed_sector_free", "ed_matvec", "ed_matvec_blocked", "ed_sector_permute", "ed_lanczos_ground", "ed_gf_lanczos", "ed_solve",
     "ed_server_create", "ed_submit", "ed_poll", "ed_wait", "ed_server_destroy",
     "ed_server_inject_alloc_failure", "ed_status_string", "ed_last_error", "ed_kernel_launches",
 ]
@@ -62,7 +62,8 @@ class ed_sector_info(C.Structure):
     _fields_ = [("ns", C.c_int32), ("norb", C.c_int32), ("nbath", C.c_int32),
                 ("nup", C.c_int32), ("ndw", C.c_int32), ("dim_up", C.c_int64),
                 ("dim_dw", C.c_int64), ("dim", C.c_int64), ("nnz_up", C.c_int64),
-                ("nnz_dw", C.c_int64), ("device_bytes", C.c_int64)]
+                ("nnz_dw", C.c_int64), ("device_bytes", C.c_int64),
+                ("blocked_stride", C.c_int64), ("blocked_dim", C.c_int64)]
 
 
 class ed_lanczos_opts(C.Structure):
@@ -137,7 +138,9 @@ def lib():
             "ed_sector_copy_tables": [vp, i32, vp, vp, vp, vp, vp, vp],
             "ed_sector_copy_w": [vp, vp],
             "ed_sector_free": [vp],
-            "ed_matvec": [vp, C.c_int, vp, vp, vp],
+            "ed_matvec": [vp, C.c_int, vp, vp, i64, vp],
+            "ed_matvec_blocked": [vp, C.c_int, vp, vp, i64, vp],
+            "ed_sector_permute": [vp, C.c_int, i32, vp, i64, vp, i64, vp],
             "ed_lanczos_ground": [vp, C.POINTER(ed_lanczos_opts), C.POINTER(ed_lanczos_result),
                                   vp, vp],
             "ed_gf_lanczos": [vp, C.c_int, vp, C.c_double, i32, i32, i32, C.c_double, i32, vp,
@@ -228,6 +231,8 @@ class Sector:
         self.nup, self.ndw = int(nup), int(ndw)
         self.dim = self.info["dim"]
         self.dim_up, self.dim_dw = self.info["dim_up"], self.info["dim_dw"]
+        self.blocked_dim = self.info["blocked_dim"]
+        self.blocked_stride = self.info["blocked_stride"]
 
     def free(self):
         if self.h:
@@ -272,9 +277,28 @@ def _prec(p):
 
 def matvec(sector: Sector, v, w, precision="fp64", stream=None):
     """w = H v for device tensors (float64 for fp64, float32 otherwise)."""
+    if v.numel() != w.numel():
+        raise ValueError("v and w differ in length")
     _check(lib().ed_matvec(sector.h, _prec(precision), C.c_void_p(v.data_ptr()),
-                           C.c_void_p(w.data_ptr()), C.c_void_p(_stream_ptr(stream))),
-           "ed_matvec")
+                           C.c_void_p(w.data_ptr()), int(v.numel()),
+                           C.c_void_p(_stream_ptr(stream))), "ed_matvec")
+
+
+def matvec_blocked(sector: Sector, v, w, precision="fp64", stream=None):
+    """w = H v with both vectors in block-major order."""
+    if v.numel() != w.numel():
+        raise ValueError("v and w differ in length")
+    _check(lib().ed_matvec_blocked(sector.h, _prec(precision), C.c_void_p(v.data_ptr()),
+                                   C.c_void_p(w.data_ptr()), int(v.numel()),
+                                   C.c_void_p(_stream_ptr(stream))), "ed_matvec_blocked")
+
+
+def permute(sector: Sector, x, out, to_blocked=True, precision="fp64", stream=None):
+    """Converts a sector vector between sector order and block-major order."""
+    _check(lib().ed_sector_permute(sector.h, _prec(precision), int(bool(to_blocked)),
+                                   C.c_void_p(x.data_ptr()), int(x.numel()),
+                                   C.c_void_p(out.data_ptr()), int(out.numel()),
+                                   C.c_void_p(_stream_ptr(stream))), "ed_sector_permute")
 
 
 def lanczos_ground(sector: Sector, precision="fp64", max_iter=0, tol=0.0, seed=0x5EED,

@@ -17,9 +17,11 @@ __device__ __forceinline__ double gf_warp_sum(double x) {
 }
 
 struct ApplyArgs {
-  // target sector (dst) strings, source sector dims
-  const uint32_t *dst_map;   // map of the spin that changes, in the target sector
-  int64_t dst_dup, dst_dim;
+  // target sector (dst) in block-major order, source psi in sector order
+  const uint32_t *dst_map;     // strings of the spin that changes, block-major order
+  const int32_t *dst_pother;   // sector index of the unchanged spin's block-major index
+  const int32_t *dst_padinv;   // padded column -> block-major up column (-1: padding)
+  int64_t dst_stride, dst_dim; // padded row length, D_dw * stride
   int64_t src_dup;
   int level;                 // level a of the operator (impurity orbital)
   int create;                // +1: c^+, -1: c
@@ -30,7 +32,9 @@ struct ApplyArgs {
 // phi[r',c'] = sign * psi[r,c] where the changed spin string of the target
 // element, with level a removed (c^+) or added (c), is the source string;
 // sign = (-1)^(occupied modes before (a,s)) in the order 1up..Ns up,
-// 1dw..Ns dw (Sec. 2.3).  Partial sums of phi^2 per CTA.
+// 1dw..Ns dw (Sec. 2.3).  phi is written in the target's block-major order,
+// psi is read in sector order (sector index = colex rank of the strings).
+// Partial sums of phi^2 per CTA.
 template <typename Ti, typename To>
 __global__ void __launch_bounds__(GF_THREADS) k_apply_op(ApplyArgs a, const Ti *psi, To *phi,
                                                          double *part) {
@@ -40,17 +44,18 @@ __global__ void __launch_bounds__(GF_THREADS) k_apply_op(ApplyArgs a, const Ti *
   const uint32_t bit = 1u << a.level;
   const uint32_t below = bit - 1u;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < a.dst_dim; i += stride) {
-    const int64_t r2 = i / a.dst_dup, c2 = i - r2 * a.dst_dup;
-    const uint32_t I2 = a.dst_map[a.spin == 0 ? c2 : r2];
-    const bool occ = (I2 & bit) != 0u;
+    const int64_t r2 = i / a.dst_stride;
+    const int32_t c2 = a.dst_padinv[i - r2 * a.dst_stride];
     To out = To(0);
-    if (occ == (a.create > 0)) {
+    const uint32_t I2 = c2 < 0 ? 0u : a.dst_map[a.spin == 0 ? (int64_t)c2 : r2];
+    const bool occ = (I2 & bit) != 0u;
+    if (c2 >= 0 && occ == (a.create > 0)) {
       const uint32_t I = I2 ^ bit;
       const int64_t src_idx = ed_rank(I);
       int parity = __popc(I & below);
       if (a.spin == 1) parity += a.nup_src;
-      const int64_t r = a.spin == 0 ? r2 : src_idx;
-      const int64_t c = a.spin == 0 ? src_idx : c2;
+      const int64_t r = a.spin == 0 ? (int64_t)a.dst_pother[r2] : src_idx;
+      const int64_t c = a.spin == 0 ? src_idx : (int64_t)a.dst_pother[c2];
       const Ti x = psi[r * a.src_dup + c];
       out = (To)((parity & 1) ? -x : x);
     }
@@ -105,8 +110,8 @@ static ed_status one_chain(ed_sector s, const Ti *psi, int orb, int spin, int cr
   ed_sector nb = nullptr;
   ED_TRY(ed_neighbor_sector(s, spin, create, cs, &nb));
   if (!nb || nb->dim == 0) return ED_OK;
-  const int64_t n = nb->dim;
-  const int64_t np1 = ed_hv_num_parts(nb, (int)sizeof(To));
+  const int64_t n = nb->bdim;  // padded block-major vectors
+  const int64_t np1 = ed_hv_num_parts(nb, 1, (int)sizeof(To));
   const int64_t g2 = ed_reduce_grid(n);
   const int64_t nparts = std::max<int64_t>(np1, 3 * g2);
   const size_t vb = al256(n * sizeof(To));
@@ -130,9 +135,10 @@ static ed_status one_chain(ed_sector s, const Ti *psi, int orb, int spin, int cr
   double *part2 = (double *)p;
 
   ApplyArgs a;
-  const SpinTables &t = nb->sp[spin];
-  a.dst_map = t.map;
-  a.dst_dup = nb->sp[0].dim;
+  a.dst_map = nb->bk[spin].map;
+  a.dst_pother = nb->bi[1 - spin].pidx;
+  a.dst_padinv = nb->padinv;
+  a.dst_stride = nb->bstride;
   a.dst_dim = n;
   a.src_dup = s->sp[0].dim;
   a.level = orb;  // impurity orbital alpha is level alpha
@@ -140,8 +146,10 @@ static ed_status one_chain(ed_sector s, const Ti *psi, int orb, int spin, int cr
   a.spin = spin;
   a.nup_src = s->nup;
   ed_status rs = ED_OK;
+  // padding entries must stay zero in every chain vector
+  if (cudaMemsetAsync(mem, 0, 3 * vb, cs) != cudaSuccess) rs = ED_ERR_CUDA;
   int32_t *flag = nullptr;
-  if (cudaMallocHost((void **)&flag, 64) != cudaSuccess) rs = ED_ERR_OOM;
+  if (rs == ED_OK && cudaMallocHost((void **)&flag, 64) != cudaSuccess) rs = ED_ERR_OOM;
   if (rs == ED_OK) {
     k_apply_op<Ti, To><<<(unsigned)g2, GF_THREADS, 0, cs>>>(a, psi, bufs[0], part);
     ed_count_launches(1);

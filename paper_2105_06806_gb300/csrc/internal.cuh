@@ -67,13 +67,70 @@ struct SpinTables {
   float *val32 = nullptr;      // [nnz]
 };
 
+// Block-major order of one spin basis.  With a diagonal H^loc, a normal bath
+// and the density-density interaction, the number of spin-s electrons in
+// each orbital group {impurity level alpha} + {bath levels of alpha} is
+// conserved (the per-orbital quantum numbers of Sec. 2.2; H_sigma then splits
+// into a Kronecker sum over orbitals, Sec. 2.4).  The states of a total-N
+// sector are therefore grouped into blocks by the tuple (n_0..n_{Norb-1}),
+// blocks in lexicographic order of the tuple; inside a block the index is
+// the mixed-radix number of the group strings (group 0 slowest), each group
+// string ranked in colex order.  H_sigma maps every block to itself.
+struct BlockView {
+  int norb, nbath, g, nblocks;
+  const int64_t *offset;    // [nblocks + 1]
+  const int8_t *keys;       // [nblocks][norb]
+  const int32_t *code2blk;  // [(g+1)^norb] -> block index or -1
+};
+
+struct BlockInfo {
+  int nblocks = 0;
+  std::vector<int64_t> offset;   // host copy, nblocks + 1
+  std::vector<int8_t> keys;      // host copy
+  int64_t *d_offset = nullptr;
+  int8_t *d_keys = nullptr;
+  int32_t *d_code2blk = nullptr;
+  int32_t *pidx = nullptr;       // [dim] blocked index -> sector (paper) index
+  int32_t *inv = nullptr;        // [dim] sector (paper) index -> blocked index
+};
+
+struct HvItem {
+  int32_t r0, nr, c0, nc;  // rows [r0, r0+nr) x columns [c0, c0+nc), one block pair
+  int32_t c0p;             // first column in the vector layout (padded in block-major)
+  int32_t deg;             // ELL width of the up block (block-major), 0: use CSR
+  int32_t ell_off;         // first ELL entry of the up block
+  int32_t ncp;             // ELL row length (padded block width)
+};
+
+struct ItemList {
+  HvItem *d_items = nullptr;
+  int64_t nitems = 0;
+  size_t smem = 0;
+};
+
 struct ed_sector_s {
   ModelParams mp;
   std::vector<double> e_imp, e_bath, v_bath;  // host copies (for neighbours)
   double U = 0, Ust = 0, Jh = 0;
   int nup = 0, ndw = 0;
   int64_t dim = 0;
-  SpinTables sp[2];
+  SpinTables sp[2];   // sector (paper) order: ascending strings
+  SpinTables bk[2];   // block-major order (Lanczos vectors live in this order)
+  BlockInfo bi[2];
+  ItemList items[2][2];  // [layout 0 sector / 1 blocked][0 FP32 / 1 FP64]
+  // Block-major vectors pad every up block to a multiple of 4 columns (16-byte
+  // aligned row segments): row length bstride, length bdim = D_dw * bstride.
+  int64_t bstride = 0, bdim = 0;
+  std::vector<int64_t> up_off_pad;   // padded column offset of every up block
+  int32_t *colpos = nullptr;         // [D_up] block-major column -> padded column
+  int32_t *padinv = nullptr;         // [bstride] padded column -> column or -1
+  // H_up of every up block as a column-major ELL table (entry e of local
+  // column c at ell_off + e * ncp + c; padded with zero values): coalesced
+  // reads when consecutive threads own consecutive columns.
+  std::vector<int32_t> ell_deg, ell_off;  // host, per up block
+  int32_t *ell_col = nullptr;             // local column of the entry
+  float *ell_v32 = nullptr;
+  double *ell_v64 = nullptr;
   double *W = nullptr;     // [2^norb][2^norb]
   float *W32 = nullptr;
   ed_sector nb[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};  // [spin][0:c,1:c+]
@@ -124,6 +181,47 @@ __device__ __forceinline__ int64_t ed_rank(uint32_t I) {
   return r;
 }
 
+__device__ __forceinline__ uint32_t ed_group_string(uint32_t I, int a, int norb, int nbath) {
+  return ((I >> a) & 1u) | (((I >> (norb + a * nbath)) & ((1u << nbath) - 1u)) << 1);
+}
+__device__ __forceinline__ uint32_t ed_group_expand(uint32_t gs, int a, int norb, int nbath) {
+  return ((gs & 1u) << a) | ((gs >> 1) << (norb + a * nbath));
+}
+
+__device__ __forceinline__ int64_t ed_blocked_rank(const BlockView &bv, uint32_t I) {
+  int code = 0;
+  uint32_t gs[ED_MAX_NORB];
+  int n[ED_MAX_NORB];
+  for (int a = 0; a < bv.norb; ++a) {
+    gs[a] = ed_group_string(I, a, bv.norb, bv.nbath);
+    n[a] = __popc(gs[a]);
+    code = code * (bv.g + 1) + n[a];
+  }
+  const int b = bv.code2blk[code];
+  int64_t idx = 0;
+  for (int a = 0; a < bv.norb; ++a) idx = idx * (int64_t)c_binom[bv.g][n[a]] + ed_rank(gs[a]);
+  return bv.offset[b] + idx;
+}
+
+__device__ __forceinline__ uint32_t ed_blocked_unrank(const BlockView &bv, int64_t i) {
+  int lo = 0, hi = bv.nblocks - 1;
+  while (lo < hi) {  // last block with offset <= i
+    int mid = (lo + hi + 1) >> 1;
+    if (bv.offset[mid] <= i) lo = mid;
+    else hi = mid - 1;
+  }
+  int64_t w = i - bv.offset[lo];
+  uint32_t I = 0;
+  for (int a = bv.norb - 1; a >= 0; --a) {
+    const int na = bv.keys[lo * bv.norb + a];
+    const int64_t cnt = (int64_t)c_binom[bv.g][na];
+    const int64_t r = w % cnt;
+    w /= cnt;
+    I |= ed_group_expand(ed_unrank((uint64_t)r, bv.g, na), a, bv.norb, bv.nbath);
+  }
+  return I;
+}
+
 // ----------------------------------------------------------------- kernels/launchers
 
 // sector.cu
@@ -139,9 +237,18 @@ struct HvTables {
   const T *val_up, *val_dw, *e_up, *e_dw, *W;
   const uint8_t *m_up, *m_dw;
   int nmask;  // 2^norb
+  const HvItem *items;
+  int64_t nitems;
+  size_t smem;
+  int64_t stride;   // row length of the vector layout
+  const int32_t *ell_col;
+  const T *ell_val;
 };
+// layout 0: sector (paper) order; 1: block-major order
 template <typename T>
-HvTables<T> ed_hv_tables(ed_sector s);
+HvTables<T> ed_hv_tables(ed_sector s, int layout);
+ed_status ed_build_items(ed_sector s, int layout, int elem);
+ed_status ed_build_ell(ed_sector s, cudaStream_t st);
 
 // Lanczos device state (lanczos.cu).
 struct LanczosState {
@@ -167,7 +274,7 @@ ed_status ed_launch_hv(ed_sector s, const HvTables<T> &tb, int mode, const T *v,
                        T *const *bufs, T *psi, LanczosState *state, double *part,
                        int64_t *nparts, cudaStream_t st);
 
-int64_t ed_hv_num_parts(ed_sector s, int elem_size);
+int64_t ed_hv_num_parts(ed_sector s, int layout, int elem_size);
 template <typename T>
 ed_status ed_hv_prepare();
 

@@ -305,15 +305,28 @@ __device__ __forceinline__ uint64_t splitmix64_at(uint64_t seed, uint64_t i) {
   return z ^ (z >> 31);
 }
 
+// The vector lives in padded block-major order: element (r', pc) holds the
+// start value of sector index pidx_dw[r'] * D_up + pidx_up[padinv[pc]], and
+// padding columns (padinv < 0) hold zero.
 template <typename T>
 __global__ void __launch_bounds__(AXPY_THREADS) k_start_vector(T *v, int64_t n, uint64_t seed,
+                                                               const int32_t *pidx_up,
+                                                               const int32_t *pidx_dw,
+                                                               const int32_t *padinv,
+                                                               int64_t stride, int64_t dup,
                                                                double *part) {
   __shared__ double red[AXPY_THREADS / 32];
   T acc = T(0);
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += stride) {
-    double u = (double)(splitmix64_at(seed, (uint64_t)i) >> 11) * (1.0 / 9007199254740992.0);
-    T x = (T)(u - 0.5);
+  const int64_t step = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += step) {
+    const int64_t r = i / stride, pc = i - r * stride;
+    const int32_t cb = padinv[pc];
+    T x = T(0);
+    if (cb >= 0) {
+      const uint64_t p = (uint64_t)pidx_dw[r] * (uint64_t)dup + (uint64_t)pidx_up[cb];
+      double u = (double)(splitmix64_at(seed, p) >> 11) * (1.0 / 9007199254740992.0);
+      x = (T)(u - 0.5);
+    }
     v[i] = x;
     acc = fmaT<T>(x, x, acc);
   }
@@ -422,54 +435,123 @@ __global__ void k_scale_copy(const Ti *x, To *y, int64_t n, const double *part, 
     y[i] = (To)((double)x[i] * f);
 }
 
-// Residual pieces of psi (normalised) and w = H psi: <psi,w>, ||w||^2,
-// ||psi||^2 per CTA (FP64).
-__global__ void __launch_bounds__(AXPY_THREADS) k_resid_parts(const double *psi, const double *w,
-                                                              int64_t n, double *part,
-                                                              int64_t nparts) {
-  __shared__ double red[3][AXPY_THREADS / 32];
-  double a = 0, b = 0, c = 0;
+// Layout changes between sector order ([D_dw][D_up], ascending strings) and
+// padded block-major order ([D_dw][bstride]):
+//   blocked[r'][pc] = sector[pidx_dw[r']][pidx_up[padinv[pc]]]  (0 at padding)
+//   sector[r][c]    = blocked[inv_dw[r]][colpos[inv_up[c]]]
+// One grid row per output row; the gathers stay inside one input row.
+template <typename Ti, typename To>
+__global__ void k_to_blocked(const Ti *in, To *out, const int32_t *pidx_dw,
+                             const int32_t *pidx_up, const int32_t *padinv, int64_t dup,
+                             int64_t stride, int64_t ddw) {
+  for (int64_t r = blockIdx.y; r < ddw; r += gridDim.y) {
+    const Ti *src = in + (int64_t)pidx_dw[r] * dup;
+    To *dst = out + r * stride;
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < stride;
+         c += (int64_t)gridDim.x * blockDim.x) {
+      const int32_t cb = padinv[c];
+      dst[c] = cb < 0 ? To(0) : (To)src[pidx_up[cb]];
+    }
+  }
+}
+
+template <typename Ti, typename To>
+__global__ void k_from_blocked(const Ti *in, To *out, const int32_t *inv_dw, const int32_t *inv_up,
+                               const int32_t *colpos, int64_t dup, int64_t stride, int64_t ddw) {
+  for (int64_t r = blockIdx.y; r < ddw; r += gridDim.y) {
+    const Ti *src = in + (int64_t)inv_dw[r] * stride;
+    To *dst = out + r * dup;
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < dup;
+         c += (int64_t)gridDim.x * blockDim.x)
+      dst[c] = (To)src[colpos[inv_up[c]]];
+  }
+}
+
+template <typename Ti, typename To>
+static ed_status permute_layout(ed_sector s, const Ti *in, To *out, bool to_blocked,
+                                cudaStream_t cs) {
+  const int64_t dup = s->sp[0].dim, ddw = s->sp[1].dim, stride = s->bstride;
+  const int64_t cols = to_blocked ? stride : dup;
+  dim3 grid((unsigned)std::max<int64_t>(1, std::min<int64_t>((cols + 255) / 256, 64)),
+            (unsigned)std::max<int64_t>(1, std::min<int64_t>(ddw, 65535)));
+  if (to_blocked)
+    k_to_blocked<Ti, To><<<grid, 256, 0, cs>>>(in, out, s->bi[1].pidx, s->bi[0].pidx, s->padinv,
+                                               dup, stride, ddw);
+  else
+    k_from_blocked<Ti, To><<<grid, 256, 0, cs>>>(in, out, s->bi[1].inv, s->bi[0].inv, s->colpos,
+                                                 dup, stride, ddw);
+  ED_LAUNCHED(1);
+  return ED_OK;
+}
+
+// Residual of psi: pass 1 forms <psi,w> and ||psi||^2 per CTA (w = H psi),
+// k_rq_final the Rayleigh quotient e; pass 2 forms ||w - e psi||^2 directly
+// (no cancellation), k_resid_final the normalised residual.
+__global__ void __launch_bounds__(AXPY_THREADS) k_rq_parts(const double *psi, const double *w,
+                                                           int64_t n, double *part,
+                                                           int64_t nparts) {
+  __shared__ double red[2][AXPY_THREADS / 32];
+  double a = 0, c = 0;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += stride) {
     a = fma(psi[i], w[i], a);
-    b = fma(w[i], w[i], b);
     c = fma(psi[i], psi[i], c);
   }
   a = warp_sum(a);
-  b = warp_sum(b);
   c = warp_sum(c);
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   if (lane == 0) {
     red[0][wid] = a;
-    red[1][wid] = b;
-    red[2][wid] = c;
+    red[1][wid] = c;
   }
   __syncthreads();
   if (threadIdx.x == 0) {
-    double ta = 0, tb = 0, tc = 0;
+    double ta = 0, tc = 0;
     for (int k = 0; k < AXPY_THREADS / 32; ++k) {
       ta += red[0][k];
-      tb += red[1][k];
-      tc += red[2][k];
+      tc += red[1][k];
     }
     part[blockIdx.x] = ta;
-    part[nparts + blockIdx.x] = tb;
-    part[2 * nparts + blockIdx.x] = tc;
+    part[nparts + blockIdx.x] = tc;
+  }
+}
+
+__global__ void k_rq_final(const double *part, int64_t nparts, double *out) {
+  __shared__ double red[SCALAR_THREADS / 32];
+  double a = cta_sum_parts(part, nparts, red);
+  double c = cta_sum_parts(part + nparts, nparts, red);
+  if (threadIdx.x == 0) {
+    out[0] = a / c;
+    out[2] = c;
+  }
+}
+
+__global__ void __launch_bounds__(AXPY_THREADS) k_resid_parts(const double *psi, const double *w,
+                                                              int64_t n, const double *out,
+                                                              double *part) {
+  __shared__ double red[AXPY_THREADS / 32];
+  const double e = out[0];
+  double b = 0;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += stride) {
+    const double r = fma(-e, psi[i], w[i]);
+    b = fma(r, r, b);
+  }
+  b = warp_sum(b);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) red[wid] = b;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0;
+    for (int k = 0; k < AXPY_THREADS / 32; ++k) t += red[k];
+    part[blockIdx.x] = t;
   }
 }
 
 __global__ void k_resid_final(const double *part, int64_t nparts, double *out) {
   __shared__ double red[SCALAR_THREADS / 32];
-  double a = cta_sum_parts(part, nparts, red);
-  double b = cta_sum_parts(part + nparts, nparts, red);
-  double c = cta_sum_parts(part + 2 * nparts, nparts, red);
-  if (threadIdx.x == 0) {
-    double e = a / c;
-    // ||w - e psi||^2 = ||w||^2 - 2 e <psi,w> + e^2 ||psi||^2
-    double r2 = b - 2.0 * e * a + e * e * c;
-    out[0] = e;
-    out[1] = sqrt(fmax(r2, 0.0) / c);
-  }
+  double b = cta_sum_parts(part, nparts, red);
+  if (threadIdx.x == 0) out[1] = sqrt(b / out[2]);
 }
 
 // ----------------------------------------------------------------- host driver
@@ -630,8 +712,9 @@ template <typename T>
 static ed_status lanczos_solve(ed_sector s, int maxit, double tol, uint64_t seed, const T *start,
                                bool want_vector, T *psi_out, LanczosState *h_state,
                                cudaStream_t cs, int *matvecs) {
-  const int64_t n = s->dim;
-  const int64_t np1 = ed_hv_num_parts(s, (int)sizeof(T));
+  const int64_t n = s->bdim;  // padded block-major vectors
+  ED_TRY(ed_build_items(s, 1, (int)sizeof(T)));
+  const int64_t np1 = ed_hv_num_parts(s, 1, (int)sizeof(T));
   const int64_t g2 = reduce_grid(n);
   const int64_t nparts = std::max<int64_t>(np1, 3 * g2);
   size_t vb = align256(n * sizeof(T));
@@ -655,6 +738,8 @@ static ed_status lanczos_solve(ed_sector s, int maxit, double tol, uint64_t seed
   double *part = (double *)p;
   p += align256(nparts * sizeof(double));
   double *part2 = (double *)p;
+  // padding entries must stay zero in every vector
+  ED_TRY_CUDA(cudaMemsetAsync(ws.mem, 0, (3 + (want_vector ? 1 : 0)) * vb, cs));
 
   PinnedFlag flag;
   const int check_every = n > (1 << 22) ? 1 : 4;
@@ -663,7 +748,9 @@ static ed_status lanczos_solve(ed_sector s, int maxit, double tol, uint64_t seed
       ED_TRY_CUDA(cudaMemcpyAsync(bufs[0], start, n * sizeof(T), cudaMemcpyDeviceToDevice, cs));
       k_norm2<T><<<(unsigned)g2, AXPY_THREADS, 0, cs>>>(bufs[0], n, part);
     } else {
-      k_start_vector<T><<<(unsigned)g2, AXPY_THREADS, 0, cs>>>(bufs[0], n, seed, part);
+      k_start_vector<T><<<(unsigned)g2, AXPY_THREADS, 0, cs>>>(
+          bufs[0], n, seed, s->bi[0].pidx, s->bi[1].pidx, s->padinv, s->bstride, s->sp[0].dim,
+          part);
     }
     ED_LAUNCHED(1);
     k_state_init<<<1, SCALAR_THREADS, 0, cs>>>(st, part, g2, maxit, tol, check_every);
@@ -671,7 +758,7 @@ static ed_status lanczos_solve(ed_sector s, int maxit, double tol, uint64_t seed
     return ED_OK;
   };
   ED_TRY(init());
-  HvTables<T> tb = ed_hv_tables<T>(s);
+  HvTables<T> tb = ed_hv_tables<T>(s, 1);
   int launched = 0;
   ED_TRY(run_steps<T>(s, tb, bufs, st, part, part2, n, maxit, cs, &launched, flag.p));
   ED_TRY_CUDA(cudaMemcpyAsync(h_state, st, sizeof(LanczosState), cudaMemcpyDeviceToHost, cs));
@@ -697,27 +784,31 @@ static ed_status lanczos_solve(ed_sector s, int maxit, double tol, uint64_t seed
   return ED_OK;
 }
 
-// FP64 residual of a normalised FP64 vector: returns (Rayleigh quotient,
-// ||H psi - e psi||).
+// FP64 residual of a normalised FP64 vector in block-major order: returns
+// (Rayleigh quotient, ||H psi - e psi||).
 static ed_status fp64_residual(ed_sector s, const double *psi, double *e, double *r,
                                cudaStream_t cs) {
-  const int64_t n = s->dim;
+  ED_TRY(ed_build_items(s, 1, 8));
+  const int64_t n = s->bdim;
   const int64_t g2 = reduce_grid(n);
   size_t bytes = align256(n * sizeof(double)) + align256(3 * g2 * sizeof(double)) + 256;
   Workspace ws;
   ED_TRY(ws.alloc(bytes, cs));
   double *w = (double *)ws.mem;
   double *part = (double *)((char *)ws.mem + align256(n * sizeof(double)));
-  double *out = part + 3 * g2 + 8;
-  out = (double *)(((uintptr_t)out + 255) & ~(uintptr_t)255);
-  if ((char *)out + 16 > (char *)ws.mem + bytes) out = part + 3 * g2;
-  ED_TRY(ed_launch_hv<double>(s, ed_hv_tables<double>(s), HV_PLAIN, psi, w, nullptr, nullptr,
-                              nullptr, nullptr, nullptr, cs));
-  k_resid_parts<<<(unsigned)g2, AXPY_THREADS, 0, cs>>>(psi, w, n, part, g2);
+  double *out = (double *)((char *)part + align256(3 * g2 * sizeof(double)));  // 3 doubles
+  ED_TRY_CUDA(cudaMemsetAsync(w, 0, n * sizeof(double), cs));  // padding of H psi
+  ED_TRY(ed_launch_hv<double>(s, ed_hv_tables<double>(s, 1), HV_PLAIN, psi, w, nullptr,
+                              nullptr, nullptr, nullptr, nullptr, cs));
+  k_rq_parts<<<(unsigned)g2, AXPY_THREADS, 0, cs>>>(psi, w, n, part, g2);
+  ED_LAUNCHED(1);
+  k_rq_final<<<1, SCALAR_THREADS, 0, cs>>>(part, g2, out);
+  ED_LAUNCHED(1);
+  k_resid_parts<<<(unsigned)g2, AXPY_THREADS, 0, cs>>>(psi, w, n, out, part);
   ED_LAUNCHED(1);
   k_resid_final<<<1, SCALAR_THREADS, 0, cs>>>(part, g2, out);
   ED_LAUNCHED(1);
-  double h[2];
+  double h[3];
   ED_TRY_CUDA(cudaMemcpyAsync(h, out, sizeof(h), cudaMemcpyDeviceToHost, cs));
   ED_TRY_CUDA(cudaStreamSynchronize(cs));
   *e = h[0];
@@ -741,83 +832,71 @@ ed_status ed_lanczos_ground_impl(ed_sector s, const ed_lanczos_opts *o, ed_lancz
   const ed_precision prec = o->precision;
   if (prec != ED_FP64 && prec != ED_FP32 && prec != ED_FP32_POLISH) return ED_ERR_ARG;
   double tol = o->tol > 0 ? o->tol : (prec == ED_FP64 ? 1e-12 : 1e-6);
-  const bool want = o->want_vector != 0 || prec == ED_FP32_POLISH;
-  const int64_t n = s->dim;
-  if (n <= 0) return ED_ERR_ARG;
+  const bool want = o->want_vector != 0 || prec == ED_FP32_POLISH || d_psi != nullptr;
+  if (s->dim <= 0) return ED_ERR_ARG;
+  const int64_t n = s->bdim;  // padded block-major vectors
   std::vector<char> hbuf(sizeof(LanczosState));
   LanczosState *h = (LanczosState *)hbuf.data();
   int mv = 0;
+  const int64_t g2 = reduce_grid(n);
   if (prec == ED_FP64) {
-    Workspace psi;
-    double *dpsi = (double *)d_psi;
-    if (want && !dpsi) {
-      ED_TRY(psi.alloc(n * sizeof(double), cs));
-      dpsi = (double *)psi.mem;
-    }
-    ED_TRY(lanczos_solve<double>(s, maxit, tol, o->seed, nullptr, want, dpsi, h, cs, &mv));
+    Workspace psi;   // block-major ground state
+    if (want) ED_TRY(psi.alloc(n * sizeof(double), cs));
+    double *bpsi = (double *)psi.mem;
+    ED_TRY(lanczos_solve<double>(s, maxit, tol, o->seed, nullptr, want, bpsi, h, cs, &mv));
     fill_result(*h, res);
     if (want) {
       double e, r;
-      ED_TRY(fp64_residual(s, dpsi, &e, &r, cs));
+      ED_TRY(fp64_residual(s, bpsi, &e, &r, cs));
       res->residual = r;
       ++mv;
+      if (d_psi) ED_TRY((permute_layout<double, double>(s, bpsi, (double *)d_psi, false, cs)));
     }
   } else {
     Workspace psi32;
-    float *fpsi = (prec == ED_FP32) ? (float *)d_psi : nullptr;
-    if (want && !fpsi) {
-      ED_TRY(psi32.alloc(n * sizeof(float), cs));
-      fpsi = (float *)psi32.mem;
-    }
+    if (want) ED_TRY(psi32.alloc(n * sizeof(float), cs));
+    float *fpsi = (float *)psi32.mem;
     ED_TRY(lanczos_solve<float>(s, maxit, tol, o->seed, nullptr, want, fpsi, h, cs, &mv));
     fill_result(*h, res);
-    if (prec == ED_FP32_POLISH) {
-      // FP64 Lanczos restarted from the FP32 ground state (a6): a few FP64
-      // steps, their Ritz pair, and the FP64 residual of the result.
-      const int steps = o->polish_steps > 0 ? o->polish_steps : 4;
-      Workspace start, psi64;
+    if (want) {
+      // FP64 copy of the FP32 ground state (normalised in FP64)
+      Workspace start, prt;
       ED_TRY(start.alloc(n * sizeof(double), cs));
-      double *dst = (double *)d_psi;
-      if (!dst) {
-        ED_TRY(psi64.alloc(n * sizeof(double), cs));
-        dst = (double *)psi64.mem;
-      }
-      const int64_t g2 = reduce_grid(n);
-      Workspace prt;
       ED_TRY(prt.alloc(g2 * sizeof(double), cs));
       k_norm2<float><<<(unsigned)g2, AXPY_THREADS, 0, cs>>>(fpsi, n, (double *)prt.mem);
       ED_LAUNCHED(1);
       k_scale_copy<float, double><<<(unsigned)g2, AXPY_THREADS, 0, cs>>>(
           fpsi, (double *)start.mem, n, (double *)prt.mem, g2);
       ED_LAUNCHED(1);
-      std::vector<char> h2buf(sizeof(LanczosState));
-      LanczosState *h2 = (LanczosState *)h2buf.data();
-      ED_TRY(lanczos_solve<double>(s, steps, 1e-300, 0, (const double *)start.mem, true, dst, h2,
-                                   cs, &mv));
-      res->e0 = h2->theta;
-      res->polish_iterations = h2->j;
-      double e, r;
-      ED_TRY(fp64_residual(s, dst, &e, &r, cs));
-      res->residual = r;
-      ++mv;
-    } else if (want) {
-      // report the FP64 residual of the FP32 vector
-      Workspace tmp;
-      ED_TRY(tmp.alloc(n * sizeof(double), cs));
-      const int64_t g2 = reduce_grid(n);
-      Workspace prt;
-      ED_TRY(prt.alloc(g2 * sizeof(double), cs));
-      k_norm2<float><<<(unsigned)g2, AXPY_THREADS, 0, cs>>>(fpsi, n, (double *)prt.mem);
-      ED_LAUNCHED(1);
-      k_scale_copy<float, double><<<(unsigned)g2, AXPY_THREADS, 0, cs>>>(
-          fpsi, (double *)tmp.mem, n, (double *)prt.mem, g2);
-      ED_LAUNCHED(1);
-      double e, r;
-      ED_TRY(fp64_residual(s, (const double *)tmp.mem, &e, &r, cs));
-      res->residual = r;
-      ++mv;
+      if (prec == ED_FP32_POLISH) {
+        // FP64 Lanczos restarted from the FP32 ground state (a6): a few FP64
+        // steps, their Ritz pair, and the FP64 residual of the result.
+        const int steps = o->polish_steps > 0 ? o->polish_steps : 4;
+        Workspace psi64;
+        ED_TRY(psi64.alloc(n * sizeof(double), cs));
+        std::vector<char> h2buf(sizeof(LanczosState));
+        LanczosState *h2 = (LanczosState *)h2buf.data();
+        ED_TRY(lanczos_solve<double>(s, steps, 1e-300, 0, (const double *)start.mem, true,
+                                     (double *)psi64.mem, h2, cs, &mv));
+        res->e0 = h2->theta;
+        res->polish_iterations = h2->j;
+        double e, r;
+        ED_TRY(fp64_residual(s, (const double *)psi64.mem, &e, &r, cs));
+        res->residual = r;
+        ++mv;
+        if (d_psi)
+          ED_TRY((permute_layout<double, double>(s, (const double *)psi64.mem, (double *)d_psi,
+                                                 false, cs)));
+      } else {
+        double e, r;
+        ED_TRY(fp64_residual(s, (const double *)start.mem, &e, &r, cs));
+        res->residual = r;
+        ++mv;
+        if (d_psi) ED_TRY((permute_layout<float, float>(s, fpsi, (float *)d_psi, false, cs)));
+      }
     }
   }
+  ED_TRY_CUDA(cudaStreamSynchronize(cs));
   res->matvecs = mv;
   if (res->stop_reason == 2) return ED_ERR_NOT_CONVERGED;
   return ED_OK;
@@ -833,9 +912,10 @@ ed_status ed_lanczos_chain(ed_sector s, T *const *bufs, LanczosState *st, double
                            int32_t *h_flag) {
   k_state_init<<<1, SCALAR_THREADS, 0, cs>>>(st, part, nparts_start, nsteps, 0.0, 1);
   ED_LAUNCHED(1);
-  HvTables<T> tb = ed_hv_tables<T>(s);
+  ED_TRY(ed_build_items(s, 1, (int)sizeof(T)));
+  HvTables<T> tb = ed_hv_tables<T>(s, 1);
   int launched = 0;
-  return run_steps<T>(s, tb, bufs, st, part, part2, s->dim, nsteps, cs, &launched, h_flag);
+  return run_steps<T>(s, tb, bufs, st, part, part2, s->bdim, nsteps, cs, &launched, h_flag);
 }
 
 template ed_status ed_lanczos_chain<float>(ed_sector, float *const *, LanczosState *, double *,
@@ -849,4 +929,22 @@ extern "C" ed_status ed_lanczos_ground(ed_sector s, const ed_lanczos_opts *opts,
                                        ed_lanczos_result *res, void *d_psi, void *stream) {
   if (!s || !opts || !res) return ED_ERR_ARG;
   return ed_lanczos_ground_impl(s, opts, res, d_psi, (cudaStream_t)stream);
+}
+
+extern "C" ed_status ed_sector_permute(ed_sector s, ed_precision prec, int32_t to_blocked,
+                                       const void *d_in, int64_t n_in, void *d_out, int64_t n_out,
+                                       void *stream) {
+  if (!s || !d_in || !d_out || d_in == d_out) return ED_ERR_ARG;
+  if (n_in != (to_blocked ? s->dim : s->bdim) || n_out != (to_blocked ? s->bdim : s->dim)) {
+    ed_set_error_msg("vector length does not match the sector layout");
+    return ED_ERR_ARG;
+  }
+  cudaStream_t cs = (cudaStream_t)stream;
+  if (prec == ED_FP64)
+    return permute_layout<double, double>(s, (const double *)d_in, (double *)d_out,
+                                          to_blocked != 0, cs);
+  if (prec == ED_FP32 || prec == ED_FP32_POLISH)
+    return permute_layout<float, float>(s, (const float *)d_in, (float *)d_out, to_blocked != 0,
+                                        cs);
+  return ED_ERR_ARG;
 }

@@ -1,13 +1,23 @@
 // Sector product w = H v (Sec. 6.7 without MPI, Eq. Hbuild) with optional
 // Lanczos epilogues (Sec. 6.6).
 //
-// Layout: v is a row-major [D_dw][D_up] array (Eq. Vmatrix); row r is one
-// down configuration.  One CTA owns R consecutive rows; it stages them in
-// shared memory (coalesced loads), applies the diagonal and H_up along each
-// row from shared memory, and adds the H_dw part by reading the neighbour
-// rows k of r at the same columns (coalesced row segments, L2 resident for
-// small sectors).  No transpose is formed: the strided axis of Sec. 3.2 is
-// read directly by row segments.
+// Layout: v is a row-major [D_dw][stride] array (Eq. Vmatrix); row r is one
+// down configuration.  The product is cut into work items, rectangles of rows
+// x columns inside one (dw block, up block) pair of the block-major order, so
+// that H_up of a column never leaves the item's columns and H_dw of a row
+// never leaves the dw block (in sector order there is one block per spin).
+//
+// Per item a CTA stages its rows in shared memory, transposed so that the RT
+// rows a thread owns are contiguous: one 16-byte shared load then feeds the
+// same H_up entry to RT rows (a small SpMM along the up axis).  Each thread
+// owns a tile of 4 consecutive columns x RT rows.  In block-major order the
+// H_up table is an ELL copy per up block interleaved by tiles (the entries
+// of a tile's 4 columns are one 16-byte word), and every up block is padded
+// to a multiple of 4 columns, so both the table and the H_dw neighbour rows
+// are read with aligned, coalesced vector loads; the neighbour lists and
+// diagonal pieces of the item's rows sit in shared memory.  No transpose is
+// formed: the strided axis of Sec. 3.2 is read directly by row segments,
+// which stay in L2 while the block pair is processed.
 #include <algorithm>
 #include <mutex>
 
@@ -36,52 +46,102 @@ __device__ __forceinline__ float add_t<float>(float a, float b) { return __fadd_
 template <>
 __device__ __forceinline__ double add_t<double>(double a, double b) { return __dadd_rn(a, b); }
 
+// Register tile: 4 consecutive columns x RT rows; the RT rows of one column
+// form one 16-byte vector in shared memory.
 template <typename T>
-HvTables<T> ed_hv_tables(ed_sector s);
+struct Tile;
 template <>
-HvTables<double> ed_hv_tables<double>(ed_sector s) {
+struct Tile<float> {
+  static constexpr int CU = 4, RT = 4;
+  using V = float4;
+};
+template <>
+struct Tile<double> {
+  static constexpr int CU = 4, RT = 2;
+  using V = double2;
+};
+
+// four consecutive values of a 16-byte aligned row segment
+__device__ __forceinline__ void load4(const float *p, float *y) {
+  const float4 v = __ldg(reinterpret_cast<const float4 *>(p));
+  y[0] = v.x;
+  y[1] = v.y;
+  y[2] = v.z;
+  y[3] = v.w;
+}
+__device__ __forceinline__ void load4(const double *p, double *y) {
+  const double2 a = __ldg(reinterpret_cast<const double2 *>(p));
+  const double2 b = __ldg(reinterpret_cast<const double2 *>(p) + 1);
+  y[0] = a.x;
+  y[1] = a.y;
+  y[2] = b.x;
+  y[3] = b.y;
+}
+
+__device__ __forceinline__ void vec_get(const float4 &v, float *x) {
+  x[0] = v.x;
+  x[1] = v.y;
+  x[2] = v.z;
+  x[3] = v.w;
+}
+__device__ __forceinline__ void vec_get(const double2 &v, double *x) {
+  x[0] = v.x;
+  x[1] = v.y;
+}
+
+template <typename T>
+static void fill_tables(HvTables<T> &t, const SpinTables &u, const SpinTables &d, const T *vu,
+                        const T *vd, const T *eu, const T *e_d, const T *W, int norb) {
+  t.dup = u.dim;
+  t.ddw = d.dim;
+  t.rp_up = u.rowptr;
+  t.col_up = u.col;
+  t.val_up = vu;
+  t.e_up = eu;
+  t.m_up = u.imask;
+  t.rp_dw = d.rowptr;
+  t.col_dw = d.col;
+  t.val_dw = vd;
+  t.e_dw = e_d;
+  t.m_dw = d.imask;
+  t.W = W;
+  t.nmask = 1 << norb;
+}
+
+template <>
+HvTables<double> ed_hv_tables<double>(ed_sector s, int layout) {
   HvTables<double> t;
-  t.dup = s->sp[0].dim;
-  t.ddw = s->sp[1].dim;
-  t.rp_up = s->sp[0].rowptr;
-  t.col_up = s->sp[0].col;
-  t.val_up = s->sp[0].val;
-  t.e_up = s->sp[0].ediag;
-  t.m_up = s->sp[0].imask;
-  t.rp_dw = s->sp[1].rowptr;
-  t.col_dw = s->sp[1].col;
-  t.val_dw = s->sp[1].val;
-  t.e_dw = s->sp[1].ediag;
-  t.m_dw = s->sp[1].imask;
-  t.W = s->W;
-  t.nmask = 1 << s->mp.norb;
+  const SpinTables *T2 = layout == 0 ? s->sp : s->bk;
+  fill_tables<double>(t, T2[0], T2[1], T2[0].val, T2[1].val, T2[0].ediag, T2[1].ediag, s->W,
+                      s->mp.norb);
+  const ItemList &il = s->items[layout][1];
+  t.items = il.d_items;
+  t.nitems = il.nitems;
+  t.smem = il.smem;
+  t.stride = layout == 0 ? s->sp[0].dim : s->bstride;
+  t.ell_col = layout == 0 ? nullptr : s->ell_col;
+  t.ell_val = layout == 0 ? nullptr : s->ell_v64;
   return t;
 }
 template <>
-HvTables<float> ed_hv_tables<float>(ed_sector s) {
+HvTables<float> ed_hv_tables<float>(ed_sector s, int layout) {
   HvTables<float> t;
-  t.dup = s->sp[0].dim;
-  t.ddw = s->sp[1].dim;
-  t.rp_up = s->sp[0].rowptr;
-  t.col_up = s->sp[0].col;
-  t.val_up = s->sp[0].val32;
-  t.e_up = s->sp[0].ediag32;
-  t.m_up = s->sp[0].imask;
-  t.rp_dw = s->sp[1].rowptr;
-  t.col_dw = s->sp[1].col;
-  t.val_dw = s->sp[1].val32;
-  t.e_dw = s->sp[1].ediag32;
-  t.m_dw = s->sp[1].imask;
-  t.W = s->W32;
-  t.nmask = 1 << s->mp.norb;
+  const SpinTables *T2 = layout == 0 ? s->sp : s->bk;
+  fill_tables<float>(t, T2[0], T2[1], T2[0].val32, T2[1].val32, T2[0].ediag32, T2[1].ediag32,
+                     s->W32, s->mp.norb);
+  const ItemList &il = s->items[layout][0];
+  t.items = il.d_items;
+  t.nitems = il.nitems;
+  t.smem = il.smem;
+  t.stride = layout == 0 ? s->sp[0].dim : s->bstride;
+  t.ell_col = layout == 0 ? nullptr : s->ell_col;
+  t.ell_val = layout == 0 ? nullptr : s->ell_v32;
   return t;
 }
 
 template <typename T>
 struct HvLaunch {
   HvTables<T> tb;
-  int rows_per_cta;
-  int use_smem;
   const T *v;
   T *w;
   T *b0, *b1, *b2;
@@ -91,7 +151,177 @@ struct HvLaunch {
 };
 
 constexpr int HV_THREADS = 512;
-constexpr size_t HV_SMEM_MAX = 112 * 1024;
+constexpr size_t HV_SMEM_TWO = 96 * 1024;   // two CTAs per SM (with the static tables)
+constexpr size_t HV_SMEM_MAX = 190 * 1024;  // one CTA per SM (very wide blocks)
+constexpr int HV_MAXROWS = 64;              // rows of an item (G * RT <= 16 * 4)
+
+static int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
+
+// ELL copy of H_up per up block (block-major order), interleaved by tiles of
+// 4 columns: entry e of local column c = 4 t + u sits at
+// ell_off + (e * ntile + t) * 4 + u.  Past a column's degree the entry is
+// (the column itself, 0), which adds an exact zero.  One grid row per block.
+__global__ void k_fill_ell(const int32_t *rowptr, const int32_t *col, const double *val,
+                           const int64_t *blk_off, const int32_t *ell_off, const int32_t *ell_deg,
+                           const int64_t *pad_off, int32_t *ell_col, float *v32, double *v64) {
+  const int b = blockIdx.y;
+  const int64_t C0 = blk_off[b], nc = blk_off[b + 1] - C0;
+  const int64_t ncp = pad_off[b + 1] - pad_off[b];
+  const int64_t ntile = ncp / 4;
+  const int deg = ell_deg[b];
+  const int64_t base = ell_off[b];
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < ncp;
+       c += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t t = c >> 2, u = c & 3;
+    int32_t k0 = 0, n = 0;
+    if (c < nc) {
+      k0 = rowptr[C0 + c];
+      n = rowptr[C0 + c + 1] - k0;
+    }
+    for (int e = 0; e < deg; ++e) {
+      const int64_t o = base + ((int64_t)e * ntile + t) * 4 + u;
+      if (e < n) {
+        ell_col[o] = (int32_t)(col[k0 + e] - C0);
+        v64[o] = val[k0 + e];
+        v32[o] = (float)val[k0 + e];
+      } else {
+        ell_col[o] = c < nc ? (int32_t)c : 0;
+        v64[o] = 0.0;
+        v32[o] = 0.0f;
+      }
+    }
+  }
+}
+
+ed_status ed_build_ell(ed_sector s, cudaStream_t st) {
+  if (s->ell_col) return ED_OK;
+  const BlockInfo &b = s->bi[0];
+  const int nb = b.nblocks;
+  std::vector<int32_t> rp(s->bk[0].dim + 1);
+  ED_TRY_CUDA(cudaMemcpy(rp.data(), s->bk[0].rowptr, rp.size() * sizeof(int32_t),
+                         cudaMemcpyDeviceToHost));
+  s->ell_deg.assign(nb, 0);
+  s->ell_off.assign(nb + 1, 0);
+  for (int k = 0; k < nb; ++k) {
+    int d = 0;
+    for (int64_t c = b.offset[k]; c < b.offset[k + 1]; ++c) d = std::max(d, rp[c + 1] - rp[c]);
+    s->ell_deg[k] = d;
+    const int64_t ncp = s->up_off_pad[k + 1] - s->up_off_pad[k];
+    const int64_t next = (int64_t)s->ell_off[k] + (int64_t)d * ncp;
+    if (next >= (int64_t)INT32_MAX) return ED_ERR_UNSUPPORTED;
+    s->ell_off[k + 1] = (int32_t)next;
+  }
+  const int64_t total = std::max<int64_t>(1, s->ell_off[nb]);
+  int64_t *d_blk = nullptr, *d_pad = nullptr;
+  int32_t *d_off = nullptr, *d_deg = nullptr;
+  auto alloc = [&](void **p, size_t bytes) -> ed_status {
+    cudaError_t e = cudaMalloc(p, std::max<size_t>(bytes, 1));
+    if (e != cudaSuccess) {
+      ed_set_cuda_error(e, "cudaMalloc(ell)", __FILE__, __LINE__);
+      return ED_ERR_OOM;
+    }
+    return ED_OK;
+  };
+  ED_TRY(alloc((void **)&s->ell_col, total * sizeof(int32_t)));
+  ED_TRY(alloc((void **)&s->ell_v32, total * sizeof(float)));
+  ED_TRY(alloc((void **)&s->ell_v64, total * sizeof(double)));
+  s->device_bytes += total * 16;
+  ED_TRY(alloc((void **)&d_blk, (nb + 1) * sizeof(int64_t)));
+  ED_TRY(alloc((void **)&d_pad, (nb + 1) * sizeof(int64_t)));
+  ED_TRY(alloc((void **)&d_off, (nb + 1) * sizeof(int32_t)));
+  ED_TRY(alloc((void **)&d_deg, nb * sizeof(int32_t)));
+  ED_TRY_CUDA(cudaMemcpy(d_blk, b.offset.data(), (nb + 1) * sizeof(int64_t), cudaMemcpyHostToDevice));
+  ED_TRY_CUDA(cudaMemcpy(d_pad, s->up_off_pad.data(), (nb + 1) * sizeof(int64_t),
+                         cudaMemcpyHostToDevice));
+  ED_TRY_CUDA(cudaMemcpy(d_off, s->ell_off.data(), (nb + 1) * sizeof(int32_t), cudaMemcpyHostToDevice));
+  ED_TRY_CUDA(cudaMemcpy(d_deg, s->ell_deg.data(), nb * sizeof(int32_t), cudaMemcpyHostToDevice));
+  int64_t maxw = 1;
+  for (int k = 0; k < nb; ++k) maxw = std::max<int64_t>(maxw, s->up_off_pad[k + 1] - s->up_off_pad[k]);
+  dim3 grid((unsigned)std::min<int64_t>((maxw + 255) / 256, 1024), (unsigned)nb);
+  k_fill_ell<<<grid, 256, 0, st>>>(s->bk[0].rowptr, s->bk[0].col, s->bk[0].val, d_blk, d_off,
+                                   d_deg, d_pad, s->ell_col, s->ell_v32, s->ell_v64);
+  ED_LAUNCHED(1);
+  ED_TRY_CUDA(cudaStreamSynchronize(st));
+  cudaFree(d_blk);
+  cudaFree(d_pad);
+  cudaFree(d_off);
+  cudaFree(d_deg);
+  return ED_OK;
+}
+
+// Rows of an item and the shared-memory bytes of one row group: the CTA is
+// split into G groups of P threads (P = the item's columns rounded up to a
+// warp, at most the CTA); group q owns rows q*RT .. q*RT+RT-1.
+static void item_shape(int64_t nc, int elem, int64_t *rows, size_t *bytes_per_group) {
+  const int RT = elem == 4 ? Tile<float>::RT : Tile<double>::RT;
+  const int64_t ntile = (nc + 3) / 4;
+  const int64_t P = ntile >= HV_THREADS ? HV_THREADS : round_up(ntile, 32);
+  const int64_t G = HV_THREADS / P;
+  *rows = G * RT;
+  *bytes_per_group = (size_t)round_up(nc, 4) * RT * elem;
+}
+
+// Work items, ordered dw block by dw block, up block by up block, rows
+// ascending: while one block pair is processed, its |dw block| x |up block|
+// slice of v is the L2 working set of the H_dw reads.
+ed_status ed_build_items(ed_sector s, int layout, int elem) {
+  ItemList &il = s->items[layout][elem == 8 ? 1 : 0];
+  if (il.d_items) return ED_OK;
+  std::vector<int64_t> ob_up, ob_dw, op_up;
+  if (layout == 0) {
+    ob_up = {0, s->sp[0].dim};
+    op_up = ob_up;
+    ob_dw = {0, s->sp[1].dim};
+  } else {
+    ED_TRY(ed_build_ell(s, 0));
+    ob_up = s->bi[0].offset;
+    op_up = s->up_off_pad;
+    ob_dw = s->bi[1].offset;
+  }
+  const int RT = elem == 4 ? Tile<float>::RT : Tile<double>::RT;
+  std::vector<HvItem> items;
+  size_t smem = 0;
+  for (size_t bd = 0; bd + 1 < ob_dw.size(); ++bd) {
+    const int64_t R0 = ob_dw[bd], R1 = ob_dw[bd + 1];
+    if (R1 <= R0) continue;
+    for (size_t bu = 0; bu + 1 < ob_up.size(); ++bu) {
+      const int64_t C0 = ob_up[bu], C1 = ob_up[bu + 1];
+      const int64_t nc = C1 - C0;
+      if (nc <= 0) continue;
+      int64_t R;
+      size_t per_group;
+      item_shape(nc, elem, &R, &per_group);
+      // shared memory holds ceil(R/RT) row groups; shrink R until it fits
+      while (R > RT && (size_t)((R + RT - 1) / RT) * per_group > HV_SMEM_TWO) R -= RT;
+      R = std::min<int64_t>(R, R1 - R0);
+      const size_t need = (size_t)((R + RT - 1) / RT) * per_group;
+      if (need <= HV_SMEM_MAX) smem = std::max(smem, need);
+      const int32_t deg = layout == 0 ? 0 : s->ell_deg[bu];
+      const int32_t eoff = layout == 0 ? 0 : s->ell_off[bu];
+      const int32_t ncp = (int32_t)(op_up[bu + 1] - op_up[bu]);
+      for (int64_t r = R0; r < R1; r += R)
+        items.push_back(HvItem{(int32_t)r, (int32_t)std::min<int64_t>(R, R1 - r), (int32_t)C0,
+                               (int32_t)nc, (int32_t)op_up[bu], deg, eoff, ncp});
+    }
+  }
+  il.nitems = (int64_t)items.size();
+  il.smem = smem;
+  cudaError_t e = cudaMalloc((void **)&il.d_items, std::max<size_t>(items.size(), 1) * sizeof(HvItem));
+  if (e != cudaSuccess) {
+    ed_set_cuda_error(e, "cudaMalloc(items)", __FILE__, __LINE__);
+    il.d_items = nullptr;
+    return ED_ERR_OOM;
+  }
+  s->device_bytes += (int64_t)(items.size() * sizeof(HvItem));
+  if (!items.empty()) {
+    e = cudaMemcpy(il.d_items, items.data(), items.size() * sizeof(HvItem), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+      ed_set_cuda_error(e, "cudaMemcpy(items)", __FILE__, __LINE__);
+      return ED_ERR_CUDA;
+    }
+  }
+  return ED_OK;
+}
 
 template <typename T>
 __device__ __forceinline__ double block_sum(double x, double *red) {
@@ -106,28 +336,119 @@ __device__ __forceinline__ double block_sum(double x, double *red) {
   return s;
 }
 
-// One output element: diagonal + H_up (row from `row`) + H_dw (neighbour rows
-// of the global array `g`).  The summation order is fixed so that the two
-// Lanczos passes reproduce each other bit for bit.
-template <typename T>
-__device__ __forceinline__ T hv_element(const HvTables<T> &tb, const T *__restrict__ row,
-                                        const T *__restrict__ g, int64_t r, int64_t c) {
-  const T x = row[c];
-  T d = add_t<T>(add_t<T>(tb.e_up[c], tb.e_dw[r]), tb.W[(int)tb.m_up[c] * tb.nmask + tb.m_dw[r]]);
-  T acc = mul_t<T>(d, x);
-  const int32_t u0 = __ldg(tb.rp_up + c), u1 = __ldg(tb.rp_up + c + 1);
-  for (int32_t k = u0; k < u1; ++k) acc = fma_t<T>(__ldg(tb.val_up + k), row[__ldg(tb.col_up + k)], acc);
-  const int32_t d0 = __ldg(tb.rp_dw + r), d1 = __ldg(tb.rp_dw + r + 1);
-  for (int32_t k = d0; k < d1; ++k)
-    acc = fma_t<T>(__ldg(tb.val_dw + k), __ldg(g + (int64_t)__ldg(tb.col_dw + k) * tb.dup + c), acc);
-  return acc;
+// One tile: 4 consecutive columns cb..cb+3 x RT rows of the thread's row
+// group.  FULL: all RT rows exist and all 4 columns are inside the block
+// (no predication).  BLK: block-major layout (ELL table, aligned vectors).
+template <typename T, bool FULL, bool BLK>
+__device__ __forceinline__ void hv_tile(const HvTables<T> &tb, const HvItem &it, const T *g,
+                                        const T *smq, bool staged, int lr0, int nrt, int cb,
+                                        const int32_t *s_dn, const int32_t *s_dcol,
+                                        const T *s_dval, const int32_t *s_mdw, const T *s_edw,
+                                        T (&acc)[4][Tile<T>::RT]) {
+  constexpr int RT = Tile<T>::RT;
+  using VT = typename Tile<T>::V;
+  const int64_t stride = tb.stride;
+  const int r0 = it.r0, c0 = it.c0, nc = it.nc;
+  const int64_t cp0 = it.c0p;
+  auto rows_at = [&](int c, T *y) {
+    if (staged) {
+      vec_get(*reinterpret_cast<const VT *>(smq + (size_t)c * RT), y);
+    } else {
+#pragma unroll
+      for (int i = 0; i < RT; ++i)
+        y[i] = (FULL || i < nrt) ? g[(int64_t)(r0 + lr0 + i) * stride + cp0 + c] : T(0);
+    }
+  };
+  // diagonal
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int c = cb + u;
+#pragma unroll
+    for (int i = 0; i < RT; ++i) acc[u][i] = T(0);
+    if (FULL || c < nc) {
+      T x[RT];
+      rows_at(c, x);
+      const int64_t cg = (int64_t)c0 + c;
+      const T eu = tb.e_up[cg];
+      const int mu = (int)tb.m_up[cg] * tb.nmask;
+#pragma unroll
+      for (int i = 0; i < RT; ++i)
+        if (FULL || i < nrt)
+          acc[u][i] =
+              mul_t<T>(add_t<T>(add_t<T>(eu, s_edw[lr0 + i]), tb.W[mu + s_mdw[lr0 + i]]), x[i]);
+    }
+  }
+  // H_up
+  if (BLK) {
+    const int64_t ntile4 = (int64_t)it.ncp;  // entries of one ELL row (4 per tile)
+    const int4 *ec = reinterpret_cast<const int4 *>(tb.ell_col + it.ell_off + cb);
+    const T *ev = tb.ell_val + it.ell_off + cb;
+    for (int e = 0; e < it.deg; ++e) {
+      const int4 kc = __ldg(ec + (e * ntile4) / 4);
+      T h[4];
+      load4(ev + e * ntile4, h);
+      const int kk[4] = {kc.x, kc.y, kc.z, kc.w};
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        if (FULL || cb + u < nc) {
+          T y[RT];
+          rows_at(kk[u], y);
+#pragma unroll
+          for (int i = 0; i < RT; ++i) acc[u][i] = fma_t<T>(h[u], y[i], acc[u][i]);
+        }
+      }
+    }
+  } else {
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int c = cb + u;
+      if (FULL || c < nc) {
+        const int64_t cg = (int64_t)c0 + c;
+        const int32_t k0 = __ldg(tb.rp_up + cg), k1 = __ldg(tb.rp_up + cg + 1);
+        for (int32_t k = k0; k < k1; ++k) {
+          const int kc = __ldg(tb.col_up + k) - c0;
+          const T h = __ldg(tb.val_up + k);
+          T y[RT];
+          rows_at(kc, y);
+#pragma unroll
+          for (int i = 0; i < RT; ++i) acc[u][i] = fma_t<T>(h, y[i], acc[u][i]);
+        }
+      }
+    }
+  }
+  // H_dw: neighbour rows at the same 4 columns
+#pragma unroll
+  for (int i = 0; i < RT; ++i) {
+    if (!FULL && i >= nrt) continue;
+    const int n = s_dn[lr0 + i];
+    const int32_t *dc = s_dcol + (lr0 + i) * ED_MAX_NS;
+    const T *dv = s_dval + (lr0 + i) * ED_MAX_NS;
+    for (int t = 0; t < n; ++t) {
+      const T h = dv[t];
+      const T *nb = g + (int64_t)dc[t] * stride + cp0 + cb;
+      T y[4];
+      if (BLK) {
+        load4(nb, y);
+      } else {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) y[u] = (FULL || cb + u < nc) ? __ldg(nb + u) : T(0);
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) acc[u][i] = fma_t<T>(h, y[u], acc[u][i]);
+    }
+  }
 }
 
-template <typename T, int MODE>
-__global__ void __launch_bounds__(HV_THREADS) k_hv(HvLaunch<T> a) {
+template <typename T, int MODE, bool BLK>
+__global__ void __launch_bounds__(HV_THREADS, 2) k_hv(HvLaunch<T> a) {
+  constexpr int RT = Tile<T>::RT;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double red[HV_THREADS / 32];
-  T *srow = reinterpret_cast<T *>(smem_raw);
+  __shared__ int32_t s_dcol[HV_MAXROWS * ED_MAX_NS];
+  __shared__ T s_dval[HV_MAXROWS * ED_MAX_NS];
+  __shared__ int32_t s_dn[HV_MAXROWS], s_mdw[HV_MAXROWS];
+  __shared__ T s_edw[HV_MAXROWS];
+  T *sm = reinterpret_cast<T *>(smem_raw);
   const HvTables<T> &tb = a.tb;
 
   int j = 0;
@@ -155,81 +476,112 @@ __global__ void __launch_bounds__(HV_THREADS) k_hv(HvLaunch<T> a) {
     }
   }
 
-  const int64_t R = a.rows_per_cta;
-  const int64_t r0 = (int64_t)blockIdx.x * R;
-  const int64_t r1 = min(r0 + R, tb.ddw);
-  const int64_t dup = tb.dup;
-  const int64_t nel = (r1 - r0) * dup;
-  const int64_t base = r0 * dup;
-  const T *rows = g + base;
-  if (a.use_smem) {
-    for (int64_t e = threadIdx.x; e < nel; e += blockDim.x) srow[e] = rows[e];
-    __syncthreads();
-    rows = srow;
-  }
-
-  T dot = T(0);
-  auto epilogue = [&](int64_t e, T acc) {
-    const int64_t gi = base + e;
-    if (MODE == HV_PLAIN) {
-      out[gi] = acc;
-    } else {
-      const T v = mul_t<T>(rows[e], s_cur);
-      T w1 = mul_t<T>(acc, s_cur);
-      if (j > 0) w1 = fma_t<T>(-beta_j, mul_t<T>(prev[gi], s_prev), w1);
-      if (MODE == HV_LANCZOS) {
-        out[gi] = w1;
-        dot = fma_t<T>(v, w1, dot);
+  const HvItem it = tb.items[blockIdx.x];
+  const int64_t stride = tb.stride;
+  const int r0 = it.r0, nr = it.nr, nc = it.nc;
+  const int64_t cp0 = it.c0p;  // first column of the item in the vector layout
+  const int ncp = (nc + 3) & ~3;
+  const int ngroups = (nr + RT - 1) / RT;
+  const bool staged = (size_t)ngroups * ncp * RT * sizeof(T) <= tb.smem;
+  // staging, transposed: sm[(q * ncp + c) * RT + i] = v[r0 + q*RT + i][c]
+  if (staged) {
+    for (int lr = 0; lr < ngroups * RT; ++lr) {
+      const int q = lr / RT, i = lr - q * RT;
+      T *dst = sm + (size_t)q * ncp * RT + i;
+      if (lr < nr) {
+        const T *src = g + (int64_t)(r0 + lr) * stride + cp0;
+        for (int c = threadIdx.x; c < ncp; c += blockDim.x) dst[c * RT] = c < nc ? src[c] : T(0);
       } else {
-        out[gi] = fma_t<T>(-alpha_j, v, w1);
-        a.psi[gi] = fma_t<T>(y_j, v, a.psi[gi]);
+        for (int c = threadIdx.x; c < ncp; c += blockDim.x) dst[c * RT] = T(0);
       }
     }
-  };
-
-  if (dup >= (int64_t)blockDim.x) {
-    for (int64_t lr = 0; lr < r1 - r0; ++lr) {
-      const T *row = rows + lr * dup;
-      for (int64_t c = threadIdx.x; c < dup; c += blockDim.x)
-        epilogue(lr * dup + c, hv_element<T>(tb, row, g, r0 + lr, c));
+  }
+  // per-row data of the item: diagonal pieces and the H_dw neighbour lists
+  for (int lr = threadIdx.x; lr < nr; lr += blockDim.x) {
+    const int64_t r = r0 + lr;
+    const int32_t d0 = __ldg(tb.rp_dw + r), d1 = __ldg(tb.rp_dw + r + 1);
+    s_dn[lr] = d1 - d0;
+    s_mdw[lr] = tb.m_dw[r];
+    s_edw[lr] = tb.e_dw[r];
+    for (int32_t k = d0; k < d1; ++k) {
+      s_dcol[lr * ED_MAX_NS + (k - d0)] = __ldg(tb.col_dw + k);
+      s_dval[lr * ED_MAX_NS + (k - d0)] = __ldg(tb.val_dw + k);
     }
-  } else {
-    for (int64_t e = threadIdx.x; e < nel; e += blockDim.x) {
-      const int64_t lr = e / dup, c = e - lr * dup;
-      epilogue(e, hv_element<T>(tb, rows + lr * dup, g, r0 + lr, c));
+  }
+  __syncthreads();
+
+  const int ntile = ncp / 4;
+  const int P = ntile >= (int)blockDim.x ? (int)blockDim.x : ((ntile + 31) & ~31);
+  const int q = threadIdx.x / P, p = threadIdx.x - q * P;
+  const int lr0 = q * RT;
+  const int nrt = min(RT, nr - lr0);  // rows of this thread (may be <= 0)
+  const T *smq = sm + (size_t)q * ncp * RT;
+
+  T dot = T(0);
+  if (nrt > 0) {
+    for (int tl = p; tl < ntile; tl += P) {
+      const int cb = tl * 4;
+      T acc[4][RT];
+      const bool full = nrt == RT && cb + 4 <= nc;
+      if (full)
+        hv_tile<T, true, BLK>(tb, it, g, smq, staged, lr0, nrt, cb, s_dn, s_dcol, s_dval, s_mdw,
+                              s_edw, acc);
+      else
+        hv_tile<T, false, BLK>(tb, it, g, smq, staged, lr0, nrt, cb, s_dn, s_dcol, s_dval, s_mdw,
+                               s_edw, acc);
+      // epilogue
+#pragma unroll
+      for (int i = 0; i < RT; ++i) {
+        if (i >= nrt) continue;
+        const int64_t rowbase = (int64_t)(r0 + lr0 + i) * stride + cp0;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int c = cb + u;
+          if (c >= nc) continue;
+          const int64_t gi = rowbase + c;
+          if (MODE == HV_PLAIN) {
+            out[gi] = acc[u][i];
+          } else {
+            const T xv = staged ? smq[(size_t)c * RT + i] : g[gi];
+            const T v = mul_t<T>(xv, s_cur);
+            T w1 = mul_t<T>(acc[u][i], s_cur);
+            if (j > 0) w1 = fma_t<T>(-beta_j, mul_t<T>(prev[gi], s_prev), w1);
+            if (MODE == HV_LANCZOS) {
+              out[gi] = w1;
+              dot = fma_t<T>(v, w1, dot);
+            } else {
+              out[gi] = fma_t<T>(-alpha_j, v, w1);
+              a.psi[gi] = fma_t<T>(y_j, v, a.psi[gi]);
+            }
+          }
+        }
+      }
     }
   }
   if (MODE == HV_LANCZOS) {
-    double s = block_sum<T>((double)dot, red);
-    if (threadIdx.x == 0) a.part[blockIdx.x] = s;
+    double smv = block_sum<T>((double)dot, red);
+    if (threadIdx.x == 0) a.part[blockIdx.x] = smv;
   }
 }
 
-static void hv_geometry(int64_t dup, int64_t ddw, int elem, int *R, int *use_smem, int64_t *nblk,
-                        size_t *smem) {
-  int64_t r = std::max<int64_t>(1, (2048 + dup - 1) / std::max<int64_t>(dup, 1));
-  r = std::min<int64_t>(r, std::max<int64_t>(ddw, 1));
-  size_t bytes = (size_t)(r * dup) * elem;
-  while (r > 1 && bytes > HV_SMEM_MAX) {
-    --r;
-    bytes = (size_t)(r * dup) * elem;
-  }
-  *R = (int)r;
-  *use_smem = bytes <= HV_SMEM_MAX ? 1 : 0;
-  *smem = *use_smem ? bytes : 0;
-  *nblk = (ddw + r - 1) / r;
-}
-
-int64_t ed_hv_num_parts(ed_sector s, int elem_size) {
-  int R, us;
-  int64_t nb;
-  size_t sm;
-  hv_geometry(s->sp[0].dim, s->sp[1].dim, elem_size, &R, &us, &nb, &sm);
-  return nb;
+int64_t ed_hv_num_parts(ed_sector s, int layout, int elem_size) {
+  if (ed_build_items(s, layout, elem_size) != ED_OK) return 0;
+  return s->items[layout][elem_size == 8 ? 1 : 0].nitems;
 }
 
 // Opt the product kernels into large dynamic shared memory, once per device
 // (outside any stream capture).
+template <typename T, bool BLK>
+static ed_status prepare_layout() {
+  ED_TRY_CUDA(cudaFuncSetAttribute(k_hv<T, HV_PLAIN, BLK>,
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)HV_SMEM_MAX));
+  ED_TRY_CUDA(cudaFuncSetAttribute(k_hv<T, HV_LANCZOS, BLK>,
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)HV_SMEM_MAX));
+  ED_TRY_CUDA(cudaFuncSetAttribute(k_hv<T, HV_SECOND, BLK>,
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)HV_SMEM_MAX));
+  return ED_OK;
+}
+
 template <typename T>
 ed_status ed_hv_prepare() {
   static std::mutex mu;
@@ -238,12 +590,8 @@ ed_status ed_hv_prepare() {
   ED_TRY_CUDA(cudaGetDevice(&dev));
   std::lock_guard<std::mutex> lk(mu);
   if (dev < 64 && done[dev]) return ED_OK;
-  ED_TRY_CUDA(cudaFuncSetAttribute(k_hv<T, HV_PLAIN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   (int)HV_SMEM_MAX));
-  ED_TRY_CUDA(cudaFuncSetAttribute(k_hv<T, HV_LANCZOS>,
-                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)HV_SMEM_MAX));
-  ED_TRY_CUDA(cudaFuncSetAttribute(k_hv<T, HV_SECOND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   (int)HV_SMEM_MAX));
+  ED_TRY((prepare_layout<T, false>()));
+  ED_TRY((prepare_layout<T, true>()));
   if (dev < 64) done[dev] = true;
   return ED_OK;
 }
@@ -251,8 +599,11 @@ template ed_status ed_hv_prepare<float>();
 template ed_status ed_hv_prepare<double>();
 
 template <typename T, int MODE>
-static ed_status launch_mode(const HvLaunch<T> &a, int64_t nblk, size_t smem, cudaStream_t st) {
-  k_hv<T, MODE><<<(unsigned)nblk, HV_THREADS, smem, st>>>(a);
+static ed_status launch_mode(const HvLaunch<T> &a, cudaStream_t st) {
+  if (a.tb.ell_col)
+    k_hv<T, MODE, true><<<(unsigned)a.tb.nitems, HV_THREADS, a.tb.smem, st>>>(a);
+  else
+    k_hv<T, MODE, false><<<(unsigned)a.tb.nitems, HV_THREADS, a.tb.smem, st>>>(a);
   ED_LAUNCHED(1);
   return ED_OK;
 }
@@ -264,11 +615,9 @@ ed_status ed_launch_hv(ed_sector s, const HvTables<T> &tb, int mode, const T *v,
   ED_TRY(ed_hv_prepare<T>());
   HvLaunch<T> a;
   a.tb = tb;
-  int64_t nblk;
-  size_t smem;
-  hv_geometry(tb.dup, tb.ddw, (int)sizeof(T), &a.rows_per_cta, &a.use_smem, &nblk, &smem);
-  if (nparts) *nparts = nblk;
-  if (nblk == 0 || tb.dup == 0) return ED_OK;
+  if (nparts) *nparts = tb.nitems;
+  if (tb.nitems == 0 || tb.dup == 0) return ED_OK;
+  if (!tb.items) return ED_ERR_ARG;
   a.v = v;
   a.w = w;
   a.b0 = bufs ? bufs[0] : nullptr;
@@ -277,9 +626,9 @@ ed_status ed_launch_hv(ed_sector s, const HvTables<T> &tb, int mode, const T *v,
   a.psi = psi;
   a.st = state;
   a.part = part;
-  if (mode == HV_PLAIN) return launch_mode<T, HV_PLAIN>(a, nblk, smem, st);
-  if (mode == HV_LANCZOS) return launch_mode<T, HV_LANCZOS>(a, nblk, smem, st);
-  return launch_mode<T, HV_SECOND>(a, nblk, smem, st);
+  if (mode == HV_PLAIN) return launch_mode<T, HV_PLAIN>(a, st);
+  if (mode == HV_LANCZOS) return launch_mode<T, HV_LANCZOS>(a, st);
+  return launch_mode<T, HV_SECOND>(a, st);
 }
 
 template ed_status ed_launch_hv<float>(ed_sector, const HvTables<float> &, int, const float *,
@@ -289,17 +638,34 @@ template ed_status ed_launch_hv<double>(ed_sector, const HvTables<double> &, int
                                         double *, double *const *, double *, LanczosState *,
                                         double *, int64_t *, cudaStream_t);
 
-extern "C" ed_status ed_matvec(ed_sector s, ed_precision prec, const void *d_v, void *d_w,
-                               void *stream) {
+static ed_status matvec_layout(ed_sector s, ed_precision prec, const void *d_v, void *d_w,
+                               int64_t n, void *stream, int layout) {
   if (!s || !d_v || !d_w || d_v == d_w) return ED_ERR_ARG;
+  if (n != (layout == 0 ? s->dim : s->bdim)) {
+    ed_set_error_msg("vector length does not match the sector layout");
+    return ED_ERR_ARG;
+  }
   cudaStream_t st = (cudaStream_t)stream;
-  if (prec == ED_FP64) ED_TRY(ed_hv_prepare<double>());
-  else ED_TRY(ed_hv_prepare<float>());
-  if (prec == ED_FP64)
-    return ed_launch_hv<double>(s, ed_hv_tables<double>(s), HV_PLAIN, (const double *)d_v,
-                                (double *)d_w, nullptr, nullptr, nullptr, nullptr, nullptr, st);
-  if (prec == ED_FP32 || prec == ED_FP32_POLISH)
-    return ed_launch_hv<float>(s, ed_hv_tables<float>(s), HV_PLAIN, (const float *)d_v,
+  if (prec == ED_FP64) {
+    ED_TRY(ed_build_items(s, layout, 8));
+    return ed_launch_hv<double>(s, ed_hv_tables<double>(s, layout), HV_PLAIN,
+                                (const double *)d_v, (double *)d_w, nullptr, nullptr, nullptr,
+                                nullptr, nullptr, st);
+  }
+  if (prec == ED_FP32 || prec == ED_FP32_POLISH) {
+    ED_TRY(ed_build_items(s, layout, 4));
+    return ed_launch_hv<float>(s, ed_hv_tables<float>(s, layout), HV_PLAIN, (const float *)d_v,
                                (float *)d_w, nullptr, nullptr, nullptr, nullptr, nullptr, st);
+  }
   return ED_ERR_ARG;
+}
+
+extern "C" ed_status ed_matvec(ed_sector s, ed_precision prec, const void *d_v, void *d_w,
+                               int64_t n, void *stream) {
+  return matvec_layout(s, prec, d_v, d_w, n, stream, 0);
+}
+
+extern "C" ed_status ed_matvec_blocked(ed_sector s, ed_precision prec, const void *d_v, void *d_w,
+                                       int64_t n, void *stream) {
+  return matvec_layout(s, prec, d_v, d_w, n, stream, 1);
 }

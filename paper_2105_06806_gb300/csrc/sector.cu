@@ -54,13 +54,25 @@ ModelParams ed_model_params(const ed_model *m, ed_status *st) {
 
 // ----------------------------------------------------------------- kernels
 
-// One thread per basis state: the string (unrank), impurity mask, diagonal
-// energy E_sigma = sum_a eps_a n_a + (U'-J) sum_{alpha<beta} n_alpha n_beta.
-__global__ void k_spin_basis(ModelParams mp, int spin, int n, int64_t dim, uint32_t *map,
-                             uint8_t *imask, double *ediag, float *ediag32) {
+template <int ORDER>
+__device__ __forceinline__ uint32_t order_unrank(const BlockView &bv, int64_t i, int ns, int n) {
+  return ORDER == 0 ? ed_unrank((uint64_t)i, ns, n) : ed_blocked_unrank(bv, i);
+}
+template <int ORDER>
+__device__ __forceinline__ int64_t order_rank(const BlockView &bv, uint32_t I) {
+  return ORDER == 0 ? ed_rank(I) : ed_blocked_rank(bv, I);
+}
+
+// One thread per basis state: the string, impurity mask, diagonal energy
+// E_sigma = sum_a eps_a n_a + (U'-J) sum_{alpha<beta} n_alpha n_beta, and for
+// the block-major order the permutation to and from sector order.
+template <int ORDER>
+__global__ void k_spin_basis(ModelParams mp, BlockView bv, int spin, int n, int64_t dim,
+                             uint32_t *map, uint8_t *imask, double *ediag, float *ediag32,
+                             int32_t *pidx, int32_t *inv) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= dim) return;
-  uint32_t I = ed_unrank((uint64_t)i, mp.ns, n);
+  uint32_t I = order_unrank<ORDER>(bv, i, mp.ns, n);
   map[i] = I;
   uint32_t m = I & ((1u << mp.norb) - 1u);
   imask[i] = (uint8_t)m;
@@ -71,6 +83,11 @@ __global__ void k_spin_basis(ModelParams mp, int spin, int n, int64_t dim, uint3
   e += (mp.Ust - mp.Jh) * (double)(k * (k - 1) / 2);
   ediag[i] = e;
   ediag32[i] = (float)e;
+  if (ORDER == 1) {
+    const int32_t p = (int32_t)ed_rank(I);
+    pidx[i] = p;
+    inv[p] = (int32_t)i;
+  }
 }
 
 // Hops of one state: for each bath level b of orbital alpha, exactly one of
@@ -121,7 +138,8 @@ __global__ void k_scan_rowptr(int64_t dim, const int32_t *cnt, int32_t *rowptr) 
 
 // CSR fill: H_sigma[i, j] = V * (-1)^(occupied levels strictly between the
 // two levels) for J = I with the electron moved (Eq. Hbuild, Sec. 2.3 signs).
-__global__ void k_fill_csr(ModelParams mp, int spin, int64_t dim, const uint32_t *map,
+template <int ORDER>
+__global__ void k_fill_csr(ModelParams mp, BlockView bv, int spin, int64_t dim, const uint32_t *map,
                            const int32_t *rowptr, int32_t *col, double *val, float *val32) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= dim) return;
@@ -136,7 +154,7 @@ __global__ void k_fill_csr(ModelParams mp, int spin, int64_t dim, const uint32_t
     int lo = d < b ? d : b, hi = d < b ? b : d;
     uint32_t between = ((1u << hi) - 1u) & ~((2u << lo) - 1u);
     double sg = (__popc(I & between) & 1) ? -1.0 : 1.0;
-    int32_t c = (int32_t)ed_rank(J);
+    int32_t c = (int32_t)order_rank<ORDER>(bv, J);
     double v = sg * mp.V[spin][b];
     // insertion keeps the row sorted by column
     int p = m;
@@ -185,15 +203,86 @@ static ed_status dalloc(ed_sector s, P **p, size_t count) {
   return ED_OK;
 }
 
-static ed_status build_spin(ed_sector s, int spin, int n, cudaStream_t st) {
+// Blocks of the block-major order: all tuples (n_0..n_{Norb-1}) with
+// 0 <= n_alpha <= Nbath+1 and sum N, in lexicographic order (host metadata).
+static void enumerate_blocks(int norb, int g, int n, int a, std::vector<int8_t> &cur,
+                             std::vector<int8_t> &keys) {
+  if (a == norb) {
+    if (n == 0) keys.insert(keys.end(), cur.begin(), cur.end());
+    return;
+  }
+  for (int k = 0; k <= std::min(g, n); ++k) {
+    cur[a] = (int8_t)k;
+    enumerate_blocks(norb, g, n - k, a + 1, cur, keys);
+  }
+}
+
+static ed_status build_blocks(ed_sector s, int spin, int n, cudaStream_t st, BlockView *bv) {
   const ModelParams &mp = s->mp;
-  SpinTables &t = s->sp[spin];
+  BlockInfo &b = s->bi[spin];
+  const int g = mp.nbath + 1;
+  std::vector<int8_t> cur(mp.norb, 0);
+  b.keys.clear();
+  enumerate_blocks(mp.norb, g, n, 0, cur, b.keys);
+  b.nblocks = (int)(b.keys.size() / mp.norb);
+  b.offset.assign(b.nblocks + 1, 0);
+  int ncode = 1;
+  for (int a = 0; a < mp.norb; ++a) ncode *= (g + 1);
+  std::vector<int32_t> code2blk(ncode, -1);
+  for (int k = 0; k < b.nblocks; ++k) {
+    int64_t sz = 1;
+    int code = 0;
+    for (int a = 0; a < mp.norb; ++a) {
+      sz *= (int64_t)host_binom(g, b.keys[k * mp.norb + a]);
+      code = code * (g + 1) + b.keys[k * mp.norb + a];
+    }
+    b.offset[k + 1] = b.offset[k] + sz;
+    code2blk[code] = k;
+  }
+  ED_TRY(dalloc(s, &b.d_offset, b.nblocks + 1));
+  ED_TRY(dalloc(s, &b.d_keys, std::max<size_t>(b.keys.size(), 1)));
+  ED_TRY(dalloc(s, &b.d_code2blk, ncode));
+  ED_TRY_CUDA(cudaMemcpyAsync(b.d_offset, b.offset.data(), (b.nblocks + 1) * sizeof(int64_t),
+                              cudaMemcpyHostToDevice, st));
+  if (!b.keys.empty())
+    ED_TRY_CUDA(cudaMemcpyAsync(b.d_keys, b.keys.data(), b.keys.size(), cudaMemcpyHostToDevice, st));
+  ED_TRY_CUDA(cudaMemcpyAsync(b.d_code2blk, code2blk.data(), ncode * sizeof(int32_t),
+                              cudaMemcpyHostToDevice, st));
+  // the host vectors must outlive the asynchronous copies: the sector build
+  // synchronises the stream before returning
+  bv->norb = mp.norb;
+  bv->nbath = mp.nbath;
+  bv->g = g;
+  bv->nblocks = b.nblocks;
+  bv->offset = b.d_offset;
+  bv->keys = b.d_keys;
+  bv->code2blk = b.d_code2blk;
+  return ED_OK;
+}
+
+BlockView ed_block_view(ed_sector s, int spin) {
+  BlockView bv;
+  const BlockInfo &b = s->bi[spin];
+  bv.norb = s->mp.norb;
+  bv.nbath = s->mp.nbath;
+  bv.g = s->mp.nbath + 1;
+  bv.nblocks = b.nblocks;
+  bv.offset = b.d_offset;
+  bv.keys = b.d_keys;
+  bv.code2blk = b.d_code2blk;
+  return bv;
+}
+
+template <int ORDER>
+static ed_status build_spin(ed_sector s, int spin, int n, cudaStream_t st, const BlockView &bv) {
+  const ModelParams &mp = s->mp;
+  SpinTables &t = ORDER == 0 ? s->sp[spin] : s->bk[spin];
   t.n = n;
   t.dim = (int64_t)host_binom(mp.ns, n);
   // every bath level contributes 2*C(Ns-2, n-1) hops (exactly one of the two
   // levels occupied)
   t.nnz = (int64_t)mp.norb * mp.nbath * 2 * (int64_t)host_binom(mp.ns - 2, n - 1);
-  if (t.nnz >= (int64_t)INT32_MAX) return ED_ERR_UNSUPPORTED;
+  if (t.nnz >= (int64_t)INT32_MAX || t.dim >= (int64_t)INT32_MAX) return ED_ERR_UNSUPPORTED;
   ED_TRY(dalloc(s, &t.map, t.dim));
   ED_TRY(dalloc(s, &t.imask, t.dim));
   ED_TRY(dalloc(s, &t.ediag, t.dim));
@@ -202,13 +291,20 @@ static ed_status build_spin(ed_sector s, int spin, int n, cudaStream_t st) {
   ED_TRY(dalloc(s, &t.col, t.nnz));
   ED_TRY(dalloc(s, &t.val, t.nnz));
   ED_TRY(dalloc(s, &t.val32, t.nnz));
+  int32_t *pidx = nullptr, *inv = nullptr;
+  if (ORDER == 1) {
+    ED_TRY(dalloc(s, &s->bi[spin].pidx, t.dim));
+    ED_TRY(dalloc(s, &s->bi[spin].inv, t.dim));
+    pidx = s->bi[spin].pidx;
+    inv = s->bi[spin].inv;
+  }
   int32_t *cnt = nullptr;
   ED_TRY_CUDA(cudaMallocAsync((void **)&cnt, std::max<int64_t>(t.dim, 1) * sizeof(int32_t), st));
   int threads = 256;
   int blocks = (int)((t.dim + threads - 1) / threads);
   if (t.dim > 0) {
-    k_spin_basis<<<blocks, threads, 0, st>>>(mp, spin, n, t.dim, t.map, t.imask, t.ediag,
-                                             t.ediag32);
+    k_spin_basis<ORDER><<<blocks, threads, 0, st>>>(mp, bv, spin, n, t.dim, t.map, t.imask,
+                                                    t.ediag, t.ediag32, pidx, inv);
     ED_LAUNCHED(1);
     k_row_counts<<<blocks, threads, 0, st>>>(mp, t.dim, t.map, cnt);
     ED_LAUNCHED(1);
@@ -216,8 +312,8 @@ static ed_status build_spin(ed_sector s, int spin, int n, cudaStream_t st) {
   k_scan_rowptr<<<1, 1024, 0, st>>>(t.dim, cnt, t.rowptr);
   ED_LAUNCHED(1);
   if (t.dim > 0) {
-    k_fill_csr<<<blocks, threads, 0, st>>>(mp, spin, t.dim, t.map, t.rowptr, t.col, t.val,
-                                           t.val32);
+    k_fill_csr<ORDER><<<blocks, threads, 0, st>>>(mp, bv, spin, t.dim, t.map, t.rowptr, t.col,
+                                                  t.val, t.val32);
     ED_LAUNCHED(1);
   }
   ED_TRY_CUDA(cudaFreeAsync(cnt, st));
@@ -233,9 +329,36 @@ ed_status ed_build_sector_impl(const ModelParams &mp, double U, double Ust, doub
   s->Jh = Jh;
   s->nup = nup;
   s->ndw = ndw;
-  ED_TRY(build_spin(s, 0, nup, st));
-  ED_TRY(build_spin(s, 1, ndw, st));
+  BlockView none;
+  memset(&none, 0, sizeof(none));
+  for (int spin = 0; spin < 2; ++spin) {
+    const int n = spin == 0 ? nup : ndw;
+    ED_TRY(build_spin<0>(s, spin, n, st, none));
+    BlockView bv;
+    ED_TRY(build_blocks(s, spin, n, st, &bv));
+    ED_TRY(build_spin<1>(s, spin, n, st, bv));
+  }
   s->dim = s->sp[0].dim * s->sp[1].dim;
+  // padded block-major columns: every up block rounded up to 4 columns
+  {
+    const BlockInfo &b = s->bi[0];
+    s->up_off_pad.assign(b.nblocks + 1, 0);
+    for (int k = 0; k < b.nblocks; ++k)
+      s->up_off_pad[k + 1] = s->up_off_pad[k] + (b.offset[k + 1] - b.offset[k] + 3) / 4 * 4;
+    s->bstride = s->up_off_pad[b.nblocks];
+    s->bdim = s->bstride * s->sp[1].dim;
+    std::vector<int32_t> colpos(s->sp[0].dim), padinv(std::max<int64_t>(s->bstride, 1), -1);
+    for (int k = 0; k < b.nblocks; ++k)
+      for (int64_t c = b.offset[k]; c < b.offset[k + 1]; ++c) {
+        const int64_t pc = s->up_off_pad[k] + (c - b.offset[k]);
+        colpos[c] = (int32_t)pc;
+        padinv[pc] = (int32_t)c;
+      }
+    ED_TRY(dalloc(s, &s->colpos, colpos.size()));
+    ED_TRY(dalloc(s, &s->padinv, padinv.size()));
+    ED_TRY_CUDA(cudaMemcpyAsync(s->colpos, colpos.data(), colpos.size() * 4, cudaMemcpyHostToDevice, st));
+    ED_TRY_CUDA(cudaMemcpyAsync(s->padinv, padinv.data(), padinv.size() * 4, cudaMemcpyHostToDevice, st));
+  }
   int nm = 1 << mp.norb;
   ED_TRY(dalloc(s, &s->W, nm * nm));
   ED_TRY(dalloc(s, &s->W32, nm * nm));
@@ -265,8 +388,21 @@ static void sector_destroy(ed_sector s) {
   if (!s) return;
   for (int a = 0; a < 2; ++a)
     for (int b = 0; b < 2; ++b) sector_destroy(s->nb[a][b]);
-  free_spin(s->sp[0]);
-  free_spin(s->sp[1]);
+  for (int sp = 0; sp < 2; ++sp) {
+    free_spin(s->sp[sp]);
+    free_spin(s->bk[sp]);
+    cudaFree(s->bi[sp].d_offset);
+    cudaFree(s->bi[sp].d_keys);
+    cudaFree(s->bi[sp].d_code2blk);
+    cudaFree(s->bi[sp].pidx);
+    cudaFree(s->bi[sp].inv);
+    for (int e = 0; e < 2; ++e) cudaFree(s->items[sp][e].d_items);
+  }
+  cudaFree(s->colpos);
+  cudaFree(s->padinv);
+  cudaFree(s->ell_col);
+  cudaFree(s->ell_v32);
+  cudaFree(s->ell_v64);
   cudaFree(s->W);
   cudaFree(s->W32);
   delete s;
@@ -337,6 +473,8 @@ extern "C" ed_status ed_sector_get_info(ed_sector s, ed_sector_info *out) {
   out->nnz_up = s->sp[0].nnz;
   out->nnz_dw = s->sp[1].nnz;
   out->device_bytes = s->device_bytes;
+  out->blocked_stride = s->bstride;
+  out->blocked_dim = s->bdim;
   return ED_OK;
 }
 

@@ -138,3 +138,52 @@ def test_matvec_full_size_sampled(ed, maker):
     got = w[flat].double().cpu().numpy()
     assert np.abs(got - want).max() <= 2e-5 * max(1.0, np.abs(want).max())
     s.free()
+
+
+@pytest.mark.parametrize("ci", range(len(SMALL)))
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_block_major_layout(ed, ci, prec):
+    """Block-major order: the permutation round-trips exactly, is a
+    permutation of the entries, and the block-major product equals the
+    sector-order product up to rounding (only the summation order of the
+    H_up terms differs)."""
+    m, nup, ndw = SMALL[ci]
+    ref = fock.Sector(m, nup, ndw)
+    s = ed.Sector(m, nup, ndw)
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    g = torch.Generator(device="cuda").manual_seed(ci)
+    v = torch.rand(s.dim, device="cuda", dtype=dt, generator=g) * 2 - 1
+    assert s.blocked_dim == s.dim_dw * s.blocked_stride and s.blocked_stride % 4 == 0
+    vb = torch.full((s.blocked_dim,), float("nan"), device="cuda", dtype=dt)
+    back = torch.empty_like(v)
+    ed.permute(s, v, vb, True, prec)
+    ed.permute(s, vb, back, False, prec)
+    assert torch.equal(back, v)
+    pad = torch.zeros(s.blocked_dim - s.dim, device="cuda", dtype=dt)
+    assert torch.equal(torch.sort(vb).values, torch.sort(torch.cat([v, pad])).values)
+    w, w2 = torch.empty_like(v), torch.empty_like(v)
+    wb = torch.empty_like(vb)
+    ed.matvec(s, v, w, prec)
+    ed.matvec_blocked(s, vb, wb, prec)
+    ed.permute(s, wb, w2, False, prec)
+    bnd = _bound(ref, v.double().cpu().numpy())
+    tol = 1e-13 if prec == "fp64" else 4e-6
+    assert np.all(np.abs((w2 - w).double().cpu().numpy()) <= tol * bnd)
+    s.free()
+
+
+def test_vector_length_checked(ed):
+    """Mismatched vector lengths are rejected before any kernel runs."""
+    s = ed.Sector(workload_ns8().model, 4, 4)
+    assert s.blocked_dim != s.dim          # 70 columns padded to 72
+    v = torch.zeros(s.dim, dtype=torch.float64, device="cuda")
+    w = torch.zeros_like(v)
+    with pytest.raises(ed.EDError) as e:
+        ed.matvec_blocked(s, v, w)
+    assert e.value.status == ed.ED_ERR_ARG
+    vb = torch.zeros(s.blocked_dim, dtype=torch.float64, device="cuda")
+    with pytest.raises(ed.EDError):
+        ed.matvec(s, vb, torch.zeros_like(vb))
+    with pytest.raises(ed.EDError):
+        ed.permute(s, v, torch.zeros_like(v), True)
+    s.free()
