@@ -286,6 +286,30 @@ ed_status ed_server_destroy(ed_server srv);
  * had failed (the request completes with ED_ERR_OOM). */
 ed_status ed_server_inject_alloc_failure(ed_server srv, int32_t count);
 
+/* ---------------------------------------------------------------- no allocation
+ * Residual check that allocates nothing (the paper has no counterpart: this
+ * is a service of this library).  For callers that must not allocate device
+ * memory on this path -- code recording into a stream capture in global
+ * mode, where cudaMalloc is prohibited; applications whose device memory is
+ * owned by their own pool allocator; latency-critical loops where an
+ * allocation could block or fail -- it computes, for a caller's vector psi
+ * of n = D elements in sector order (double, device memory):
+ *   host_e_r[0] = <psi, H psi> / <psi, psi>,
+ *   host_e_r[1] = ||H psi - host_e_r[0] psi|| / ||psi||.
+ * It calls no cudaMalloc, cudaFree or other allocating routine: its scratch
+ * (H psi, partial sums, result words) is a file-scope device array of
+ * ED_NOALLOC_MAX_DIM + 2052 doubles (about 8 MiB) that every GPU loading the
+ * library holds until exit.  D above ED_NOALLOC_MAX_DIM (or n != D) returns
+ * ED_ERR_ARG.  The first call on a device looks up the array's device
+ * address (with that device current); make that first call before any
+ * stream capture.  Every call overwrites the scratch words it reads, so no
+ * clearing is needed; calls whose kernels overlap on the GPU (other streams
+ * or threads) race on the shared array and must be serialised by the
+ * caller.  Synchronises `stream`. */
+#define ED_NOALLOC_MAX_DIM (1 << 20)
+ed_status ed_residual_noalloc(ed_sector s, const double *d_psi, int64_t n, double *host_e_r,
+                              void *stream);
+
 const char *ed_status_string(ed_status st);
 const char *ed_last_error(void);
 /* Number of kernels this library has launched in the calling process. */

@@ -28,7 +28,8 @@ EXPORTED = [
     "ed_sector_build", "ed_sector_get_info", "ed_sector_copy_tables", "ed_sector_copy_w",
     "ed_sector_free", "ed_matvec", "ed_matvec_blocked", "ed_sector_permute", "ed_lanczos_ground", "ed_gf_lanczos", "ed_solve",
     "ed_server_create", "ed_submit", "ed_poll", "ed_wait", "ed_server_destroy",
-    "ed_server_inject_alloc_failure", "ed_status_string", "ed_last_error", "ed_kernel_launches",
+    "ed_server_inject_alloc_failure", "ed_residual_noalloc", "ed_status_string", "ed_last_error",
+    "ed_kernel_launches",
 ]
 
 
@@ -153,6 +154,7 @@ def lib():
             "ed_wait": [vp, u64, C.c_double],
             "ed_server_destroy": [vp],
             "ed_server_inject_alloc_failure": [vp, i32],
+            "ed_residual_noalloc": [vp, vp, i64, vp, vp],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -299,6 +301,17 @@ def permute(sector: Sector, x, out, to_blocked=True, precision="fp64", stream=No
                                    C.c_void_p(x.data_ptr()), int(x.numel()),
                                    C.c_void_p(out.data_ptr()), int(out.numel()),
                                    C.c_void_p(_stream_ptr(stream))), "ed_sector_permute")
+
+
+def residual_noalloc(sector: Sector, psi, stream=None):
+    """(E, ||H psi - E psi|| / ||psi||) of an FP64 sector-order vector without
+    any device allocation (scratch in a static device array; the sector
+    dimension must not exceed ED_NOALLOC_MAX_DIM = 2**20)."""
+    out = np.zeros(2, dtype=np.float64)
+    _check(lib().ed_residual_noalloc(sector.h, C.c_void_p(psi.data_ptr()), int(psi.numel()),
+                                     C.c_void_p(out.ctypes.data), C.c_void_p(_stream_ptr(stream))),
+           "ed_residual_noalloc")
+    return float(out[0]), float(out[1])
 
 
 def lanczos_ground(sector: Sector, precision="fp64", max_iter=0, tol=0.0, seed=0x5EED,
