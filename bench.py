@@ -129,6 +129,32 @@ def _sum_over_ranks(dist, x):
     return float(t.item())
 
 
+def _profiled_traffic(workload):
+    """DRAM bytes per launch of the product kernel from the committed ncu
+    summary, or None when the kernel source changed since that capture."""
+    import hashlib
+    import re
+    f = os.path.join(ROOT, "profiles", f"k_hv_blocked_fp32_{workload}.md")
+    src = os.path.join(ROOT, "paper_2105_06806_gb300", "csrc", "matvec.cu")
+    if not os.path.exists(f):
+        return None
+    txt = open(f).read()
+    m = re.search(r"sha256 prefix ([0-9a-f]+)", txt)
+    t = re.search(r"traffic_bytes_per_launch: (\d+)", txt)
+    if not m or not t:
+        return None
+    if hashlib.sha256(open(src, "rb").read()).hexdigest()[:len(m.group(1))] != m.group(1):
+        return None
+    return int(t.group(1))
+
+
+def combine_ranks(dist, nbytes, iters, seconds):
+    """Replicas: every rank ran its own copy of the workload.  Whole-job
+    throughput = all ranks' bytes (iterations) / the slowest rank's time."""
+    t_max = _max_over_ranks(dist, seconds)
+    return (_sum_over_ranks(dist, nbytes) / t_max / 1e9, _sum_over_ranks(dist, iters) / t_max, t_max)
+
+
 def _workload(name):
     import workloads
     return workloads.WORKLOADS[name](0)
@@ -211,7 +237,6 @@ def run_ours(args):
     launches = E.kernel_launches() - l0
     step_ms = [a.elapsed_time(b) for a, b in ev]
     t_s = sum(step_ms) / 1e3
-    t_max = _max_over_ranks(dist, t_s)
     clk = clocks.stop()
 
     # dominant kernel alone: the FP32 block-major product (the one inside
@@ -260,10 +285,9 @@ def run_ours(args):
 
     serving = None
     if rank == 0 and args.serving > 0:
-        serving = run_serving(E, args.serving, args.serving_max_ns)
+        serving = run_serving(E, args.serving, args.serving_max_ns, args.serving_rate)
 
-    value = _sum_over_ranks(dist, tot_bytes) / t_max / 1e9
-    iters_s = _sum_over_ranks(dist, tot_it) / t_max
+    value, iters_s, t_max = combine_ranks(dist, tot_bytes, tot_it, t_s)
     if rank != 0:
         return
     line = {
@@ -280,7 +304,8 @@ def run_ours(args):
         "matvecs_per_step": tot_mv / args.steps,
         "e0": last["e0"], "e0_raw": last["e0_raw"], "residual": last["residual"],
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm,
-                     "unit": "GB/s", "frac": round(achieved / hbm, 4), "traffic": None,
+                     "unit": "GB/s", "frac": round(achieved / hbm, 4),
+                     "traffic": _profiled_traffic(args.workload),
                      "kernel": "k_hv<float, HV_PLAIN> block-major (ed_matvec_blocked)",
                      "peak_source": src, "products_ms": mv,
                      "kernel_ms": round(mv_ms, 4), "algorithmic_bytes": int(alg)},
@@ -372,12 +397,13 @@ def cpu_baseline(wl, budget_s):
             "iters_per_s": round(r["k"] / t, 4), "host_cores_available": os.cpu_count()}
 
 
-def run_serving(E, n_requests, max_ns):
+def run_serving(E, n_requests, max_ns, rate=0.0):
     """Serving stream: Poisson arrivals, mixed (Norb, Ns, sector); returns
     solves/s and p50/p99 latency of t_done - t_submit."""
     import numpy as np
     import workloads
-    reqs = workloads.serving_stream(n_requests, rate_per_s=1e9, seed=0, max_ns=max_ns)
+    reqs = workloads.serving_stream(n_requests, rate_per_s=rate if rate > 0 else 1e9, seed=0,
+                                    max_ns=max_ns)
     srv = E.Server(slots=8)
     t0 = time.perf_counter()
     tickets = []
@@ -403,7 +429,9 @@ def run_serving(E, n_requests, max_ns):
     return {"requests": n_requests, "completed_ok": int(ok), "solves_per_s": round(ok / wall, 3),
             "p50_s": round(float(np.percentile(lat, 50)), 4),
             "p99_s": round(float(np.percentile(lat, 99)), 4), "max_ns": max_ns,
-            "note": "all requests submitted at once (saturation); GS + G(512) per request"}
+            "arrival_rate_per_s": rate if rate > 0 else "all at once (saturation)",
+            "work": "FP32 ground state + FP64 polish + G(512 Matsubara, 200-step FP32 chains) "
+                    "for every orbital and spin"}
 
 
 # ----------------------------------------------------------------- reference arm
@@ -465,8 +493,10 @@ def main():
     ap.add_argument("--quick-gf", action="store_true")
     ap.add_argument("--no-e2e", dest="e2e", action="store_false")
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    ap.add_argument("--serving-rate", type=float, default=0.0,
+                    help="Poisson arrival rate of the serving stream (0: all at once)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
-    ap.add_argument("--serving", type=int, default=0, help="requests of the serving stream")
+    ap.add_argument("--serving", type=int, default=96, help="requests of the serving stream (0: off)")
     ap.add_argument("--serving-max-ns", type=int, default=12)
     ap.add_argument("--matvec-only", default="",
                     help="comma list of {blocked,sector}_{fp32,fp64}: time products only")
