@@ -1,20 +1,20 @@
 """Benchmark of the exact-diagonalisation hot path on GB300.
 
-One step = one impurity solve of the Ns=16 two-orbital Kanamori workload
-(Norb=2, Nbath=7, half filling N_up=N_dw=8, D=165,636,900): sector build
-(tables), FP32 Lanczos ground state with FP64 scalars, second pass, FP64
-polish, and G(i w_n) of orbital 0 (spin up; spin down follows by symmetry)
-from 200-step FP32 Lanczos chains on the N+-1 sectors, 512 Matsubara points
-at beta=100.  All of it runs in libedgb.so; PyTorch supplies the device
-memory of the ground state, the stream and the events.
+One step = one impurity solve (ed_solve) of the Ns=16 two-orbital Kanamori
+workload (Norb=2, Nbath=7, half filling N_up=N_dw=8, D=165,636,900): sector
+build (tables), FP32 Lanczos ground state with FP64 scalars, second pass, FP64
+polish, and G(i w_n) of both orbitals (spin down follows by symmetry) from
+200-step FP32 Lanczos chains on the N+-1 sectors, run concurrently, 512
+Matsubara points at beta=100.  All of it runs in libedgb.so; PyTorch supplies
+the stream, the events and the ground-state buffer of the e2e leg.
 
 value   = algorithmic H.v bytes of every product in the timed steps (8 D per
           FP32 product, 16 D per FP64 product; read v + write w) / time.
 roofline= the product kernel timed alone with CUDA events on its stream
-          (ed_matvec, FP32, 8 D bytes per launch) against the measured HBM
-          copy bandwidth.
-e2e     = the same solve through ed_solve from host model arrays, with the
-          FP64 ground state and G copied back to pinned host memory.
+          (ed_matvec_blocked, FP32, 8 D bytes per launch) against the measured
+          HBM copy bandwidth.
+e2e     = the same solve timed on the host clock, with the FP64 ground state
+          copied back to pinned host memory inside the timed region.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                        [--workload ns16|ns14|ns18] [--serving N]
@@ -185,31 +185,23 @@ def run_ours(args):
     stream = torch.cuda.current_stream()
     psi = torch.empty(D, dtype=torch.float64, device=dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # 256 MB > L2
-    gf_steps, nmats, beta = 200, 512, 100.0
+    gf_steps, nmats, beta = (50 if args.quick_gf else 200), 512, 100.0
     do_gf = args.gf and wl.gf_steps > 0
 
-    def one_step():
-        """Returns (matvec count, algorithmic bytes, lanczos iterations)."""
-        s = E.Sector(m, wl.nup, wl.ndw, stream=stream)
-        r = E.lanczos_ground(s, "fp32_polish", psi=psi, stream=stream)
-        nbytes = 0
-        nmv = r["matvecs"]
-        # first and second FP32 passes: 8 D per product; polish and residual
-        # products in FP64: 16 D
-        n32 = r["iterations"] + max(r["iterations"] - 1, 0) + 1
-        n64 = nmv - n32
-        nbytes += 8 * D * n32 + 16 * D * n64
-        iters = r["iterations"] + r["polish_iterations"]
-        if do_gf:
-            for orb in range(1 if args.quick_gf else m.norb):
-                G, info = E.gf_lanczos(s, psi, r["e0"], orb, 0, "fp32_polish", nsteps=gf_steps,
-                                       beta=beta, nmats=nmats, stream=stream)
-                dp = _sector_dim(ns, wl.nup + 1, wl.ndw)
-                dh = _sector_dim(ns, wl.nup - 1, wl.ndw)
-                nbytes += 8 * dp * info["steps_particle"] + 8 * dh * info["steps_hole"]
-                nmv += info["steps_particle"] + info["steps_hole"]
-                iters += info["steps_particle"] + info["steps_hole"]
-        s.free()
+    def one_step(psi_out=None):
+        """One impurity solve through ed_solve.  Returns (products,
+        algorithmic bytes, Lanczos iterations, result)."""
+        r, G = E.solve(m, wl.nup, wl.ndw, stream=stream, psi=psi_out, precision="fp32_polish",
+                       gf_precision="fp32", nmats=nmats if do_gf else 0, beta=beta,
+                       gf_steps=gf_steps)
+        # ground state: FP32 first pass (k) and second pass (k-1) at 8 D per
+        # product; polish passes and residual products in FP64 at 16 D
+        k = r["iterations"]
+        n32 = k + max(k - 1, 0)
+        n64 = r["matvecs"] - n32
+        nbytes = 8 * D * n32 + 16 * D * n64 + r["gf_product_bytes"]
+        nmv = r["matvecs"] + r["gf_steps_total"]
+        iters = k + r["polish_iterations"] + r["gf_steps_total"]
         return nmv, nbytes, iters, r
 
     for _ in range(args.warmup):
@@ -247,37 +239,47 @@ def run_ours(args):
     alg = 8.0 * D
     achieved = alg / (mv_ms / 1e3) / 1e9
 
-    # end to end through the public one-call API, host buffers
+    # end to end through the public one-call API: host model arrays in; E0,
+    # G and the FP64 ground state back in (pinned) host memory
     e2e = None
     if args.e2e:
-        mm = E.Model(m)
-        o = E.solve_opts(precision="fp32_polish", gf_precision="fp32", nmats=nmats if do_gf else 0,
-                         beta=beta, gf_steps=gf_steps)
-        G = np.zeros(2 * 2 * m.norb * max(o.nmats, 0) + 2)
         host_psi = torch.empty(D, dtype=torch.float64, pin_memory=True)
-        import ctypes as C
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        res = E.ed_solve_result()
-        st = E.lib().ed_solve(C.byref(mm.c), wl.nup, wl.ndw, C.byref(o), C.byref(res),
-                              C.c_void_p(G.ctypes.data if o.nmats > 0 else 0),
-                              C.c_void_p(stream.cuda_stream))
-        host_psi.copy_(psi, non_blocking=True)    # previous step's state vector
+        nmv_e, nb_e, _, r_e = one_step(psi_out=psi)
+        host_psi.copy_(psi, non_blocking=True)
         torch.cuda.synchronize()
         t1 = time.perf_counter()
-        if st != 0:
-            raise E.EDError(st, "ed_solve")
-        n32 = res.ground.iterations * 2
-        n64 = res.ground.matvecs - n32
-        e_bytes = 8 * D * n32 + 16 * D * max(n64, 0)
-        if do_gf:
-            e_bytes += 8 * gf_steps * (_sector_dim(ns, wl.nup + 1, wl.ndw)
-                                       + _sector_dim(ns, wl.nup - 1, wl.ndw)) * m.norb
+        mm = E.Model(m)
         h2d = mm.e_imp.nbytes + mm.e_bath.nbytes + mm.v_bath.nbytes
-        d2h = 8 * D + G.nbytes - 16 + 8 * 6
-        e2e = {"value": round(e_bytes / (t1 - t0) / 1e9, 3), "unit": "GB/s",
+        d2h = 8 * D + (16 * 2 * m.norb * nmats if do_gf else 0) + 8 * 16
+        e2e = {"value": round(nb_e / (t1 - t0) / 1e9, 3), "unit": "GB/s",
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
-               "seconds": round(t1 - t0, 4), "api": "ed_solve + psi to pinned host"}
+               "seconds": round(t1 - t0, 4),
+               "api": "ed_solve (host model in; E0, G out) + ground state to pinned host"}
+
+    # plain FP64 GPU Lanczos against FP32 + FP64 polish, ground state only,
+    # time to solution at the same 1e-10 accuracy target
+    cmp = None
+    if rank == 0 and args.compare:
+        s = E.Sector(m, wl.nup, wl.ndw, stream=stream)
+        out = {}
+        for prec in ("fp64", "fp32_polish", "fp64", "fp32_polish"):   # second round timed
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            r = E.lanczos_ground(s, prec, want_vector=False, stream=stream, allow_maxit=True)
+            torch.cuda.synchronize()
+            out[prec] = (time.perf_counter() - t0, r)
+        s.free()
+        (t64, r64), (t32, r32) = out["fp64"], out["fp32_polish"]
+        cmp = {"fp64_seconds": round(t64, 4), "fp64_iterations": r64["iterations"],
+               "fp64_iters_per_s": round(r64["iterations"] / t64, 2), "fp64_e0": r64["e0"],
+               "fp32_polish_seconds": round(t32, 4),
+               "fp32_polish_iterations": r32["iterations"] + r32["polish_iterations"],
+               "fp32_polish_e0": r32["e0"], "fp32_raw_e0": r32["e0_raw"],
+               "rel_diff_polished": abs(r32["e0"] - r64["e0"]) / abs(r64["e0"]),
+               "rel_diff_raw_fp32": abs(r32["e0_raw"] - r64["e0"]) / abs(r64["e0"]),
+               "speedup_time_to_solution": round(t64 / t32, 3)}
 
     cpu = None
     if rank == 0 and args.cpu_baseline:
@@ -297,7 +299,9 @@ def run_ours(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
         "config": {"workload": wl.name, "dim": D, "norb": m.norb, "ns": ns,
                    "sector": [wl.nup, wl.ndw], "precision": "fp32 Lanczos + fp64 polish",
-                   "gf": f"orbital 0 up, {gf_steps} steps, {nmats} Matsubara, beta={beta}" if do_gf else "none",
+                   "gf": (f"all orbitals, particle and hole chains ({gf_steps} FP32 steps) "
+                          f"concurrently, {nmats} Matsubara points, beta={beta}; spin down by "
+                          "symmetry") if do_gf else "none",
                    "l2": "256 MB flush between steps; vectors 0.66 GB > L2",
                    "parallelism": "replicas" if ws > 1 else "single GPU"},
         "iters_per_s": round(iters_s, 2),
@@ -310,7 +314,7 @@ def run_ours(args):
                      "peak_source": src, "products_ms": mv,
                      "kernel_ms": round(mv_ms, 4), "algorithmic_bytes": int(alg)},
         "e2e": e2e, "gpu_launches": int(launches), "clocks": clk,
-        "cpu_baseline": cpu, "serving": serving,
+        "cpu_baseline": cpu, "serving": serving, "fp64_vs_fp32_polish": cmp,
     }
     print(json.dumps(line))
 
@@ -490,8 +494,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="ns16", choices=["ns14", "ns16", "ns18"])
     ap.add_argument("--no-gf", dest="gf", action="store_false")
-    ap.add_argument("--quick-gf", action="store_true")
+    ap.add_argument("--quick-gf", action="store_true", help="50-step chains instead of 200")
     ap.add_argument("--no-e2e", dest="e2e", action="store_false")
+    ap.add_argument("--no-compare", dest="compare", action="store_false")
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--serving-rate", type=float, default=0.0,
                     help="Poisson arrival rate of the serving stream (0: all at once)")

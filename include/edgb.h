@@ -222,7 +222,8 @@ ed_status ed_gf_lanczos(ed_sector s, ed_precision prec, const void *d_psi, doubl
 
 /* One impurity solve: sector build, ground state, and G for every orbital and
  * both spins (the down spin is copied from the up spin when N_up = N_dw and
- * the model is spin symmetric, Sec. 6.6 twin symmetry).  host_G receives
+ * the model is spin symmetric, Sec. 6.6 twin symmetry).  The particle and
+ * hole chains of all orbitals run concurrently, each on its own stream.  host_G receives
  * [2][norb][nmats] complex values as 2*2*norb*nmats doubles (may be NULL when
  * nmats == 0). */
 typedef struct {
@@ -236,11 +237,17 @@ typedef struct {
 typedef struct {
   ed_lanczos_result ground;
   double t_build_s, t_ground_s, t_gf_s;  /* wall time of each phase */
+  int32_t gf_chains;         /* Lanczos chains run for G                   */
+  int32_t gf_steps_total;    /* products of all chains                     */
+  double gf_product_bytes;   /* algorithmic bytes of those products
+                                (read v + write w per product)              */
 } ed_solve_result;
 
+/* d_psi (nullable, device): receives the normalised ground state in sector
+ * order, D elements, double unless the ground precision is ED_FP32 (float). */
 ed_status ed_solve(const ed_model *model, int32_t nup, int32_t ndw,
                    const ed_solve_opts *opts, ed_solve_result *res,
-                   double *host_G, void *stream);
+                   double *host_G, void *d_psi, void *stream);
 
 /* ---------------------------------------------------------------- serving
  * A request loop on a host thread: requests are admitted while their

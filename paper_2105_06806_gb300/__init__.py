@@ -94,7 +94,8 @@ class ed_solve_opts(C.Structure):
 
 class ed_solve_result(C.Structure):
     _fields_ = [("ground", ed_lanczos_result), ("t_build_s", C.c_double),
-                ("t_ground_s", C.c_double), ("t_gf_s", C.c_double)]
+                ("t_ground_s", C.c_double), ("t_gf_s", C.c_double), ("gf_chains", C.c_int32),
+                ("gf_steps_total", C.c_int32), ("gf_product_bytes", C.c_double)]
 
 
 class ed_server_opts(C.Structure):
@@ -147,7 +148,7 @@ def lib():
             "ed_gf_lanczos": [vp, C.c_int, vp, C.c_double, i32, i32, i32, C.c_double, i32, vp,
                               C.POINTER(ed_gf_info), vp],
             "ed_solve": [C.POINTER(ed_model), i32, i32, C.POINTER(ed_solve_opts),
-                         C.POINTER(ed_solve_result), vp, vp],
+                         C.POINTER(ed_solve_result), vp, vp, vp],
             "ed_server_create": [C.POINTER(ed_server_opts), C.POINTER(vp)],
             "ed_submit": [vp, C.POINTER(ed_request), C.POINTER(u64)],
             "ed_poll": [vp, u64, C.POINTER(ed_result), vp],
@@ -349,16 +350,21 @@ def solve_opts(precision="fp32_polish", gf_precision=None, nmats=512, beta=100.0
                          int(gf_steps), int(nmats), float(beta), gp)
 
 
-def solve(model, nup, ndw, stream=None, **kw):
+def solve(model, nup, ndw, stream=None, psi=None, **kw):
+    """One impurity solve (ed_solve): returns (result dict, G[2][norb][nmats]);
+    `psi` (optional device tensor of D elements) receives the ground state."""
     m = as_model(model)
     o = solve_opts(**kw)
     r = ed_solve_result()
     G = np.zeros(2 * 2 * m.norb * max(o.nmats, 0), dtype=np.float64)
     _check(lib().ed_solve(C.byref(m.c), int(nup), int(ndw), C.byref(o), C.byref(r),
                           C.c_void_p(G.ctypes.data if o.nmats > 0 else 0),
+                          C.c_void_p(psi.data_ptr() if psi is not None else 0),
                           C.c_void_p(_stream_ptr(stream))), "ed_solve")
     out = r.ground.as_dict()
-    out.update(t_build_s=r.t_build_s, t_ground_s=r.t_ground_s, t_gf_s=r.t_gf_s)
+    out.update(t_build_s=r.t_build_s, t_ground_s=r.t_ground_s, t_gf_s=r.t_gf_s,
+               gf_chains=r.gf_chains, gf_steps_total=r.gf_steps_total,
+               gf_product_bytes=r.gf_product_bytes)
     return out, G.view(np.complex128).reshape(2, m.norb, max(o.nmats, 0))
 
 

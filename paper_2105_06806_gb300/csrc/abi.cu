@@ -6,6 +6,8 @@
 #include <atomic>
 #include <chrono>
 #include <string>
+#include <thread>
+#include <vector>
 
 #include "internal.cuh"
 
@@ -45,6 +47,11 @@ extern "C" const char *ed_status_string(ed_status st) {
 ed_status ed_gf_impl(ed_sector s, ed_precision prec, const void *d_psi, double e0, int orb,
                      int spin, int nsteps, double beta, int nmats, double *host_G,
                      ed_gf_info *info, cudaStream_t cs);
+ed_status ed_gf_chain_job(ed_sector s, ed_precision prec, const void *d_psi, double e0, int orb,
+                          int spin, int create, int nsteps, double beta, int nmats,
+                          double *host_G, double *weight, int *steps, int64_t *dim,
+                          cudaEvent_t after);
+ed_status ed_gf_prepare(ed_sector s, int spin, int create, int elem, cudaStream_t cs);
 
 static double now_s() {
   using namespace std::chrono;
@@ -52,11 +59,12 @@ static double now_s() {
 }
 
 ed_status ed_solve_impl(const ed_model *model, int nup, int ndw, const ed_solve_opts *o,
-                        ed_solve_result *res, double *host_G, cudaStream_t cs) {
+                        ed_solve_result *res, double *host_G, void *d_psi_out, cudaStream_t cs) {
   if (!model || !o || !res) return ED_ERR_ARG;
   memset(res, 0, sizeof(*res));
   const int nmats = o->nmats;
   if (nmats < 0 || (nmats > 0 && !host_G)) return ED_ERR_ARG;
+  if (nmats > 0) memset(host_G, 0, sizeof(double) * 2 * 2 * (size_t)model->norb * nmats);
   const ed_precision gp = o->lanczos.precision;
   const bool psi_double = gp != ED_FP32;
   const bool chain32 = o->gf_precision != ED_FP64;
@@ -71,8 +79,10 @@ ed_status ed_solve_impl(const ed_model *model, int nup, int ndw, const ed_solve_
   void *psi = nullptr;
   ed_status rs = ED_OK;
   ed_lanczos_opts lo = o->lanczos;
-  lo.want_vector = nmats > 0 ? 1 : lo.want_vector;
-  if (lo.want_vector) {
+  lo.want_vector = (nmats > 0 || d_psi_out) ? 1 : lo.want_vector;
+  if (d_psi_out) {
+    psi = d_psi_out;  // the caller's buffer holds psi for the chains too
+  } else if (lo.want_vector) {
     cudaError_t e = cudaMallocAsync(&psi, s->dim * (psi_double ? 8 : 4), cs);
     if (e != cudaSuccess) {
       ed_set_cuda_error(e, "cudaMallocAsync(psi)", __FILE__, __LINE__);
@@ -89,20 +99,67 @@ ed_status ed_solve_impl(const ed_model *model, int nup, int ndw, const ed_solve_
     const int steps = o->gf_steps > 0 ? o->gf_steps : 200;
     const double beta = o->beta > 0 ? o->beta : 100.0;
     const int norb = s->mp.norb;
-    for (int spin = 0; spin < 2 && rs == ED_OK; ++spin) {
-      for (int orb = 0; orb < norb && rs == ED_OK; ++orb) {
-        double *G = host_G + 2 * (size_t)nmats * (spin * norb + orb);
-        if (spin == 1 && nup == ndw && s->spin_symmetric) {
-          memcpy(G, host_G + 2 * (size_t)nmats * orb, 2 * sizeof(double) * nmats);
-          continue;
+    const bool copy_dw = nup == ndw && s->spin_symmetric;
+    const int elem = gfp == ED_FP64 ? 8 : 4;
+    struct Job {
+      int orb, spin, create;
+      std::vector<double> G;
+      double weight = 0;
+      int steps = 0;
+      int64_t dim = 0;
+      ed_status st = ED_OK;
+    };
+    std::vector<Job> jobs;
+    for (int spin = 0; spin < 2; ++spin) {
+      if (spin == 1 && copy_dw) continue;
+      for (int create = 1; create >= -1; create -= 2) {
+        if (rs == ED_OK) rs = ed_gf_prepare(s, spin, create, elem, cs);
+        for (int orb = 0; orb < norb; ++orb) {
+          Job j;
+          j.orb = orb;
+          j.spin = spin;
+          j.create = create;
+          j.G.assign(2 * (size_t)nmats, 0.0);
+          jobs.push_back(std::move(j));
         }
-        rs = ed_gf_impl(s, gfp, psi, res->ground.e0, orb, spin, steps, beta, nmats, G, nullptr,
-                        cs);
       }
     }
+    cudaEvent_t ready = nullptr;
+    if (rs == ED_OK && cudaEventCreateWithFlags(&ready, cudaEventDisableTiming) != cudaSuccess)
+      rs = ED_ERR_CUDA;
+    if (rs == ED_OK && cudaEventRecord(ready, cs) != cudaSuccess) rs = ED_ERR_CUDA;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    // chains run concurrently, at most kMaxChains at a time
+    const size_t kMaxChains = 8;
+    for (size_t b = 0; rs == ED_OK && b < jobs.size(); b += kMaxChains) {
+      std::vector<std::thread> th;
+      for (size_t k = b; k < std::min(jobs.size(), b + kMaxChains); ++k) {
+        th.emplace_back([&, k] {
+          cudaSetDevice(dev);
+          Job &j = jobs[k];
+          j.st = ed_gf_chain_job(s, gfp, psi, res->ground.e0, j.orb, j.spin, j.create, steps, beta,
+                                 nmats, j.G.data(), &j.weight, &j.steps, &j.dim, ready);
+        });
+      }
+      for (auto &t : th) t.join();
+    }
+    if (ready) cudaEventDestroy(ready);
+    for (auto &j : jobs) {
+      if (rs == ED_OK && j.st != ED_OK) rs = j.st;
+      double *G = host_G + 2 * (size_t)nmats * (j.spin * norb + j.orb);
+      for (int n = 0; n < 2 * nmats; ++n) G[n] += j.G[n];
+      res->gf_chains += j.steps > 0 ? 1 : 0;
+      res->gf_steps_total += j.steps;
+      res->gf_product_bytes += (double)j.steps * (double)j.dim * 2.0 * elem;
+    }
+    if (copy_dw)
+      for (int orb = 0; orb < norb; ++orb)
+        memcpy(host_G + 2 * (size_t)nmats * (norb + orb), host_G + 2 * (size_t)nmats * orb,
+               2 * sizeof(double) * nmats);
   }
   res->t_gf_s = now_s() - t2;
-  if (psi) cudaFreeAsync(psi, cs);
+  if (psi && psi != d_psi_out) cudaFreeAsync(psi, cs);
   cudaStreamSynchronize(cs);
   ed_sector_free(s);
   return rs;
@@ -110,6 +167,6 @@ ed_status ed_solve_impl(const ed_model *model, int nup, int ndw, const ed_solve_
 
 extern "C" ed_status ed_solve(const ed_model *model, int32_t nup, int32_t ndw,
                               const ed_solve_opts *opts, ed_solve_result *res, double *host_G,
-                              void *stream) {
-  return ed_solve_impl(model, nup, ndw, opts, res, host_G, (cudaStream_t)stream);
+                              void *d_psi, void *stream) {
+  return ed_solve_impl(model, nup, ndw, opts, res, host_G, d_psi, (cudaStream_t)stream);
 }

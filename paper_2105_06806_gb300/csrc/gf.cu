@@ -223,6 +223,60 @@ ed_status ed_gf_impl(ed_sector s, ed_precision prec, const void *d_psi, double e
   return rs;
 }
 
+// One chain (particle: create = +1, hole: -1) of G_{orb,spin}, on its own
+// stream ordered after `after`; its contribution to G goes to host_G
+// (2*nmats doubles, overwritten).  Used by ed_solve to run the chains of a
+// solve concurrently; the neighbour sector and its work lists must already
+// exist (ed_gf_prepare) so that concurrent jobs share no mutable state.
+ed_status ed_gf_chain_job(ed_sector s, ed_precision prec, const void *d_psi, double e0, int orb,
+                          int spin, int create, int nsteps, double beta, int nmats,
+                          double *host_G, double *weight, int *steps, int64_t *dim,
+                          cudaEvent_t after) {
+  *weight = 0.0;
+  *steps = 0;
+  *dim = 0;
+  cudaStream_t cs = nullptr;
+  ED_TRY_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+  ed_status rs = ED_OK;
+  if (after && cudaStreamWaitEvent(cs, after, 0) != cudaSuccess) rs = ED_ERR_CUDA;
+  double2 *dG = nullptr;
+  if (rs == ED_OK &&
+      cudaMallocAsync((void **)&dG, std::max(1, nmats) * sizeof(double2), cs) != cudaSuccess)
+    rs = ED_ERR_OOM;
+  if (rs == ED_OK && cudaMemsetAsync(dG, 0, std::max(1, nmats) * sizeof(double2), cs) != cudaSuccess)
+    rs = ED_ERR_CUDA;
+  if (rs == ED_OK) {
+    if (prec == ED_FP64)
+      rs = one_chain<double, double>(s, (const double *)d_psi, orb, spin, create, nsteps, e0,
+                                     beta, nmats, dG, weight, steps, cs);
+    else if (prec == ED_FP32)
+      rs = one_chain<float, float>(s, (const float *)d_psi, orb, spin, create, nsteps, e0, beta,
+                                   nmats, dG, weight, steps, cs);
+    else
+      rs = one_chain<double, float>(s, (const double *)d_psi, orb, spin, create, nsteps, e0,
+                                    beta, nmats, dG, weight, steps, cs);
+  }
+  if (rs == ED_OK && nmats > 0) {
+    cudaError_t e = cudaMemcpyAsync(host_G, dG, nmats * sizeof(double2), cudaMemcpyDeviceToHost, cs);
+    if (e != cudaSuccess) rs = ED_ERR_CUDA;
+  }
+  if (dG) cudaFreeAsync(dG, cs);
+  if (cudaStreamSynchronize(cs) != cudaSuccess && rs == ED_OK) rs = ED_ERR_CUDA;
+  cudaStreamDestroy(cs);
+  ed_sector nb = s->nb[spin][create > 0 ? 1 : 0];
+  *dim = nb ? nb->dim : 0;
+  return rs;
+}
+
+// Builds the neighbour sector of a chain and its product work lists on the
+// calling thread (before concurrent chain jobs start).
+ed_status ed_gf_prepare(ed_sector s, int spin, int create, int elem, cudaStream_t cs) {
+  ed_sector nb = nullptr;
+  ED_TRY(ed_neighbor_sector(s, spin, create, cs, &nb));
+  if (nb && nb->dim > 0) ED_TRY(ed_build_items(nb, 1, elem));
+  return ED_OK;
+}
+
 extern "C" ed_status ed_gf_lanczos(ed_sector s, ed_precision prec, const void *d_psi, double e0,
                                    int32_t orb, int32_t spin, int32_t nsteps, double beta,
                                    int32_t nmats, double *host_G, ed_gf_info *info, void *stream) {

@@ -585,8 +585,20 @@ static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 // capture is not allowed on the legacy default stream, so the captured
 // Lanczos chunks run here, ordered after and before the caller's stream by
 // events.
+struct ThreadStreams {
+  cudaStream_t s[64] = {nullptr};
+  ~ThreadStreams() {  // released when the owning host thread exits
+    for (int d = 0; d < 64; ++d)
+      if (s[d]) {
+        cudaSetDevice(d);
+        cudaStreamDestroy(s[d]);
+      }
+  }
+};
+
 static cudaStream_t private_stream(ed_status *st) {
-  static thread_local cudaStream_t streams[64] = {nullptr};
+  static thread_local ThreadStreams ts;
+  cudaStream_t *streams = ts.s;
   int dev = 0;
   *st = ED_OK;
   if (cudaGetDevice(&dev) != cudaSuccess || dev >= 64) {

@@ -20,6 +20,7 @@
 // which stay in L2 while the block pair is processed.
 #include <algorithm>
 #include <mutex>
+#include <type_traits>
 
 #include "internal.cuh"
 
@@ -47,13 +48,20 @@ template <>
 __device__ __forceinline__ double add_t<double>(double a, double b) { return __dadd_rn(a, b); }
 
 // Register tile: 4 consecutive columns x RT rows; the RT rows of one column
-// form one 16-byte vector in shared memory.
+// form one 16-byte vector in shared memory (FP32: RT = 4, or 2 with an
+// 8-byte vector when EDGB_RT_F32 = 2).
+#ifndef EDGB_RT_F32
+#define EDGB_RT_F32 4
+#endif
+#ifndef EDGB_DW_UNROLL
+#define EDGB_DW_UNROLL 2
+#endif
 template <typename T>
 struct Tile;
 template <>
 struct Tile<float> {
-  static constexpr int CU = 4, RT = 4;
-  using V = float4;
+  static constexpr int CU = 4, RT = EDGB_RT_F32;
+  using V = typename std::conditional<EDGB_RT_F32 == 4, float4, float2>::type;
 };
 template <>
 struct Tile<double> {
@@ -85,6 +93,10 @@ __device__ __forceinline__ void vec_get(const float4 &v, float *x) {
   x[3] = v.w;
 }
 __device__ __forceinline__ void vec_get(const double2 &v, double *x) {
+  x[0] = v.x;
+  x[1] = v.y;
+}
+__device__ __forceinline__ void vec_get(const float2 &v, float *x) {
   x[0] = v.x;
   x[1] = v.y;
 }
@@ -151,9 +163,12 @@ struct HvLaunch {
 };
 
 constexpr int HV_THREADS = 512;
-constexpr size_t HV_SMEM_TWO = 96 * 1024;   // two CTAs per SM (with the static tables)
+constexpr size_t HV_SMEM_TWO = 88 * 1024;   // two CTAs per SM (with the static tables)
 constexpr size_t HV_SMEM_MAX = 190 * 1024;  // one CTA per SM (very wide blocks)
 constexpr int HV_MAXROWS = 64;              // rows of an item (G * RT <= 16 * 4)
+#ifndef EDGB_MIN_CTAS
+#define EDGB_MIN_CTAS 2
+#endif
 
 static int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
 
@@ -423,7 +438,23 @@ __device__ __forceinline__ void hv_tile(const HvTables<T> &tb, const HvItem &it,
     const int n = s_dn[lr0 + i];
     const int32_t *dc = s_dcol + (lr0 + i) * ED_MAX_NS;
     const T *dv = s_dval + (lr0 + i) * ED_MAX_NS;
-    for (int t = 0; t < n; ++t) {
+    int t = 0;
+    if (BLK && EDGB_DW_UNROLL > 1) {
+      // neighbour loads of EDGB_DW_UNROLL rows issued together
+      for (; t + EDGB_DW_UNROLL <= n; t += EDGB_DW_UNROLL) {
+        T y[EDGB_DW_UNROLL][4];
+#pragma unroll
+        for (int q2 = 0; q2 < EDGB_DW_UNROLL; ++q2)
+          load4(g + (int64_t)dc[t + q2] * stride + cp0 + cb, y[q2]);
+#pragma unroll
+        for (int q2 = 0; q2 < EDGB_DW_UNROLL; ++q2) {
+          const T h = dv[t + q2];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) acc[u][i] = fma_t<T>(h, y[q2][u], acc[u][i]);
+        }
+      }
+    }
+    for (; t < n; ++t) {
       const T h = dv[t];
       const T *nb = g + (int64_t)dc[t] * stride + cp0 + cb;
       T y[4];
@@ -440,7 +471,7 @@ __device__ __forceinline__ void hv_tile(const HvTables<T> &tb, const HvItem &it,
 }
 
 template <typename T, int MODE, bool BLK>
-__global__ void __launch_bounds__(HV_THREADS, 2) k_hv(HvLaunch<T> a) {
+__global__ void __launch_bounds__(HV_THREADS, EDGB_MIN_CTAS) k_hv(HvLaunch<T> a) {
   constexpr int RT = Tile<T>::RT;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double red[HV_THREADS / 32];

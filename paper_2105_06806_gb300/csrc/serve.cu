@@ -10,6 +10,7 @@
 #include <math.h>
 #include <string.h>
 
+#include <algorithm>
 #include <chrono>
 #include <condition_variable>
 #include <deque>
@@ -22,7 +23,7 @@
 #include "internal.cuh"
 
 ed_status ed_solve_impl(const ed_model *model, int nup, int ndw, const ed_solve_opts *o,
-                        ed_solve_result *res, double *host_G, cudaStream_t cs);
+                        ed_solve_result *res, double *host_G, void *d_psi_out, cudaStream_t cs);
 
 namespace {
 
@@ -76,8 +77,8 @@ struct ed_server_s {
 
 // Device bytes a solve needs besides the small sector tables: three Lanczos
 // vectors and psi in the ground precision, two FP64 vectors for the polish,
-// three vectors of the largest neighbour sector for the Green's function
-// chains, plus a fixed allowance.
+// three vectors of the largest neighbour sector for each Green's function
+// chain that runs concurrently (up to 8), plus a fixed allowance.
 static int64_t estimate_bytes(const OwnedRequest &r) {
   const int ns = r.model.norb * (r.model.nbath + 1);
   const int64_t d = (int64_t)binom(ns, r.nup) * (int64_t)binom(ns, r.ndw);
@@ -89,7 +90,8 @@ static int64_t estimate_bytes(const OwnedRequest &r) {
   const int elem = r.opts.lanczos.precision == ED_FP64 ? 8 : 4;
   const int gelem = r.opts.gf_precision == ED_FP64 ? 8 : 4;
   int64_t b = d * (4 * elem + 8 + (r.opts.lanczos.precision == ED_FP32_POLISH ? 5 * 8 : 8));
-  if (r.opts.nmats > 0) b += dn * 3 * gelem;
+  const int64_t chains = std::min(8, 4 * r.model.norb);
+  if (r.opts.nmats > 0) b += chains * dn * 3 * gelem;
   return b + (32ll << 20);
 }
 
@@ -133,7 +135,7 @@ void ed_server_s::worker_main() {
     } else {
       ed_solve_result sr;
       d.res.status = ed_solve_impl(&req->model, req->nup, req->ndw, &req->opts, &sr,
-                                   d.G.empty() ? nullptr : d.G.data(), cs);
+                                   d.G.empty() ? nullptr : d.G.data(), nullptr, cs);
       d.res.ground = sr.ground;
       d.res.e0 = sr.ground.e0;
     }

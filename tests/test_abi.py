@@ -51,7 +51,7 @@ STRUCTS = {
     "ed_lanczos_result": ["e0", "residual_estimate", "iterations", "matvecs"],
     "ed_gf_info": ["weight_hole", "steps_particle", "steps_hole"],
     "ed_solve_opts": ["lanczos", "gf_steps", "nmats", "beta", "gf_precision"],
-    "ed_solve_result": ["ground", "t_build_s", "t_gf_s"],
+    "ed_solve_result": ["ground", "t_build_s", "t_gf_s", "gf_chains", "gf_product_bytes"],
     "ed_server_opts": ["slots", "device_mem_budget", "queue_capacity"],
     "ed_request": ["model", "nup", "ndw", "opts"],
     "ed_result": ["status", "e0", "ground", "norb", "nmats", "t_submit_s", "t_done_s"],
