@@ -83,11 +83,7 @@ ed_status ed_solve_impl(const ed_model *model, int nup, int ndw, const ed_solve_
   if (d_psi_out) {
     psi = d_psi_out;  // the caller's buffer holds psi for the chains too
   } else if (lo.want_vector) {
-    cudaError_t e = cudaMallocAsync(&psi, s->dim * (psi_double ? 8 : 4), cs);
-    if (e != cudaSuccess) {
-      ed_set_cuda_error(e, "cudaMallocAsync(psi)", __FILE__, __LINE__);
-      rs = ED_ERR_OOM;
-    }
+    rs = ed_dmalloc(&psi, s->dim * (psi_double ? 8 : 4), cs, "psi");
   }
   if (rs == ED_OK) {
     rs = ed_lanczos_ground_impl(s, &lo, &res->ground, psi, cs);
@@ -159,9 +155,15 @@ ed_status ed_solve_impl(const ed_model *model, int nup, int ndw, const ed_solve_
                2 * sizeof(double) * nmats);
   }
   res->t_gf_s = now_s() - t2;
-  if (psi && psi != d_psi_out) cudaFreeAsync(psi, cs);
-  cudaStreamSynchronize(cs);
-  ed_sector_free(s);
+  if (psi && psi != d_psi_out) ed_dfree(psi, cs);
+  // every chain job has synchronised its own stream; after this the sector's
+  // tables have no reader left and are released stream-ordered on cs
+  cudaError_t e = cudaStreamSynchronize(cs);
+  ed_sector_release(s, cs);
+  if (rs == ED_OK && e != cudaSuccess) {
+    ed_set_cuda_error(e, "solve stream", __FILE__, __LINE__);
+    rs = ED_ERR_CUDA;
+  }
   return rs;
 }
 

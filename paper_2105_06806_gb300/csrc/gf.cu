@@ -117,11 +117,8 @@ static ed_status one_chain(ed_sector s, const Ti *psi, int orb, int spin, int cr
   const size_t vb = al256(n * sizeof(To));
   const size_t bytes = 3 * vb + al256(sizeof(LanczosState)) + 2 * al256(nparts * sizeof(double));
   void *mem = nullptr;
-  cudaError_t e = cudaMallocAsync(&mem, bytes, cs);
-  if (e != cudaSuccess) {
-    ed_set_cuda_error(e, "cudaMallocAsync(gf chain)", __FILE__, __LINE__);
-    return ED_ERR_OOM;
-  }
+  ED_TRY(ed_dmalloc(&mem, bytes, cs, "gf chain workspace"));
+  cudaError_t e = cudaSuccess;
   char *p = (char *)mem;
   To *bufs[3];
   for (int b = 0; b < 3; ++b) {
@@ -148,14 +145,14 @@ static ed_status one_chain(ed_sector s, const Ti *psi, int orb, int spin, int cr
   ed_status rs = ED_OK;
   // padding entries must stay zero in every chain vector
   if (cudaMemsetAsync(mem, 0, 3 * vb, cs) != cudaSuccess) rs = ED_ERR_CUDA;
-  int32_t *flag = nullptr;
-  if (rs == ED_OK && cudaMallocHost((void **)&flag, 64) != cudaSuccess) rs = ED_ERR_OOM;
+  PinnedFlag flag;
+  if (rs == ED_OK && !flag.p) rs = ED_ERR_OOM;
   if (rs == ED_OK) {
     k_apply_op<Ti, To><<<(unsigned)g2, GF_THREADS, 0, cs>>>(a, psi, bufs[0], part);
     ed_count_launches(1);
     if (cudaGetLastError() != cudaSuccess) rs = ED_ERR_CUDA;
   }
-  if (rs == ED_OK) rs = ed_lanczos_chain<To>(nb, bufs, st, part, part2, g2, nsteps, cs, flag);
+  if (rs == ED_OK) rs = ed_lanczos_chain<To>(nb, bufs, st, part, part2, g2, nsteps, cs, flag.p);
   double hw[2] = {0, 0};
   int32_t hj = 0;
   if (rs == ED_OK) {
@@ -175,8 +172,7 @@ static ed_status one_chain(ed_sector s, const Ti *psi, int orb, int spin, int cr
   }
   *weight = hw[0];
   *steps = hj;
-  cudaFreeAsync(mem, cs);
-  if (flag) cudaFreeHost(flag);
+  ed_dfree(mem, cs);
   return rs;
 }
 
@@ -187,7 +183,7 @@ ed_status ed_gf_impl(ed_sector s, ed_precision prec, const void *d_psi, double e
       nsteps > ED_MAX_LANCZOS || nmats < 0 || (nmats > 0 && (!host_G || !(beta > 0))))
     return ED_ERR_ARG;
   double2 *dG = nullptr;
-  ED_TRY_CUDA(cudaMallocAsync((void **)&dG, std::max(1, nmats) * sizeof(double2), cs));
+  ED_TRY(ed_dmalloc((void **)&dG, std::max(1, nmats) * sizeof(double2), cs, "gf accumulator"));
   ed_status rs = ED_OK;
   if (cudaMemsetAsync(dG, 0, std::max(1, nmats) * sizeof(double2), cs) != cudaSuccess) rs = ED_ERR_CUDA;
   double wp = 0, wh = 0;
@@ -213,7 +209,7 @@ ed_status ed_gf_impl(ed_sector s, ed_precision prec, const void *d_psi, double e
       rs = ED_ERR_CUDA;
     }
   }
-  cudaFreeAsync(dG, cs);
+  ed_dfree(dG, cs);
   if (info) {
     info->weight_particle = wp;
     info->weight_hole = wh;
@@ -240,9 +236,8 @@ ed_status ed_gf_chain_job(ed_sector s, ed_precision prec, const void *d_psi, dou
   ed_status rs = ED_OK;
   if (after && cudaStreamWaitEvent(cs, after, 0) != cudaSuccess) rs = ED_ERR_CUDA;
   double2 *dG = nullptr;
-  if (rs == ED_OK &&
-      cudaMallocAsync((void **)&dG, std::max(1, nmats) * sizeof(double2), cs) != cudaSuccess)
-    rs = ED_ERR_OOM;
+  if (rs == ED_OK)
+    rs = ed_dmalloc((void **)&dG, std::max(1, nmats) * sizeof(double2), cs, "gf accumulator");
   if (rs == ED_OK && cudaMemsetAsync(dG, 0, std::max(1, nmats) * sizeof(double2), cs) != cudaSuccess)
     rs = ED_ERR_CUDA;
   if (rs == ED_OK) {
@@ -260,7 +255,7 @@ ed_status ed_gf_chain_job(ed_sector s, ed_precision prec, const void *d_psi, dou
     cudaError_t e = cudaMemcpyAsync(host_G, dG, nmats * sizeof(double2), cudaMemcpyDeviceToHost, cs);
     if (e != cudaSuccess) rs = ED_ERR_CUDA;
   }
-  if (dG) cudaFreeAsync(dG, cs);
+  ed_dfree(dG, cs);
   if (cudaStreamSynchronize(cs) != cudaSuccess && rs == ED_OK) rs = ED_ERR_CUDA;
   cudaStreamDestroy(cs);
   ed_sector nb = s->nb[spin][create > 0 ? 1 : 0];

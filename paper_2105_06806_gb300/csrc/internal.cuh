@@ -39,6 +39,26 @@ void ed_count_launches(int64_t n);
     }                                                                       \
   } while (0)
 
+// ----------------------------------------------------------------- memory (memory.cu)
+
+// Stream-ordered device allocation from the library's pool (never
+// synchronises the device); ed_dfree orders the release on `st`.
+ed_status ed_dmalloc(void **p, size_t bytes, cudaStream_t st, const char *what);
+void ed_dfree(void *p, cudaStream_t st);
+// Non-blocking stream private to the calling host thread (current device).
+cudaStream_t ed_private_stream(ed_status *st);
+// Page-locked 4-byte host word for polling a device flag, from a recycled pool.
+int32_t *ed_pinned_flag_acquire();
+void ed_pinned_flag_release(int32_t *f);
+
+struct PinnedFlag {
+  int32_t *p = ed_pinned_flag_acquire();
+  PinnedFlag() = default;
+  PinnedFlag(const PinnedFlag &) = delete;
+  PinnedFlag &operator=(const PinnedFlag &) = delete;
+  ~PinnedFlag() { ed_pinned_flag_release(p); }
+};
+
 // ----------------------------------------------------------------- model
 
 // Level energies and hybridisations indexed by level (Sec. 2.1): level a < Norb
@@ -131,6 +151,10 @@ struct ed_sector_s {
   int32_t *ell_col = nullptr;             // local column of the entry
   float *ell_v32 = nullptr;
   double *ell_v64 = nullptr;
+  // Per padded column of a block-major row (small sectors only): {column in
+  // block-major up order or -1 for padding, its first ELL entry, first padded
+  // column of its up block, (ELL row length << 8) | ELL width}.
+  int4 *small_cols = nullptr;
   double *W = nullptr;     // [2^norb][2^norb]
   float *W32 = nullptr;
   ed_sector nb[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};  // [spin][0:c,1:c+]
@@ -243,6 +267,8 @@ struct HvTables {
   int64_t stride;   // row length of the vector layout
   const int32_t *ell_col;
   const T *ell_val;
+  const int4 *small_cols;  // non-null: element-parallel product (small sectors)
+  int64_t small_grid;      // its CTAs (= block partials of the Lanczos mode)
 };
 // layout 0: sector (paper) order; 1: block-major order
 template <typename T>
@@ -289,3 +315,6 @@ ed_status ed_lanczos_ground_impl(ed_sector s, const ed_lanczos_opts *o, ed_lancz
 
 // sector.cu
 ed_status ed_neighbor_sector(ed_sector s, int spin, int create, cudaStream_t st, ed_sector *out);
+// Releases s (and its neighbour sectors) ordered on st, without
+// synchronising the device; no work that reads s may be pending elsewhere.
+void ed_sector_release(ed_sector s, cudaStream_t st);

@@ -68,10 +68,14 @@ __device__ __forceinline__ double mulT<double>(double a, double b) { return __dm
 
 // ----------------------------------------------------------------- tridiagonal
 
+// The helpers below read T_k from shared-memory copies: a[i] = alpha_i,
+// b[i] = beta_i, b2[i] = beta_i^2 (i < k; b[0] unused), so that their serial
+// recurrences wait on shared rather than global loads.
+
 // Sturm count: eigenvalues of T_k below x = sign changes of the leading
 // principal minors p_i = det(T_i - x) (division-free recurrence, rescaled by
 // powers of two; an exact zero counts as a change, as a tiny negative pivot).
-__device__ int sturm_count(const double *a, const double *b, int k, double x) {
+__device__ int sturm_count(const double *a, const double *b2, int k, double x) {
   double pm = 1.0, p = a[0] - x;
   int cnt = 0;
   if (p <= 0.0) {
@@ -79,7 +83,7 @@ __device__ int sturm_count(const double *a, const double *b, int k, double x) {
     cnt = 1;
   }
   for (int i = 1; i < k; ++i) {
-    double pn = (a[i] - x) * p - b[i] * b[i] * pm;
+    double pn = (a[i] - x) * p - b2[i] * pm;
     if (pn == 0.0) pn = -copysign(1e-300, p);
     if ((pn < 0.0) != (p < 0.0)) ++cnt;
     pm = p;
@@ -98,12 +102,12 @@ __device__ int sturm_count(const double *a, const double *b, int k, double x) {
 
 // Squared last component of the normalised eigenvector of T_k for the
 // eigenvalue theta: -p_{k-1}(theta) / p_k'(theta).
-__device__ double last_component_sq(const double *a, const double *b, int k, double x) {
+__device__ double last_component_sq(const double *a, const double *b2, int k, double x) {
   double pm = 1.0, p = a[0] - x;
   double dpm = 0.0, dp = -1.0;
   for (int i = 1; i < k; ++i) {
-    double pn = (a[i] - x) * p - b[i] * b[i] * pm;
-    double dpn = -p + (a[i] - x) * dp - b[i] * b[i] * dpm;
+    double pn = (a[i] - x) * p - b2[i] * pm;
+    double dpn = -p + (a[i] - x) * dp - b2[i] * dpm;
     pm = p;
     p = pn;
     dpm = dp;
@@ -126,25 +130,38 @@ __device__ double last_component_sq(const double *a, const double *b, int k, dou
 
 // Ritz vector of T_k for theta by inverse iteration with the tridiagonal
 // (Thomas) solver: `sweeps` sweeps from a flat start, normalised, largest
-// entry positive.  One thread; `piv` holds k pivots, `y` k entries.
+// entry positive.  One thread.  The factorisation is formed once: rpiv[i] =
+// 1 / pivot_i and mult[i] = beta_i / pivot_{i-1} (scratch of k entries each);
+// y receives k entries.
 __device__ void ritz_vector(const double *a, const double *b, int k, double th, int sweeps,
-                            double *piv, double *y) {
+                            double *rpiv, double *mult, double *y) {
   const double shift = th - 1e-13 * fmax(1.0, fabs(th));
-  piv[0] = a[0] - shift;
-  if (piv[0] == 0.0) piv[0] = 1e-300;
+  double piv = a[0] - shift;
+  if (piv == 0.0) piv = 1e-300;
+  rpiv[0] = 1.0 / piv;
   for (int i = 1; i < k; ++i) {
-    double m = b[i] / piv[i - 1];
+    const double m = b[i] * rpiv[i - 1];
+    mult[i] = m;
     double di = a[i] - shift - m * b[i];
-    piv[i] = di == 0.0 ? 1e-300 : di;
+    if (di == 0.0) di = 1e-300;
+    rpiv[i] = 1.0 / di;
   }
   const double y0 = 1.0 / sqrt((double)k);
   for (int i = 0; i < k; ++i) y[i] = y0;
   for (int it = 0; it < sweeps; ++it) {
-    for (int i = 1; i < k; ++i) y[i] -= (b[i] / piv[i - 1]) * y[i - 1];
-    y[k - 1] = y[k - 1] / piv[k - 1];
-    for (int i = k - 2; i >= 0; --i) y[i] = (y[i] - b[i + 1] * y[i + 1]) / piv[i];
-    double s = 0.0;
-    for (int i = 0; i < k; ++i) s += y[i] * y[i];
+    double yp = y[0];
+    for (int i = 1; i < k; ++i) {
+      yp = y[i] - mult[i] * yp;
+      y[i] = yp;
+    }
+    yp = yp * rpiv[k - 1];
+    y[k - 1] = yp;
+    double s = yp * yp;
+    for (int i = k - 2; i >= 0; --i) {
+      yp = (y[i] - b[i + 1] * yp) * rpiv[i];
+      y[i] = yp;
+      s += yp * yp;
+    }
     s = 1.0 / sqrt(s);
     for (int i = 0; i < k; ++i) y[i] *= s;
   }
@@ -155,10 +172,21 @@ __device__ void ritz_vector(const double *a, const double *b, int k, double th, 
     for (int i = 0; i < k; ++i) y[i] = -y[i];
 }
 
+// Copies T_k of the device state into shared memory (all threads).
+__device__ void stage_tridiag(const LanczosState *st, int k, double *a, double *b, double *b2) {
+  for (int i = threadIdx.x; i < k; i += blockDim.x) {
+    a[i] = st->alpha[i];
+    const double bi = st->beta[i];
+    b[i] = bi;
+    b2[i] = bi * bi;
+  }
+  __syncthreads();
+}
+
 // Lowest eigenvalue of T_k by multisection: every thread evaluates the Sturm
 // count at one interior point; the bracket shrinks by blockDim+1 per round.
-__device__ double lowest_eigenvalue(const double *a, const double *b, int k, double hint_hi,
-                                    double hint_lo, double *sh) {
+__device__ double lowest_eigenvalue(const double *a, const double *b, const double *b2, int k,
+                                    double hint_hi, double hint_lo) {
   __shared__ int first;
   __shared__ double blo, bhi;
   if (threadIdx.x == 0) {
@@ -175,7 +203,8 @@ __device__ double lowest_eigenvalue(const double *a, const double *b, int k, dou
   // warm bracket [hint_lo, hint_hi] when it provably contains the minimum
   if (hint_hi < bhi && hint_lo > blo && hint_lo < hint_hi) {
     __shared__ int ok;
-    if (threadIdx.x == 0) ok = (sturm_count(a, b, k, hint_lo) == 0 && sturm_count(a, b, k, hint_hi) >= 1);
+    if (threadIdx.x == 0)
+      ok = (sturm_count(a, b2, k, hint_lo) == 0 && sturm_count(a, b2, k, hint_hi) >= 1);
     __syncthreads();
     if (ok && threadIdx.x == 0) {
       blo = hint_lo;
@@ -190,7 +219,7 @@ __device__ double lowest_eigenvalue(const double *a, const double *b, int k, dou
     if (threadIdx.x == 0) first = T;
     __syncthreads();
     double x = lo + (hi - lo) * (double)(threadIdx.x + 1) / (double)(T + 1);
-    if (x > lo && x < hi && sturm_count(a, b, k, x) >= 1) atomicMin(&first, (int)threadIdx.x);
+    if (x > lo && x < hi && sturm_count(a, b2, k, x) >= 1) atomicMin(&first, (int)threadIdx.x);
     __syncthreads();
     if (threadIdx.x == 0) {
       int f = first;
@@ -250,7 +279,9 @@ __global__ void __launch_bounds__(AXPY_THREADS) k_axpy_norm(LanczosState *st, T 
 __global__ void k_beta(LanczosState *st, const double *part, int64_t nparts) {
   __shared__ double red[SCALAR_THREADS / 32];
   __shared__ int stop;
-  __shared__ double s_piv[ED_MAX_LANCZOS];
+  // T_k, its squared off-diagonal, then (inverse iteration) pivots and y
+  __shared__ double s_a[ED_MAX_LANCZOS], s_b[ED_MAX_LANCZOS], s_b2[ED_MAX_LANCZOS];
+  __shared__ double s_rp[ED_MAX_LANCZOS], s_y[ED_MAX_LANCZOS];
   if (st->done) return;
   double s2 = cta_sum_parts(part, nparts, red);
   const int j = st->j;
@@ -268,25 +299,31 @@ __global__ void k_beta(LanczosState *st, const double *part, int64_t nparts) {
   const int k = j + 1;
   const bool want = st->tol > 0.0 && (stop != 0 || (k % st->check_every) == 0 || k <= 2);
   if (want) {
+    stage_tridiag(st, k, s_a, s_b, s_b2);
     double prev = st->theta;
     double hi = (k > 1 && isfinite(prev)) ? prev : 1e300;
     double dl = isfinite(st->acc[3]) ? fabs(st->acc[3]) : 0.0;
     double lo = (k > 1 && isfinite(prev)) ? prev - fmax(8.0 * dl, 1e-9 * fmax(1.0, fabs(prev))) : -1e300;
-    double th = lowest_eigenvalue(st->alpha, st->beta, k, hi, lo, red);
+    double th = lowest_eigenvalue(s_a, s_b, s_b2, k, hi, lo);
+    __shared__ int ritz;
     if (threadIdx.x == 0) {
-      double y2 = last_component_sq(st->alpha, st->beta, k, th);
+      double y2 = last_component_sq(s_a, s_b2, k, th);
       double rest = be * sqrt(y2);
       // The polynomial formula loses relative accuracy once the Ritz value
       // has converged; near convergence use inverse iteration instead.
-      if (rest < 1e-6 * fmax(1.0, fabs(th))) {
-        ritz_vector(st->alpha, st->beta, k, th, 3, s_piv, st->y);
-        rest = be * fabs(st->y[k - 1]);
+      ritz = rest < 1e-6 * fmax(1.0, fabs(th));
+      if (ritz) {
+        ritz_vector(s_a, s_b, k, th, 3, s_rp, s_b2, s_y);
+        rest = be * fabs(s_y[k - 1]);
       }
       st->acc[3] = isfinite(prev) ? th - prev : 1e300;
       st->theta = th;
       st->rest = rest;
       if (stop == 0 && rest <= st->tol * fmax(1.0, fabs(th)) && k >= 2) stop = 1;
     }
+    __syncthreads();
+    if (ritz)
+      for (int i = threadIdx.x; i < k; i += blockDim.x) st->y[i] = s_y[i];
   }
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -384,11 +421,17 @@ __global__ void k_state_init(LanczosState *st, const double *part, int64_t npart
   }
 }
 
-// Final Ritz vector of T_k (4 inverse-iteration sweeps), one thread.
+// Final Ritz vector of T_k (4 inverse-iteration sweeps): staged by the CTA,
+// solved by one thread.  Dynamic shared memory: 5 * ED_MAX_LANCZOS doubles.
+constexpr int TRIDIAG_THREADS = 128;
 __global__ void k_tridiag_vector(LanczosState *st, int k) {
-  extern __shared__ double piv[];
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  ritz_vector(st->alpha, st->beta, k, st->theta, 4, piv, st->y);
+  extern __shared__ double sh[];
+  double *a = sh, *b = sh + ED_MAX_LANCZOS, *b2 = sh + 2 * ED_MAX_LANCZOS;
+  double *rp = sh + 3 * ED_MAX_LANCZOS, *y = sh + 4 * ED_MAX_LANCZOS;
+  stage_tridiag(st, k, a, b, b2);
+  if (threadIdx.x == 0) ritz_vector(a, b, k, st->theta, 4, rp, b2, y);
+  __syncthreads();
+  for (int i = threadIdx.x; i < k; i += blockDim.x) st->y[i] = y[i];
 }
 
 // Second pass bookkeeping: v_{j+1} = w / beta_{j+1}.
@@ -561,17 +604,9 @@ struct Workspace {
   cudaStream_t st = nullptr;
   ed_status alloc(size_t bytes, cudaStream_t s) {
     st = s;
-    cudaError_t e = cudaMallocAsync(&mem, std::max<size_t>(bytes, 256), s);
-    if (e != cudaSuccess) {
-      ed_set_cuda_error(e, "cudaMallocAsync(workspace)", __FILE__, __LINE__);
-      mem = nullptr;
-      return ED_ERR_OOM;
-    }
-    return ED_OK;
+    return ed_dmalloc(&mem, std::max<size_t>(bytes, 256), s, "Lanczos workspace");
   }
-  ~Workspace() {
-    if (mem) cudaFreeAsync(mem, st);
-  }
+  ~Workspace() { ed_dfree(mem, st); }
 };
 
 static int64_t reduce_grid(int64_t n) {
@@ -581,41 +616,9 @@ static int64_t reduce_grid(int64_t n) {
 
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
-// Library-private stream of the calling thread (one per device): CUDA graph
-// capture is not allowed on the legacy default stream, so the captured
-// Lanczos chunks run here, ordered after and before the caller's stream by
-// events.
-struct ThreadStreams {
-  cudaStream_t s[64] = {nullptr};
-  ~ThreadStreams() {  // released when the owning host thread exits
-    for (int d = 0; d < 64; ++d)
-      if (s[d]) {
-        cudaSetDevice(d);
-        cudaStreamDestroy(s[d]);
-      }
-  }
-};
-
-static cudaStream_t private_stream(ed_status *st) {
-  static thread_local ThreadStreams ts;
-  cudaStream_t *streams = ts.s;
-  int dev = 0;
-  *st = ED_OK;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev >= 64) {
-    *st = ED_ERR_CUDA;
-    return nullptr;
-  }
-  if (!streams[dev]) {
-    cudaError_t e = cudaStreamCreateWithFlags(&streams[dev], cudaStreamNonBlocking);
-    if (e != cudaSuccess) {
-      ed_set_cuda_error(e, "cudaStreamCreateWithFlags", __FILE__, __LINE__);
-      *st = ED_ERR_CUDA;
-      return nullptr;
-    }
-  }
-  return streams[dev];
-}
-
+// CUDA graph capture is not allowed on the legacy default stream, so the
+// captured Lanczos chunks run on the calling thread's private stream, ordered
+// after and before the caller's stream by events.
 struct StreamJoin {
   cudaEvent_t ev = nullptr;
   ~StreamJoin() {
@@ -640,7 +643,7 @@ static ed_status run_steps(ed_sector s, const HvTables<T> &tb, T *const *bufs, L
   int chunk = n < (1 << 20) ? 16 : 4;
   chunk = std::min(chunk, std::max(1, maxit));
   ed_status ps = ED_OK;
-  cudaStream_t cs = private_stream(&ps);
+  cudaStream_t cs = ed_private_stream(&ps);
   if (ps != ED_OK) return ps;
   StreamJoin join;
   ED_TRY(join.order(caller, cs));
@@ -710,14 +713,6 @@ static ed_status second_pass(ed_sector s, const HvTables<T> &tb, T *const *bufs,
   return ED_OK;
 }
 
-struct PinnedFlag {
-  int32_t *p = nullptr;
-  PinnedFlag() { cudaMallocHost((void **)&p, 64); }
-  ~PinnedFlag() {
-    if (p) cudaFreeHost(p);
-  }
-};
-
 // One Lanczos solve in precision T on sector s, starting from either the
 // seeded vector or (start != nullptr) a given vector in precision T.
 template <typename T>
@@ -754,6 +749,10 @@ static ed_status lanczos_solve(ed_sector s, int maxit, double tol, uint64_t seed
   ED_TRY_CUDA(cudaMemsetAsync(ws.mem, 0, (3 + (want_vector ? 1 : 0)) * vb, cs));
 
   PinnedFlag flag;
+  if (!flag.p) {
+    ed_set_error_msg("page-locked stop flag allocation failed");
+    return ED_ERR_OOM;
+  }
   const int check_every = n > (1 << 22) ? 1 : 4;
   auto init = [&]() -> ed_status {
     if (start) {
@@ -778,7 +777,7 @@ static ed_status lanczos_solve(ed_sector s, int maxit, double tol, uint64_t seed
   const int k = h_state->j;
   int mv = k;
   if (want_vector && k > 0) {
-    k_tridiag_vector<<<1, 1, sizeof(double) * ED_MAX_LANCZOS, cs>>>(st, k);
+    k_tridiag_vector<<<1, TRIDIAG_THREADS, 5 * sizeof(double) * ED_MAX_LANCZOS, cs>>>(st, k);
     ED_LAUNCHED(1);
     // restart the recurrence bookkeeping for the second pass
     ED_TRY(init());

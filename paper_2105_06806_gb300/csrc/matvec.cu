@@ -101,6 +101,15 @@ __device__ __forceinline__ void vec_get(const float2 &v, float *x) {
   x[1] = v.y;
 }
 
+// Element-parallel product for small sectors (one thread per element of the
+// padded block-major vector): below EDGB_SMALL_MAX_DIM elements the tiled
+// kernel has too few work items to fill the GPU and its time is set by the
+// serial per-thread tile, so one thread per element is faster.
+constexpr int HVS_THREADS = 256;
+#ifndef EDGB_SMALL_MAX_DIM
+#define EDGB_SMALL_MAX_DIM (1 << 20)
+#endif
+
 template <typename T>
 static void fill_tables(HvTables<T> &t, const SpinTables &u, const SpinTables &d, const T *vu,
                         const T *vd, const T *eu, const T *e_d, const T *W, int norb) {
@@ -133,6 +142,8 @@ HvTables<double> ed_hv_tables<double>(ed_sector s, int layout) {
   t.stride = layout == 0 ? s->sp[0].dim : s->bstride;
   t.ell_col = layout == 0 ? nullptr : s->ell_col;
   t.ell_val = layout == 0 ? nullptr : s->ell_v64;
+  t.small_cols = layout == 0 ? nullptr : s->small_cols;
+  t.small_grid = t.small_cols ? (s->bdim + HVS_THREADS - 1) / HVS_THREADS : 0;
   return t;
 }
 template <>
@@ -148,6 +159,8 @@ HvTables<float> ed_hv_tables<float>(ed_sector s, int layout) {
   t.stride = layout == 0 ? s->sp[0].dim : s->bstride;
   t.ell_col = layout == 0 ? nullptr : s->ell_col;
   t.ell_val = layout == 0 ? nullptr : s->ell_v32;
+  t.small_cols = layout == 0 ? nullptr : s->small_cols;
+  t.small_grid = t.small_cols ? (s->bdim + HVS_THREADS - 1) / HVS_THREADS : 0;
   return t;
 }
 
@@ -213,8 +226,9 @@ ed_status ed_build_ell(ed_sector s, cudaStream_t st) {
   const BlockInfo &b = s->bi[0];
   const int nb = b.nblocks;
   std::vector<int32_t> rp(s->bk[0].dim + 1);
-  ED_TRY_CUDA(cudaMemcpy(rp.data(), s->bk[0].rowptr, rp.size() * sizeof(int32_t),
-                         cudaMemcpyDeviceToHost));
+  ED_TRY_CUDA(cudaMemcpyAsync(rp.data(), s->bk[0].rowptr, rp.size() * sizeof(int32_t),
+                              cudaMemcpyDeviceToHost, st));
+  ED_TRY_CUDA(cudaStreamSynchronize(st));
   s->ell_deg.assign(nb, 0);
   s->ell_off.assign(nb + 1, 0);
   for (int k = 0; k < nb; ++k) {
@@ -229,38 +243,85 @@ ed_status ed_build_ell(ed_sector s, cudaStream_t st) {
   const int64_t total = std::max<int64_t>(1, s->ell_off[nb]);
   int64_t *d_blk = nullptr, *d_pad = nullptr;
   int32_t *d_off = nullptr, *d_deg = nullptr;
-  auto alloc = [&](void **p, size_t bytes) -> ed_status {
-    cudaError_t e = cudaMalloc(p, std::max<size_t>(bytes, 1));
-    if (e != cudaSuccess) {
-      ed_set_cuda_error(e, "cudaMalloc(ell)", __FILE__, __LINE__);
-      return ED_ERR_OOM;
-    }
-    return ED_OK;
+  int32_t *ell_col = nullptr;
+  float *ell_v32 = nullptr;
+  double *ell_v64 = nullptr;
+  ed_status rs = ed_dmalloc((void **)&ell_col, total * sizeof(int32_t), st, "ell");
+  if (rs == ED_OK) rs = ed_dmalloc((void **)&ell_v32, total * sizeof(float), st, "ell");
+  if (rs == ED_OK) rs = ed_dmalloc((void **)&ell_v64, total * sizeof(double), st, "ell");
+  // block bounds for the fill kernel, released (stream-ordered) after it
+  if (rs == ED_OK) rs = ed_dmalloc((void **)&d_blk, (nb + 1) * sizeof(int64_t), st, "ell bounds");
+  if (rs == ED_OK) rs = ed_dmalloc((void **)&d_pad, (nb + 1) * sizeof(int64_t), st, "ell bounds");
+  if (rs == ED_OK) rs = ed_dmalloc((void **)&d_off, (nb + 1) * sizeof(int32_t), st, "ell bounds");
+  if (rs == ED_OK) rs = ed_dmalloc((void **)&d_deg, nb * sizeof(int32_t), st, "ell bounds");
+  auto h2d = [&](void *dst, const void *src, size_t bytes) {
+    if (rs == ED_OK && cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, st) != cudaSuccess)
+      rs = ED_ERR_CUDA;
   };
-  ED_TRY(alloc((void **)&s->ell_col, total * sizeof(int32_t)));
-  ED_TRY(alloc((void **)&s->ell_v32, total * sizeof(float)));
-  ED_TRY(alloc((void **)&s->ell_v64, total * sizeof(double)));
+  h2d(d_blk, b.offset.data(), (nb + 1) * sizeof(int64_t));
+  h2d(d_pad, s->up_off_pad.data(), (nb + 1) * sizeof(int64_t));
+  h2d(d_off, s->ell_off.data(), (nb + 1) * sizeof(int32_t));
+  h2d(d_deg, s->ell_deg.data(), nb * sizeof(int32_t));
+  if (rs == ED_OK) {
+    int64_t maxw = 1;
+    for (int k = 0; k < nb; ++k)
+      maxw = std::max<int64_t>(maxw, s->up_off_pad[k + 1] - s->up_off_pad[k]);
+    dim3 grid((unsigned)std::min<int64_t>((maxw + 255) / 256, 1024), (unsigned)nb);
+    k_fill_ell<<<grid, 256, 0, st>>>(s->bk[0].rowptr, s->bk[0].col, s->bk[0].val, d_blk, d_off,
+                                     d_deg, d_pad, ell_col, ell_v32, ell_v64);
+    ed_count_launches(1);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+      ed_set_cuda_error(e, "k_fill_ell", __FILE__, __LINE__);
+      rs = ED_ERR_CUDA;
+    }
+  }
+  ed_dfree(d_blk, st);
+  ed_dfree(d_pad, st);
+  ed_dfree(d_off, st);
+  ed_dfree(d_deg, st);
+  if (rs == ED_OK && cudaStreamSynchronize(st) != cudaSuccess) rs = ED_ERR_CUDA;
+  if (rs != ED_OK) {
+    ed_dfree(ell_col, st);
+    ed_dfree(ell_v32, st);
+    ed_dfree(ell_v64, st);
+    return rs;
+  }
+  // published only once filled
+  s->ell_col = ell_col;
+  s->ell_v32 = ell_v32;
+  s->ell_v64 = ell_v64;
   s->device_bytes += total * 16;
-  ED_TRY(alloc((void **)&d_blk, (nb + 1) * sizeof(int64_t)));
-  ED_TRY(alloc((void **)&d_pad, (nb + 1) * sizeof(int64_t)));
-  ED_TRY(alloc((void **)&d_off, (nb + 1) * sizeof(int32_t)));
-  ED_TRY(alloc((void **)&d_deg, nb * sizeof(int32_t)));
-  ED_TRY_CUDA(cudaMemcpy(d_blk, b.offset.data(), (nb + 1) * sizeof(int64_t), cudaMemcpyHostToDevice));
-  ED_TRY_CUDA(cudaMemcpy(d_pad, s->up_off_pad.data(), (nb + 1) * sizeof(int64_t),
-                         cudaMemcpyHostToDevice));
-  ED_TRY_CUDA(cudaMemcpy(d_off, s->ell_off.data(), (nb + 1) * sizeof(int32_t), cudaMemcpyHostToDevice));
-  ED_TRY_CUDA(cudaMemcpy(d_deg, s->ell_deg.data(), nb * sizeof(int32_t), cudaMemcpyHostToDevice));
-  int64_t maxw = 1;
-  for (int k = 0; k < nb; ++k) maxw = std::max<int64_t>(maxw, s->up_off_pad[k + 1] - s->up_off_pad[k]);
-  dim3 grid((unsigned)std::min<int64_t>((maxw + 255) / 256, 1024), (unsigned)nb);
-  k_fill_ell<<<grid, 256, 0, st>>>(s->bk[0].rowptr, s->bk[0].col, s->bk[0].val, d_blk, d_off,
-                                   d_deg, d_pad, s->ell_col, s->ell_v32, s->ell_v64);
-  ED_LAUNCHED(1);
-  ED_TRY_CUDA(cudaStreamSynchronize(st));
-  cudaFree(d_blk);
-  cudaFree(d_pad);
-  cudaFree(d_off);
-  cudaFree(d_deg);
+  return ED_OK;
+}
+
+// Column table of the element-parallel product (small sectors): built once,
+// after the ELL table.  Sectors whose blocks do not fit the packing stay on
+// the tiled kernel.
+static ed_status build_small_cols(ed_sector s, cudaStream_t cs) {
+  if (s->small_cols || s->bdim == 0 || s->bdim > (int64_t)EDGB_SMALL_MAX_DIM) return ED_OK;
+  const BlockInfo &b = s->bi[0];
+  std::vector<int4> cols(s->bstride);
+  for (int k = 0; k < b.nblocks; ++k) {
+    const int64_t C0 = b.offset[k], nc = b.offset[k + 1] - C0;
+    const int64_t p0 = s->up_off_pad[k], ncp = s->up_off_pad[k + 1] - p0;
+    if (ncp >= (1 << 23) || s->ell_deg[k] > 255) return ED_OK;
+    for (int64_t c = 0; c < ncp; ++c)
+      cols[p0 + c] = make_int4(c < nc ? (int)(C0 + c) : -1, s->ell_off[k] + (int)c, (int)p0,
+                               (int)(ncp << 8) | s->ell_deg[k]);
+  }
+  int4 *d = nullptr;
+  ED_TRY(ed_dmalloc((void **)&d, cols.size() * sizeof(int4), cs, "small-sector columns"));
+  cudaError_t e = cudaMemcpyAsync(d, cols.data(), cols.size() * sizeof(int4),
+                                  cudaMemcpyHostToDevice, cs);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(cs);
+  if (e != cudaSuccess) {
+    ed_set_cuda_error(e, "small-sector columns upload", __FILE__, __LINE__);
+    ed_dfree(d, cs);
+    return ED_ERR_CUDA;
+  }
+  s->small_cols = d;
+  s->device_bytes += (int64_t)(cols.size() * sizeof(int4));
   return ED_OK;
 }
 
@@ -282,13 +343,18 @@ static void item_shape(int64_t nc, int elem, int64_t *rows, size_t *bytes_per_gr
 ed_status ed_build_items(ed_sector s, int layout, int elem) {
   ItemList &il = s->items[layout][elem == 8 ? 1 : 0];
   if (il.d_items) return ED_OK;
+  // built once per sector on this thread's private stream, complete on return
+  ed_status ps = ED_OK;
+  cudaStream_t cs = ed_private_stream(&ps);
+  if (ps != ED_OK) return ps;
   std::vector<int64_t> ob_up, ob_dw, op_up;
   if (layout == 0) {
     ob_up = {0, s->sp[0].dim};
     op_up = ob_up;
     ob_dw = {0, s->sp[1].dim};
   } else {
-    ED_TRY(ed_build_ell(s, 0));
+    ED_TRY(ed_build_ell(s, cs));
+    ED_TRY(build_small_cols(s, cs));
     ob_up = s->bi[0].offset;
     op_up = s->up_off_pad;
     ob_dw = s->bi[1].offset;
@@ -319,22 +385,24 @@ ed_status ed_build_items(ed_sector s, int layout, int elem) {
                                (int32_t)nc, (int32_t)op_up[bu], deg, eoff, ncp});
     }
   }
+  HvItem *d_items = nullptr;
+  ED_TRY(ed_dmalloc((void **)&d_items, std::max<size_t>(items.size(), 1) * sizeof(HvItem), cs,
+                    "work items"));
+  cudaError_t e = cudaSuccess;
+  if (!items.empty())
+    e = cudaMemcpyAsync(d_items, items.data(), items.size() * sizeof(HvItem),
+                        cudaMemcpyHostToDevice, cs);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(cs);
+  if (e != cudaSuccess) {
+    ed_set_cuda_error(e, "work items upload", __FILE__, __LINE__);
+    ed_dfree(d_items, cs);
+    return ED_ERR_CUDA;
+  }
+  // published only once complete
   il.nitems = (int64_t)items.size();
   il.smem = smem;
-  cudaError_t e = cudaMalloc((void **)&il.d_items, std::max<size_t>(items.size(), 1) * sizeof(HvItem));
-  if (e != cudaSuccess) {
-    ed_set_cuda_error(e, "cudaMalloc(items)", __FILE__, __LINE__);
-    il.d_items = nullptr;
-    return ED_ERR_OOM;
-  }
+  il.d_items = d_items;
   s->device_bytes += (int64_t)(items.size() * sizeof(HvItem));
-  if (!items.empty()) {
-    e = cudaMemcpy(il.d_items, items.data(), items.size() * sizeof(HvItem), cudaMemcpyHostToDevice);
-    if (e != cudaSuccess) {
-      ed_set_cuda_error(e, "cudaMemcpy(items)", __FILE__, __LINE__);
-      return ED_ERR_CUDA;
-    }
-  }
   return ED_OK;
 }
 
@@ -595,8 +663,84 @@ __global__ void __launch_bounds__(HV_THREADS, EDGB_MIN_CTAS) k_hv(HvLaunch<T> a)
   }
 }
 
+// The same product, one thread per element of the padded block-major vector
+// (small sectors).  Every element takes the same operations in the same
+// order as in k_hv: the diagonal, the H_up entries in ELL order, the H_dw
+// entries in CSR order, then the same epilogue; the Lanczos mode leaves one
+// partial of <v_j, w1> per CTA.
+template <typename T, int MODE>
+__global__ void __launch_bounds__(HVS_THREADS) k_hv_small(HvLaunch<T> a) {
+  __shared__ double red[HVS_THREADS / 32];
+  const HvTables<T> &tb = a.tb;
+  int j = 0;
+  T s_cur = T(1), s_prev = T(0), beta_j = T(0), alpha_j = T(0), y_j = T(0);
+  const T *g;
+  const T *prev = nullptr;
+  T *out;
+  if (MODE == HV_PLAIN) {
+    g = a.v;
+    out = a.w;
+  } else {
+    const LanczosState *st = a.st;
+    if (MODE == HV_LANCZOS && st->done) return;
+    j = st->j;
+    const int m3 = j % 3;  // buffers selected without a local array
+    g = m3 == 0 ? a.b0 : (m3 == 1 ? a.b1 : a.b2);
+    out = m3 == 0 ? a.b1 : (m3 == 1 ? a.b2 : a.b0);
+    prev = m3 == 0 ? a.b2 : (m3 == 1 ? a.b0 : a.b1);
+    s_cur = (T)st->scale[j % 3];
+    s_prev = (T)st->scale[(j + 2) % 3];
+    beta_j = (T)st->beta[j];
+    if (MODE == HV_SECOND) {
+      alpha_j = (T)st->alpha[j];
+      y_j = (T)st->y[j];
+    }
+  }
+  const int64_t stride = tb.stride;
+  const int64_t gi = blockIdx.x * (int64_t)HVS_THREADS + threadIdx.x;
+  T dot = T(0);
+  if (gi < tb.ddw * stride) {
+    const int64_t r = gi / stride;
+    const int pc = (int)(gi - r * stride);
+    const int4 ci = __ldg(tb.small_cols + pc);
+    if (ci.x >= 0) {
+      const T x = g[gi];
+      const T *row = g + r * stride + ci.z;
+      const int deg = ci.w & 255, ncp = ci.w >> 8;
+      const int mu = (int)tb.m_up[ci.x] * tb.nmask;
+      T acc = mul_t<T>(add_t<T>(add_t<T>(tb.e_up[ci.x], tb.e_dw[r]), tb.W[mu + tb.m_dw[r]]), x);
+      for (int e = 0; e < deg; ++e) {
+        const int o = ci.y + e * ncp;
+        acc = fma_t<T>(__ldg(tb.ell_val + o), row[__ldg(tb.ell_col + o)], acc);
+      }
+      const int32_t d0 = __ldg(tb.rp_dw + r), d1 = __ldg(tb.rp_dw + r + 1);
+      for (int32_t k = d0; k < d1; ++k)
+        acc = fma_t<T>(__ldg(tb.val_dw + k), g[(int64_t)__ldg(tb.col_dw + k) * stride + pc], acc);
+      if (MODE == HV_PLAIN) {
+        out[gi] = acc;
+      } else {
+        const T v = mul_t<T>(x, s_cur);
+        T w1 = mul_t<T>(acc, s_cur);
+        if (j > 0) w1 = fma_t<T>(-beta_j, mul_t<T>(prev[gi], s_prev), w1);
+        if (MODE == HV_LANCZOS) {
+          out[gi] = w1;
+          dot = mul_t<T>(v, w1);
+        } else {
+          out[gi] = fma_t<T>(-alpha_j, v, w1);
+          a.psi[gi] = fma_t<T>(y_j, v, a.psi[gi]);
+        }
+      }
+    }
+  }
+  if (MODE == HV_LANCZOS) {
+    double smv = block_sum<T>((double)dot, red);
+    if (threadIdx.x == 0) a.part[blockIdx.x] = smv;
+  }
+}
+
 int64_t ed_hv_num_parts(ed_sector s, int layout, int elem_size) {
   if (ed_build_items(s, layout, elem_size) != ED_OK) return 0;
+  if (layout == 1 && s->small_cols) return (s->bdim + HVS_THREADS - 1) / HVS_THREADS;
   return s->items[layout][elem_size == 8 ? 1 : 0].nitems;
 }
 
@@ -631,7 +775,9 @@ template ed_status ed_hv_prepare<double>();
 
 template <typename T, int MODE>
 static ed_status launch_mode(const HvLaunch<T> &a, cudaStream_t st) {
-  if (a.tb.ell_col)
+  if (a.tb.small_cols)
+    k_hv_small<T, MODE><<<(unsigned)a.tb.small_grid, HVS_THREADS, 0, st>>>(a);
+  else if (a.tb.ell_col)
     k_hv<T, MODE, true><<<(unsigned)a.tb.nitems, HV_THREADS, a.tb.smem, st>>>(a);
   else
     k_hv<T, MODE, false><<<(unsigned)a.tb.nitems, HV_THREADS, a.tb.smem, st>>>(a);
@@ -646,7 +792,7 @@ ed_status ed_launch_hv(ed_sector s, const HvTables<T> &tb, int mode, const T *v,
   ED_TRY(ed_hv_prepare<T>());
   HvLaunch<T> a;
   a.tb = tb;
-  if (nparts) *nparts = tb.nitems;
+  if (nparts) *nparts = tb.small_cols ? tb.small_grid : tb.nitems;
   if (tb.nitems == 0 || tb.dup == 0) return ED_OK;
   if (!tb.items) return ED_ERR_ARG;
   a.v = v;

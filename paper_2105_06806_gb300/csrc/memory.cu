@@ -1,0 +1,136 @@
+// Device and pinned-host memory of the library, and the per-thread private
+// stream.
+//
+// Every device buffer (sector tables, work lists, Lanczos and chain
+// workspaces, psi) comes from one stream-ordered pool per device, owned by
+// the library.  Allocation and release are ordered on a stream and never
+// synchronise the device, so concurrent solves on other streams (the serving
+// loop, the concurrent Green's function chains) do not wait for one another
+// when one of them sets up or tears down a sector.  Freed blocks up to
+// kPoolKeepBytes stay mapped in the pool across synchronisations; above that
+// the pool returns memory to the device at the next synchronisation point.
+//
+// The 4-byte host words that the Lanczos drivers poll for the device stop
+// flag are page-locked (so that the copy of the flag is a true async copy);
+// they are recycled through a free list instead of being allocated and freed
+// per call, because releasing page-locked memory synchronises the device.
+#include <mutex>
+#include <vector>
+
+#include "internal.cuh"
+
+namespace {
+
+constexpr int kMaxDevices = 64;
+constexpr uint64_t kPoolKeepBytes = 2ull << 30;
+
+std::mutex g_pool_mu;
+cudaMemPool_t g_pool[kMaxDevices] = {nullptr};
+
+std::mutex g_flag_mu;
+std::vector<int32_t *> g_free_flags;
+constexpr int kFlagStride = 16;   // one 64-byte line per flag
+constexpr int kFlagsPerChunk = 64;
+
+ed_status device_pool(cudaMemPool_t *out) {
+  int dev = 0;
+  ED_TRY_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxDevices) {
+    ed_set_error_msg("device ordinal out of range");
+    return ED_ERR_CUDA;
+  }
+  std::lock_guard<std::mutex> lk(g_pool_mu);
+  if (!g_pool[dev]) {
+    cudaMemPoolProps props = {};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.handleTypes = cudaMemHandleTypeNone;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaMemPool_t p = nullptr;
+    ED_TRY_CUDA(cudaMemPoolCreate(&p, &props));
+    uint64_t keep = kPoolKeepBytes;
+    cudaError_t e = cudaMemPoolSetAttribute(p, cudaMemPoolAttrReleaseThreshold, &keep);
+    if (e != cudaSuccess) {
+      cudaMemPoolDestroy(p);
+      ed_set_cuda_error(e, "cudaMemPoolSetAttribute", __FILE__, __LINE__);
+      return ED_ERR_CUDA;
+    }
+    g_pool[dev] = p;
+  }
+  *out = g_pool[dev];
+  return ED_OK;
+}
+
+// Private streams of a host thread, one per device; destroyed when the
+// thread exits.
+struct ThreadStreams {
+  cudaStream_t s[kMaxDevices] = {nullptr};
+  ~ThreadStreams() {
+    for (int d = 0; d < kMaxDevices; ++d)
+      if (s[d]) {
+        cudaSetDevice(d);
+        cudaStreamDestroy(s[d]);
+      }
+  }
+};
+
+}  // namespace
+
+ed_status ed_dmalloc(void **p, size_t bytes, cudaStream_t st, const char *what) {
+  *p = nullptr;
+  cudaMemPool_t pool = nullptr;
+  ED_TRY(device_pool(&pool));
+  cudaError_t e = cudaMallocFromPoolAsync(p, bytes > 0 ? bytes : 1, pool, st);
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    ed_set_cuda_error(e, what ? what : "cudaMallocFromPoolAsync", __FILE__, __LINE__);
+    return e == cudaErrorMemoryAllocation ? ED_ERR_OOM : ED_ERR_CUDA;
+  }
+  return ED_OK;
+}
+
+void ed_dfree(void *p, cudaStream_t st) {
+  if (p) cudaFreeAsync(p, st);
+}
+
+cudaStream_t ed_private_stream(ed_status *st) {
+  static thread_local ThreadStreams ts;
+  int dev = 0;
+  *st = ED_OK;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+    *st = ED_ERR_CUDA;
+    return nullptr;
+  }
+  if (!ts.s[dev]) {
+    cudaError_t e = cudaStreamCreateWithFlags(&ts.s[dev], cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+      ed_set_cuda_error(e, "cudaStreamCreateWithFlags", __FILE__, __LINE__);
+      ts.s[dev] = nullptr;
+      *st = ED_ERR_CUDA;
+      return nullptr;
+    }
+  }
+  return ts.s[dev];
+}
+
+int32_t *ed_pinned_flag_acquire() {
+  std::lock_guard<std::mutex> lk(g_flag_mu);
+  if (g_free_flags.empty()) {
+    int32_t *chunk = nullptr;
+    // chunks stay allocated for the life of the process
+    if (cudaMallocHost((void **)&chunk, sizeof(int32_t) * kFlagStride * kFlagsPerChunk) !=
+        cudaSuccess)
+      return nullptr;
+    for (int i = kFlagsPerChunk - 1; i >= 0; --i) g_free_flags.push_back(chunk + i * kFlagStride);
+  }
+  int32_t *f = g_free_flags.back();
+  g_free_flags.pop_back();
+  *f = 0;
+  return f;
+}
+
+void ed_pinned_flag_release(int32_t *f) {
+  if (!f) return;
+  std::lock_guard<std::mutex> lk(g_flag_mu);
+  g_free_flags.push_back(f);
+}

@@ -192,13 +192,9 @@ __global__ void k_wtable(ModelParams mp, double *W, float *W32) {
 // ----------------------------------------------------------------- host
 
 template <typename P>
-static ed_status dalloc(ed_sector s, P **p, size_t count) {
+static ed_status dalloc(ed_sector s, cudaStream_t st, P **p, size_t count) {
   size_t bytes = std::max<size_t>(count, 1) * sizeof(P);
-  cudaError_t e = cudaMalloc((void **)p, bytes);
-  if (e != cudaSuccess) {
-    ed_set_cuda_error(e, "cudaMalloc(sector table)", __FILE__, __LINE__);
-    return ED_ERR_OOM;
-  }
+  ED_TRY(ed_dmalloc((void **)p, bytes, st, "sector table"));
   s->device_bytes += (int64_t)bytes;
   return ED_OK;
 }
@@ -239,9 +235,9 @@ static ed_status build_blocks(ed_sector s, int spin, int n, cudaStream_t st, Blo
     b.offset[k + 1] = b.offset[k] + sz;
     code2blk[code] = k;
   }
-  ED_TRY(dalloc(s, &b.d_offset, b.nblocks + 1));
-  ED_TRY(dalloc(s, &b.d_keys, std::max<size_t>(b.keys.size(), 1)));
-  ED_TRY(dalloc(s, &b.d_code2blk, ncode));
+  ED_TRY(dalloc(s, st, &b.d_offset, b.nblocks + 1));
+  ED_TRY(dalloc(s, st, &b.d_keys, std::max<size_t>(b.keys.size(), 1)));
+  ED_TRY(dalloc(s, st, &b.d_code2blk, ncode));
   ED_TRY_CUDA(cudaMemcpyAsync(b.d_offset, b.offset.data(), (b.nblocks + 1) * sizeof(int64_t),
                               cudaMemcpyHostToDevice, st));
   if (!b.keys.empty())
@@ -283,23 +279,23 @@ static ed_status build_spin(ed_sector s, int spin, int n, cudaStream_t st, const
   // levels occupied)
   t.nnz = (int64_t)mp.norb * mp.nbath * 2 * (int64_t)host_binom(mp.ns - 2, n - 1);
   if (t.nnz >= (int64_t)INT32_MAX || t.dim >= (int64_t)INT32_MAX) return ED_ERR_UNSUPPORTED;
-  ED_TRY(dalloc(s, &t.map, t.dim));
-  ED_TRY(dalloc(s, &t.imask, t.dim));
-  ED_TRY(dalloc(s, &t.ediag, t.dim));
-  ED_TRY(dalloc(s, &t.ediag32, t.dim));
-  ED_TRY(dalloc(s, &t.rowptr, t.dim + 1));
-  ED_TRY(dalloc(s, &t.col, t.nnz));
-  ED_TRY(dalloc(s, &t.val, t.nnz));
-  ED_TRY(dalloc(s, &t.val32, t.nnz));
+  ED_TRY(dalloc(s, st, &t.map, t.dim));
+  ED_TRY(dalloc(s, st, &t.imask, t.dim));
+  ED_TRY(dalloc(s, st, &t.ediag, t.dim));
+  ED_TRY(dalloc(s, st, &t.ediag32, t.dim));
+  ED_TRY(dalloc(s, st, &t.rowptr, t.dim + 1));
+  ED_TRY(dalloc(s, st, &t.col, t.nnz));
+  ED_TRY(dalloc(s, st, &t.val, t.nnz));
+  ED_TRY(dalloc(s, st, &t.val32, t.nnz));
   int32_t *pidx = nullptr, *inv = nullptr;
   if (ORDER == 1) {
-    ED_TRY(dalloc(s, &s->bi[spin].pidx, t.dim));
-    ED_TRY(dalloc(s, &s->bi[spin].inv, t.dim));
+    ED_TRY(dalloc(s, st, &s->bi[spin].pidx, t.dim));
+    ED_TRY(dalloc(s, st, &s->bi[spin].inv, t.dim));
     pidx = s->bi[spin].pidx;
     inv = s->bi[spin].inv;
   }
   int32_t *cnt = nullptr;
-  ED_TRY_CUDA(cudaMallocAsync((void **)&cnt, std::max<int64_t>(t.dim, 1) * sizeof(int32_t), st));
+  ED_TRY(ed_dmalloc((void **)&cnt, std::max<int64_t>(t.dim, 1) * sizeof(int32_t), st, "row counts"));
   int threads = 256;
   int blocks = (int)((t.dim + threads - 1) / threads);
   if (t.dim > 0) {
@@ -316,7 +312,7 @@ static ed_status build_spin(ed_sector s, int spin, int n, cudaStream_t st, const
                                                   t.val, t.val32);
     ED_LAUNCHED(1);
   }
-  ED_TRY_CUDA(cudaFreeAsync(cnt, st));
+  ed_dfree(cnt, st);
   return ED_OK;
 }
 
@@ -354,14 +350,14 @@ ed_status ed_build_sector_impl(const ModelParams &mp, double U, double Ust, doub
         colpos[c] = (int32_t)pc;
         padinv[pc] = (int32_t)c;
       }
-    ED_TRY(dalloc(s, &s->colpos, colpos.size()));
-    ED_TRY(dalloc(s, &s->padinv, padinv.size()));
+    ED_TRY(dalloc(s, st, &s->colpos, colpos.size()));
+    ED_TRY(dalloc(s, st, &s->padinv, padinv.size()));
     ED_TRY_CUDA(cudaMemcpyAsync(s->colpos, colpos.data(), colpos.size() * 4, cudaMemcpyHostToDevice, st));
     ED_TRY_CUDA(cudaMemcpyAsync(s->padinv, padinv.data(), padinv.size() * 4, cudaMemcpyHostToDevice, st));
   }
   int nm = 1 << mp.norb;
-  ED_TRY(dalloc(s, &s->W, nm * nm));
-  ED_TRY(dalloc(s, &s->W32, nm * nm));
+  ED_TRY(dalloc(s, st, &s->W, nm * nm));
+  ED_TRY(dalloc(s, st, &s->W32, nm * nm));
   k_wtable<<<(nm * nm + 63) / 64, 64, 0, st>>>(mp, s->W, s->W32);
   ED_LAUNCHED(1);
   bool sym = true;
@@ -372,41 +368,47 @@ ed_status ed_build_sector_impl(const ModelParams &mp, double U, double Ust, doub
   return ED_OK;
 }
 
-static void free_spin(SpinTables &t) {
-  cudaFree(t.map);
-  cudaFree(t.imask);
-  cudaFree(t.ediag);
-  cudaFree(t.ediag32);
-  cudaFree(t.rowptr);
-  cudaFree(t.col);
-  cudaFree(t.val);
-  cudaFree(t.val32);
+static void free_spin(SpinTables &t, cudaStream_t st) {
+  ed_dfree(t.map, st);
+  ed_dfree(t.imask, st);
+  ed_dfree(t.ediag, st);
+  ed_dfree(t.ediag32, st);
+  ed_dfree(t.rowptr, st);
+  ed_dfree(t.col, st);
+  ed_dfree(t.val, st);
+  ed_dfree(t.val32, st);
   t = SpinTables();
 }
 
-static void sector_destroy(ed_sector s) {
+// Releases the device tables of s and of its cached neighbour sectors,
+// ordered on `st`; work on other streams that reads them must already be
+// complete or ordered before `st`.
+static void sector_destroy(ed_sector s, cudaStream_t st) {
   if (!s) return;
   for (int a = 0; a < 2; ++a)
-    for (int b = 0; b < 2; ++b) sector_destroy(s->nb[a][b]);
+    for (int b = 0; b < 2; ++b) sector_destroy(s->nb[a][b], st);
   for (int sp = 0; sp < 2; ++sp) {
-    free_spin(s->sp[sp]);
-    free_spin(s->bk[sp]);
-    cudaFree(s->bi[sp].d_offset);
-    cudaFree(s->bi[sp].d_keys);
-    cudaFree(s->bi[sp].d_code2blk);
-    cudaFree(s->bi[sp].pidx);
-    cudaFree(s->bi[sp].inv);
-    for (int e = 0; e < 2; ++e) cudaFree(s->items[sp][e].d_items);
+    free_spin(s->sp[sp], st);
+    free_spin(s->bk[sp], st);
+    ed_dfree(s->bi[sp].d_offset, st);
+    ed_dfree(s->bi[sp].d_keys, st);
+    ed_dfree(s->bi[sp].d_code2blk, st);
+    ed_dfree(s->bi[sp].pidx, st);
+    ed_dfree(s->bi[sp].inv, st);
+    for (int e = 0; e < 2; ++e) ed_dfree(s->items[sp][e].d_items, st);
   }
-  cudaFree(s->colpos);
-  cudaFree(s->padinv);
-  cudaFree(s->ell_col);
-  cudaFree(s->ell_v32);
-  cudaFree(s->ell_v64);
-  cudaFree(s->W);
-  cudaFree(s->W32);
+  ed_dfree(s->colpos, st);
+  ed_dfree(s->padinv, st);
+  ed_dfree(s->ell_col, st);
+  ed_dfree(s->ell_v32, st);
+  ed_dfree(s->ell_v64, st);
+  ed_dfree(s->small_cols, st);
+  ed_dfree(s->W, st);
+  ed_dfree(s->W32, st);
   delete s;
 }
+
+void ed_sector_release(ed_sector s, cudaStream_t st) { sector_destroy(s, st); }
 
 extern "C" ed_status ed_sector_build(const ed_model *model, int32_t nup, int32_t ndw,
                                      void *stream, ed_sector *out) {
@@ -426,7 +428,7 @@ extern "C" ed_status ed_sector_build(const ed_model *model, int32_t nup, int32_t
   st = ed_build_sector_impl(mp, model->U, model->Ust, model->Jh, nup, ndw,
                             (cudaStream_t)stream, s);
   if (st != ED_OK) {
-    sector_destroy(s);
+    sector_destroy(s, (cudaStream_t)stream);
     return st;
   }
   *out = s;
@@ -452,7 +454,7 @@ ed_status ed_neighbor_sector(ed_sector s, int spin, int create, cudaStream_t st,
   n->v_bath = s->v_bath;
   ed_status r = ed_build_sector_impl(s->mp, s->U, s->Ust, s->Jh, nup, ndw, st, n);
   if (r != ED_OK) {
-    sector_destroy(n);
+    sector_destroy(n, st);
     return r;
   }
   s->nb[spin][slot] = n;
@@ -504,6 +506,16 @@ extern "C" ed_status ed_sector_copy_w(ed_sector s, double *host_w) {
 
 extern "C" ed_status ed_sector_free(ed_sector s) {
   if (!s) return ED_ERR_ARG;
-  sector_destroy(s);
+  // the caller's streams are not known here: wait for all work of the
+  // device, then release on this thread's private stream
+  ed_status ps = ED_OK;
+  cudaStream_t cs = ed_private_stream(&ps);
+  cudaError_t e = cudaDeviceSynchronize();
+  sector_destroy(s, cs);
+  if (ps != ED_OK) return ps;
+  if (e != cudaSuccess) {
+    ed_set_cuda_error(e, "cudaDeviceSynchronize", __FILE__, __LINE__);
+    return ED_ERR_CUDA;
+  }
   return ED_OK;
 }
