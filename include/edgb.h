@@ -160,6 +160,17 @@ ed_status ed_matvec(ed_sector s, ed_precision prec, const void *d_v, void *d_w, 
  * count does not match the layout, and are asynchronous. */
 ed_status ed_matvec_blocked(ed_sector s, ed_precision prec, const void *d_v, void *d_w,
                             int64_t n, void *stream);
+
+/* Which product kernel serves the block-major layout of s (builds the
+ * block-major work tables if they do not exist yet; synchronous):
+ *   ED_KERNEL_TILED       rows of a work item staged in shared memory, H_up
+ *                         from an ELL table, H_dw from neighbour rows;
+ *   ED_KERNEL_ELEMENTWISE one thread per vector element (sectors of at most
+ *                         2^20 padded elements).
+ * ED_ERR_ARG for a null handle or output. */
+#define ED_KERNEL_TILED 0
+#define ED_KERNEL_ELEMENTWISE 1
+ed_status ed_sector_blocked_kernel(ed_sector s, int32_t *kernel);
 ed_status ed_sector_permute(ed_sector s, ed_precision prec, int32_t to_blocked,
                             const void *d_in, int64_t n_in, void *d_out, int64_t n_out,
                             void *stream);

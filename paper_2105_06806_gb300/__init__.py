@@ -26,7 +26,8 @@ PRECISIONS = {"fp64": FP64, "fp32": FP32, "fp32_polish": FP32_POLISH}
 
 EXPORTED = [
     "ed_sector_build", "ed_sector_get_info", "ed_sector_copy_tables", "ed_sector_copy_w",
-    "ed_sector_free", "ed_matvec", "ed_matvec_blocked", "ed_sector_permute", "ed_lanczos_ground", "ed_gf_lanczos", "ed_solve",
+    "ed_sector_free", "ed_matvec", "ed_matvec_blocked", "ed_sector_blocked_kernel",
+    "ed_sector_permute", "ed_lanczos_ground", "ed_gf_lanczos", "ed_solve",
     "ed_server_create", "ed_submit", "ed_poll", "ed_wait", "ed_server_destroy",
     "ed_server_inject_alloc_failure", "ed_residual_noalloc", "ed_status_string", "ed_last_error",
     "ed_kernel_launches",
@@ -142,6 +143,7 @@ def lib():
             "ed_sector_free": [vp],
             "ed_matvec": [vp, C.c_int, vp, vp, i64, vp],
             "ed_matvec_blocked": [vp, C.c_int, vp, vp, i64, vp],
+            "ed_sector_blocked_kernel": [vp, C.POINTER(i32)],
             "ed_sector_permute": [vp, C.c_int, i32, vp, i64, vp, i64, vp],
             "ed_lanczos_ground": [vp, C.POINTER(ed_lanczos_opts), C.POINTER(ed_lanczos_result),
                                   vp, vp],
@@ -266,6 +268,13 @@ class Sector:
             out["imask"].ctypes.data), "ed_sector_copy_tables")
         out["col"], out["val"] = out["col"][:nnz], out["val"][:nnz]
         return out
+
+    def blocked_kernel(self):
+        """Product kernel of the block-major layout: "tiled" or "elementwise"
+        (ed_sector_blocked_kernel)."""
+        k = C.c_int32()
+        _check(lib().ed_sector_blocked_kernel(self.h, C.byref(k)), "ed_sector_blocked_kernel")
+        return {0: "tiled", 1: "elementwise"}[k.value]
 
     def wtable(self):
         nm = 1 << self.model.norb

@@ -846,3 +846,10 @@ extern "C" ed_status ed_matvec_blocked(ed_sector s, ed_precision prec, const voi
                                        int64_t n, void *stream) {
   return matvec_layout(s, prec, d_v, d_w, n, stream, 1);
 }
+
+extern "C" ed_status ed_sector_blocked_kernel(ed_sector s, int32_t *kernel) {
+  if (!s || !kernel) return ED_ERR_ARG;
+  ED_TRY(ed_build_items(s, 1, 4));
+  *kernel = s->small_cols ? ED_KERNEL_ELEMENTWISE : ED_KERNEL_TILED;
+  return ED_OK;
+}

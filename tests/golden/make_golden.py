@@ -9,8 +9,10 @@ the workload recipe and the oracle's FP64 results:
 * ``oracle_ns14.json`` — Ns=14 single-orbital AIM, sector (7,7), seeded bath
   (seed 0): E0 and G_{0,up}(i w_n) from 200-step chains, plus sampled
   components of psi.
+* ``oracle_norb2_ns14.json`` — Ns=14 two-orbital Kanamori AIM, sector (5,6),
+  seeded bath (seed 0): the same quantities (orbital 0, spin up).
 
-Usage: python tests/golden/make_golden.py [ns8] [ns14]
+Usage: python tests/golden/make_golden.py [ns8] [ns14] [norb2_ns14]
 """
 import json
 import os
@@ -23,7 +25,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, os.path.dirname(os.path.dirname(HERE)))
 
 from oracle import fock, gf, lanczos  # noqa: E402
-from workloads import workload_ns8, workload_ns14  # noqa: E402
+from workloads import workload_ns8, workload_ns14, workload_norb2_ns14  # noqa: E402
 
 SEED = 0x5EED
 
@@ -61,7 +63,10 @@ def main(which):
     if "ns14" in which:
         with open(os.path.join(HERE, "oracle_ns14.json"), "w") as f:
             json.dump(run(workload_ns14(0), nsamp=256), f, indent=1)
+    if "norb2_ns14" in which:
+        with open(os.path.join(HERE, "oracle_norb2_ns14.json"), "w") as f:
+            json.dump(run(workload_norb2_ns14(0), nsamp=256), f, indent=1)
 
 
 if __name__ == "__main__":
-    main(sys.argv[1:] or ["ns8", "ns14"])
+    main(sys.argv[1:] or ["ns8", "ns14", "norb2_ns14"])

@@ -10,7 +10,7 @@ import pytest
 import torch
 
 from oracle import fock, gf, lanczos
-from workloads import make_model, workload_ns8, workload_ns14
+from workloads import make_model, workload_ns8, workload_ns14, workload_norb2_ns14
 
 pytestmark = pytest.mark.gpu
 GOLD = os.path.join(os.path.dirname(__file__), "golden")
@@ -62,6 +62,32 @@ def test_ns14_gf(ed):
     G, _ = ed.gf_lanczos(s, psi, r["e0"], 0, 0, "fp64", nsteps=200, beta=100.0, nmats=512)
     assert np.abs(G - Gref).max() <= 1e-8
     rp, psip = _ground(ed, s, "fp32_polish")
+    G2, _ = ed.gf_lanczos(s, psip, rp["e0"], 0, 0, "fp32_polish", nsteps=200, beta=100.0,
+                          nmats=512)
+    assert np.abs(G2 - Gref).max() <= 1e-5
+    s.free()
+
+
+def test_norb2_ns14_ground_and_gf(ed):
+    """Two-orbital Kanamori sector (5,6), D = 6,012,006 (tiled product, many
+    block pairs, N_up != N_dw): E0, psi samples and G_{0,up} against the
+    oracle, FP64 and FP32 + polish."""
+    g, Gref = _gold("oracle_norb2_ns14.json")
+    wl = workload_norb2_ns14(0)
+    s = ed.Sector(wl.model, wl.nup, wl.ndw)
+    assert s.blocked_kernel() == "tiled"
+    r, psi = _ground(ed, s, "fp64")
+    assert abs(r["e0"] - g["e0"]) <= 1e-10 * abs(g["e0"])
+    p = psi.cpu().numpy()
+    p *= np.sign(p[np.argmax(np.abs(p))])
+    idx = np.array(g["psi_index"])
+    assert np.abs(p[idx] - np.array(g["psi_value"])).max() < 1e-8
+    G, info = ed.gf_lanczos(s, psi, r["e0"], 0, 0, "fp64", nsteps=200, beta=100.0, nmats=512)
+    assert np.abs(G - Gref).max() <= 1e-8
+    assert abs(info["weight_particle"] - g["weight_particle"]) < 1e-10
+    assert abs(info["weight_hole"] - g["weight_hole"]) < 1e-10
+    rp, psip = _ground(ed, s, "fp32_polish")
+    assert abs(rp["e0"] - g["e0"]) <= 1e-10 * abs(g["e0"])
     G2, _ = ed.gf_lanczos(s, psip, rp["e0"], 0, 0, "fp32_polish", nsteps=200, beta=100.0,
                           nmats=512)
     assert np.abs(G2 - Gref).max() <= 1e-5

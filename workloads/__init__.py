@@ -173,6 +173,17 @@ def workload_ns14(seed: int = 0) -> Workload:
                     description=f"Norb=1 Nbath=13 Ns=14 sector (7,7) D=11778624 U=4 seed={seed}")
 
 
+def workload_norb2_ns14(seed: int = 0) -> Workload:
+    """Two-orbital density-density Kanamori AIM, Nbath=6 per orbital
+    (Ns=14), off half filling (5,6), D=6,012,006; U=3, J=0.5, U'=2.  A
+    parity case for the two-orbital product at a size the oracle solves in
+    minutes."""
+    e, v = random_bath(2, 6, seed)
+    m = make_model(2, 6, U=3.0, Jh=0.5, Ust=2.0, e_bath=e, v_bath=v, name="kanamori2_ns14")
+    return Workload("kanamori_norb2_ns14_n5_6", m, 5, 6,
+                    description=f"Norb=2 Nbath=6 Ns=14 sector (5,6) D=6012006 U=3 J=0.5 seed={seed}")
+
+
 def workload_ns16(seed: int = 0) -> Workload:
     """Two-orbital density-density Kanamori AIM, Nbath=7 per orbital (Ns=16),
     half filling (8,8), D=165,636,900; U=3, J=0.5, U'=2, e_d=-3.25."""
