@@ -53,9 +53,6 @@ __device__ __forceinline__ double add_t<double>(double a, double b) { return __d
 #ifndef EDGB_RT_F32
 #define EDGB_RT_F32 4
 #endif
-#ifndef EDGB_DW_UNROLL
-#define EDGB_DW_UNROLL 2
-#endif
 template <typename T>
 struct Tile;
 template <>
@@ -191,13 +188,15 @@ static int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
 // (the column itself, 0), which adds an exact zero.  One grid row per block.
 __global__ void k_fill_ell(const int32_t *rowptr, const int32_t *col, const double *val,
                            const int64_t *blk_off, const int32_t *ell_off, const int32_t *ell_deg,
-                           const int64_t *pad_off, int32_t *ell_col, float *v32, double *v64) {
+                           const int64_t *pad_off, const int32_t *run_len, int32_t *ell_col,
+                           float *v32, double *v64) {
   const int b = blockIdx.y;
   const int64_t C0 = blk_off[b], nc = blk_off[b + 1] - C0;
   const int64_t ncp = pad_off[b + 1] - pad_off[b];
   const int64_t ntile = ncp / 4;
   const int deg = ell_deg[b];
   const int64_t base = ell_off[b];
+  const int64_t dF = run_len[b];
   for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < ncp;
        c += (int64_t)gridDim.x * blockDim.x) {
     const int64_t t = c >> 2, u = c & 3;
@@ -206,17 +205,26 @@ __global__ void k_fill_ell(const int32_t *rowptr, const int32_t *col, const doub
       k0 = rowptr[C0 + c];
       n = rowptr[C0 + c + 1] - k0;
     }
-    for (int e = 0; e < deg; ++e) {
-      const int64_t o = base + ((int64_t)e * ntile + t) * 4 + u;
-      if (e < n) {
-        ell_col[o] = (int32_t)(col[k0 + e] - C0);
-        v64[o] = val[k0 + e];
-        v32[o] = (float)val[k0 + e];
-      } else {
-        ell_col[o] = c < nc ? (int32_t)c : 0;
-        v64[o] = 0.0;
-        v32[o] = 0.0f;
+    // entry order: first the hops that keep the last group's string (they
+    // shift the column by whole runs of dF, the same for every column of a
+    // run), then the others, each in ascending target order
+    int e = 0;
+    for (int pass = 0; pass < 2; ++pass)
+      for (int32_t k = k0; k < k0 + n; ++k) {
+        const int64_t tgt = col[k] - C0;
+        const bool same_run_pos = (tgt % dF) == (c % dF);
+        if (same_run_pos != (pass == 0)) continue;
+        const int64_t o = base + ((int64_t)e * ntile + t) * 4 + u;
+        ell_col[o] = (int32_t)tgt;
+        v64[o] = val[k];
+        v32[o] = (float)val[k];
+        ++e;
       }
+    for (; e < deg; ++e) {
+      const int64_t o = base + ((int64_t)e * ntile + t) * 4 + u;
+      ell_col[o] = c < nc ? (int32_t)c : 0;
+      v64[o] = 0.0;
+      v32[o] = 0.0f;
     }
   }
 }
@@ -254,6 +262,23 @@ ed_status ed_build_ell(ed_sector s, cudaStream_t st) {
   if (rs == ED_OK) rs = ed_dmalloc((void **)&d_pad, (nb + 1) * sizeof(int64_t), st, "ell bounds");
   if (rs == ED_OK) rs = ed_dmalloc((void **)&d_off, (nb + 1) * sizeof(int32_t), st, "ell bounds");
   if (rs == ED_OK) rs = ed_dmalloc((void **)&d_deg, nb * sizeof(int32_t), st, "ell bounds");
+  // run length of every up block: the strings of its last orbital group
+  // (Norb = 1: the whole block); inside a block the index is (slow, run)
+  std::vector<int32_t> run(std::max(nb, 1), 1);
+  {
+    const int norb = s->mp.norb, g = s->mp.nbath + 1;
+    for (int k = 0; k < nb; ++k) {
+      int64_t d = b.offset[k + 1] - b.offset[k];
+      if (norb >= 2) {
+        const int m = b.keys[(size_t)k * norb + norb - 1];
+        d = 1;
+        for (int i = 1; i <= m; ++i) d = d * (g - m + i) / i;
+      }
+      run[k] = (int32_t)std::max<int64_t>(d, 1);
+    }
+  }
+  int32_t *d_run = nullptr;
+  if (rs == ED_OK) rs = ed_dmalloc((void **)&d_run, run.size() * sizeof(int32_t), st, "ell bounds");
   auto h2d = [&](void *dst, const void *src, size_t bytes) {
     if (rs == ED_OK && cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, st) != cudaSuccess)
       rs = ED_ERR_CUDA;
@@ -262,13 +287,14 @@ ed_status ed_build_ell(ed_sector s, cudaStream_t st) {
   h2d(d_pad, s->up_off_pad.data(), (nb + 1) * sizeof(int64_t));
   h2d(d_off, s->ell_off.data(), (nb + 1) * sizeof(int32_t));
   h2d(d_deg, s->ell_deg.data(), nb * sizeof(int32_t));
+  h2d(d_run, run.data(), run.size() * sizeof(int32_t));
   if (rs == ED_OK) {
     int64_t maxw = 1;
     for (int k = 0; k < nb; ++k)
       maxw = std::max<int64_t>(maxw, s->up_off_pad[k + 1] - s->up_off_pad[k]);
     dim3 grid((unsigned)std::min<int64_t>((maxw + 255) / 256, 1024), (unsigned)nb);
     k_fill_ell<<<grid, 256, 0, st>>>(s->bk[0].rowptr, s->bk[0].col, s->bk[0].val, d_blk, d_off,
-                                     d_deg, d_pad, ell_col, ell_v32, ell_v64);
+                                     d_deg, d_pad, d_run, ell_col, ell_v32, ell_v64);
     ed_count_launches(1);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) {
@@ -280,6 +306,7 @@ ed_status ed_build_ell(ed_sector s, cudaStream_t st) {
   ed_dfree(d_pad, st);
   ed_dfree(d_off, st);
   ed_dfree(d_deg, st);
+  ed_dfree(d_run, st);
   if (rs == ED_OK && cudaStreamSynchronize(st) != cudaSuccess) rs = ED_ERR_CUDA;
   if (rs != ED_OK) {
     ed_dfree(ell_col, st);
@@ -419,6 +446,13 @@ __device__ __forceinline__ double block_sum(double x, double *red) {
   return s;
 }
 
+// Slot of column c in a staged row group of ncp = 4 q4 columns: columns are
+// interleaved by c mod 4 (all columns 0 mod 4 first, then 1 mod 4, ...).  The
+// lanes of a warp own consecutive 4-column tiles, so when they all read
+// member u of their tiles (the diagonal, or hops that shift whole runs of
+// columns) they read consecutive 16-byte slots: no bank conflicts.
+__device__ __forceinline__ int stage_pos(int c, int q4) { return (c & 3) * q4 + (c >> 2); }
+
 // One tile: 4 consecutive columns cb..cb+3 x RT rows of the thread's row
 // group.  FULL: all RT rows exist and all 4 columns are inside the block
 // (no predication).  BLK: block-major layout (ELL table, aligned vectors).
@@ -432,10 +466,11 @@ __device__ __forceinline__ void hv_tile(const HvTables<T> &tb, const HvItem &it,
   using VT = typename Tile<T>::V;
   const int64_t stride = tb.stride;
   const int r0 = it.r0, c0 = it.c0, nc = it.nc;
+  const int q4 = (nc + 3) >> 2;
   const int64_t cp0 = it.c0p;
   auto rows_at = [&](int c, T *y) {
     if (staged) {
-      vec_get(*reinterpret_cast<const VT *>(smq + (size_t)c * RT), y);
+      vec_get(*reinterpret_cast<const VT *>(smq + (size_t)stage_pos(c, q4) * RT), y);
     } else {
 #pragma unroll
       for (int i = 0; i < RT; ++i)
@@ -507,15 +542,14 @@ __device__ __forceinline__ void hv_tile(const HvTables<T> &tb, const HvItem &it,
     const int32_t *dc = s_dcol + (lr0 + i) * ED_MAX_NS;
     const T *dv = s_dval + (lr0 + i) * ED_MAX_NS;
     int t = 0;
-    if (BLK && EDGB_DW_UNROLL > 1) {
-      // neighbour loads of EDGB_DW_UNROLL rows issued together
-      for (; t + EDGB_DW_UNROLL <= n; t += EDGB_DW_UNROLL) {
-        T y[EDGB_DW_UNROLL][4];
+    if (BLK) {
+      for (; t + 2 <= n; t += 2) {
+        T y[2][4];
 #pragma unroll
-        for (int q2 = 0; q2 < EDGB_DW_UNROLL; ++q2)
+        for (int q2 = 0; q2 < 2; ++q2)
           load4(g + (int64_t)dc[t + q2] * stride + cp0 + cb, y[q2]);
 #pragma unroll
-        for (int q2 = 0; q2 < EDGB_DW_UNROLL; ++q2) {
+        for (int q2 = 0; q2 < 2; ++q2) {
           const T h = dv[t + q2];
 #pragma unroll
           for (int u = 0; u < 4; ++u) acc[u][i] = fma_t<T>(h, y[q2][u], acc[u][i]);
@@ -582,16 +616,17 @@ __global__ void __launch_bounds__(HV_THREADS, EDGB_MIN_CTAS) k_hv(HvLaunch<T> a)
   const int ncp = (nc + 3) & ~3;
   const int ngroups = (nr + RT - 1) / RT;
   const bool staged = (size_t)ngroups * ncp * RT * sizeof(T) <= tb.smem;
-  // staging, transposed: sm[(q * ncp + c) * RT + i] = v[r0 + q*RT + i][c]
+  // staging, transposed: sm[(q * ncp + stage_pos(c)) * RT + i] = v[r0 + q*RT + i][c]
   if (staged) {
     for (int lr = 0; lr < ngroups * RT; ++lr) {
       const int q = lr / RT, i = lr - q * RT;
       T *dst = sm + (size_t)q * ncp * RT + i;
       if (lr < nr) {
         const T *src = g + (int64_t)(r0 + lr) * stride + cp0;
-        for (int c = threadIdx.x; c < ncp; c += blockDim.x) dst[c * RT] = c < nc ? src[c] : T(0);
+        for (int c = threadIdx.x; c < ncp; c += blockDim.x)
+          dst[stage_pos(c, ncp >> 2) * RT] = c < nc ? src[c] : T(0);
       } else {
-        for (int c = threadIdx.x; c < ncp; c += blockDim.x) dst[c * RT] = T(0);
+        for (int c = threadIdx.x; c < ncp; c += blockDim.x) dst[stage_pos(c, ncp >> 2) * RT] = T(0);
       }
     }
   }
@@ -641,7 +676,7 @@ __global__ void __launch_bounds__(HV_THREADS, EDGB_MIN_CTAS) k_hv(HvLaunch<T> a)
           if (MODE == HV_PLAIN) {
             out[gi] = acc[u][i];
           } else {
-            const T xv = staged ? smq[(size_t)c * RT + i] : g[gi];
+            const T xv = staged ? smq[(size_t)stage_pos(c, ncp >> 2) * RT + i] : g[gi];
             const T v = mul_t<T>(xv, s_cur);
             T w1 = mul_t<T>(acc[u][i], s_cur);
             if (j > 0) w1 = fma_t<T>(-beta_j, mul_t<T>(prev[gi], s_prev), w1);
