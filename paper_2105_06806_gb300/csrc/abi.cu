@@ -52,6 +52,11 @@ ed_status ed_gf_chain_job(ed_sector s, ed_precision prec, const void *d_psi, dou
                           double *host_G, double *weight, int *steps, int64_t *dim,
                           cudaEvent_t after);
 ed_status ed_gf_prepare(ed_sector s, int spin, int create, int elem, cudaStream_t cs);
+bool ed_gf_batchable(ed_sector s, int spin, int create);
+ed_status ed_gf_chain_batch(ed_sector s, ed_precision prec, const void *d_psi, double e0,
+                            int nsteps, double beta, int nmats, int njobs, const int *orb,
+                            const int *spin, const int *create, double *host_G, double *weight,
+                            int *steps, int64_t *dim, cudaStream_t cs);
 
 static double now_s() {
   using namespace std::chrono;
@@ -120,15 +125,40 @@ ed_status ed_solve_impl(const ed_model *model, int nup, int ndw, const ed_solve_
         }
       }
     }
+    // small sectors: every chain in one batched launch on the solve's stream
+    bool batch = rs == ED_OK;
+    for (const Job &j : jobs) batch = batch && ed_gf_batchable(s, j.spin, j.create);
+    if (batch) {
+      const int nj = (int)jobs.size();
+      std::vector<int> jo(nj), js(nj), jc(nj), jsteps(nj);
+      std::vector<double> jw(nj), jG((size_t)nj * 2 * nmats);
+      std::vector<int64_t> jd(nj);
+      for (int q = 0; q < nj; ++q) {
+        jo[q] = jobs[q].orb;
+        js[q] = jobs[q].spin;
+        jc[q] = jobs[q].create;
+      }
+      rs = ed_gf_chain_batch(s, gfp, psi, res->ground.e0, steps, beta, nmats, nj, jo.data(),
+                             js.data(), jc.data(), jG.data(), jw.data(), jsteps.data(), jd.data(),
+                             cs);
+      for (int q = 0; q < nj && rs == ED_OK; ++q) {
+        jobs[q].weight = jw[q];
+        jobs[q].steps = jsteps[q];
+        jobs[q].dim = jd[q];
+        memcpy(jobs[q].G.data(), jG.data() + 2 * (size_t)nmats * q, 2 * sizeof(double) * nmats);
+      }
+    }
     cudaEvent_t ready = nullptr;
-    if (rs == ED_OK && cudaEventCreateWithFlags(&ready, cudaEventDisableTiming) != cudaSuccess)
+    if (rs == ED_OK && !batch &&
+        cudaEventCreateWithFlags(&ready, cudaEventDisableTiming) != cudaSuccess)
       rs = ED_ERR_CUDA;
-    if (rs == ED_OK && cudaEventRecord(ready, cs) != cudaSuccess) rs = ED_ERR_CUDA;
+    if (rs == ED_OK && !batch && cudaEventRecord(ready, cs) != cudaSuccess) rs = ED_ERR_CUDA;
     int dev = 0;
     cudaGetDevice(&dev);
-    // chains run concurrently, at most kMaxChains at a time
+    // larger sectors: chains run concurrently on their own streams, at most
+    // kMaxChains at a time
     const size_t kMaxChains = 8;
-    for (size_t b = 0; rs == ED_OK && b < jobs.size(); b += kMaxChains) {
+    for (size_t b = 0; rs == ED_OK && !batch && b < jobs.size(); b += kMaxChains) {
       std::vector<std::thread> th;
       for (size_t k = b; k < std::min(jobs.size(), b + kMaxChains); ++k) {
         th.emplace_back([&, k] {

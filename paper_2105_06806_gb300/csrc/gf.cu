@@ -87,19 +87,222 @@ __global__ void k_cfrac(const LanczosState *st, double weight, double e0, double
   double fr = zr - st->alpha[k - 1], fi = zi;
   for (int m = k - 2; m >= 0; --m) {
     const double b2 = st->beta[m + 1] * st->beta[m + 1];
-    const double den = fr * fr + fi * fi;
-    // b2 / f = b2 * conj(f) / |f|^2
-    const double qr = b2 * fr / den, qi = -b2 * fi / den;
+    // b2 / f = b2 * conj(f) / |f|^2 (one FP64 division per level)
+    const double inv = 1.0 / (fr * fr + fi * fi);
+    const double qr = b2 * fr * inv, qi = -b2 * fi * inv;
     fr = zr - st->alpha[m] - qr;
     fi = zi - qi;
   }
-  const double den = fr * fr + fi * fi;
-  const double gr = weight * fr / den, gi = -weight * fi / den;
+  const double inv = 1.0 / (fr * fr + fi * fi);
+  const double gr = weight * fr * inv, gi = -weight * fi * inv;
   G[n].x += sgn * gr;
   G[n].y += sgn * gi;
 }
 
 static size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// ----------------------------------------------------------------- batched chains
+//
+// All chains of a solve whose sectors are small run in one persistent launch:
+// each CTA takes a chain from a device counter and runs it to the end alone
+// (start vector c^+-|gs>, nsteps of the recurrence of lanczos.cu with the
+// element-parallel product, FP64 scalars), so a chain costs one CTA and no
+// host round trip.  The chains of a solve have different lengths (the
+// c^+ and c sectors differ in dimension); a CTA that finishes takes the next.
+// v_j is staged in shared memory every step, so every gather of the product
+// is a shared-memory load.
+constexpr int CHAIN_THREADS = 1024;
+// padded elements of a batched chain's sector (FP64: 128 KB of shared memory)
+constexpr int64_t CHAIN_MAX_DIM = 1 << 14;
+
+template <typename Ti, typename To>
+struct ChainTask {
+  HvTables<To> tb;     // target sector, block-major, element-parallel form
+  ApplyArgs a;         // start vector gather
+  const Ti *psi;       // ground state, sector order
+  To *b0, *b1, *b2;    // three vectors of a.dst_dim elements
+  LanczosState *st;    // output: alpha, beta, j, acc[0] = ||phi||^2
+  int nsteps;
+};
+
+// Sum over the CTA, the same value in every thread, fixed order: lanes in
+// the vector type (FP64 is the slow pipe), the 32 warp sums in FP64.
+template <typename T>
+__device__ double chain_allsum(T x, double *red) {
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) red[wid] = (double)x;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += red[k];
+    red[32] = t;
+  }
+  __syncthreads();
+  const double r = red[32];
+  __syncthreads();
+  return r;
+}
+
+template <typename T>
+__device__ __forceinline__ T ch_fma(T a, T b, T c);
+template <>
+__device__ __forceinline__ float ch_fma<float>(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+template <>
+__device__ __forceinline__ double ch_fma<double>(double a, double b, double c) { return __fma_rn(a, b, c); }
+
+template <typename Ti, typename To>
+__global__ void __launch_bounds__(CHAIN_THREADS) k_chain_batch(const ChainTask<Ti, To> *tasks,
+                                                               int ntasks, int *next) {
+  extern __shared__ __align__(16) unsigned char chain_smem[];
+  To *S = reinterpret_cast<To *>(chain_smem);  // v_j (unscaled) of the current step
+  __shared__ double red[33];
+  __shared__ double s_scal[2];
+  __shared__ int s_task, s_done;
+  for (;;) {
+    if (threadIdx.x == 0) s_task = atomicAdd(next, 1);
+    __syncthreads();
+    const int t = s_task;
+    __syncthreads();
+    if (t >= ntasks) return;
+    const ChainTask<Ti, To> &tk = tasks[t];
+    const HvTables<To> &tb = tk.tb;
+    const ApplyArgs &a = tk.a;
+    const int64_t n = a.dst_dim, stride = a.dst_stride;
+    const float inv_stride = 1.0f / (float)stride;
+    To *bufs[3] = {tk.b0, tk.b1, tk.b2};
+    // start vector into b0 (the gather of k_apply_op), b1 = b2 = 0
+    double sq = 0.0;
+    {
+      const uint32_t bit = 1u << a.level, below = bit - 1u;
+      for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+        // exact row index: (i + 1/2) / stride lies 1/(2 stride) from an integer
+        const int64_t r2 = __float2int_rz(((float)i + 0.5f) * inv_stride);
+        const int32_t c2 = a.dst_padinv[i - r2 * stride];
+        To out = To(0);
+        const uint32_t I2 = c2 < 0 ? 0u : a.dst_map[a.spin == 0 ? (int64_t)c2 : r2];
+        if (c2 >= 0 && ((I2 & bit) != 0u) == (a.create > 0)) {
+          const uint32_t I = I2 ^ bit;
+          const int64_t src_idx = ed_rank(I);
+          int parity = __popc(I & below);
+          if (a.spin == 1) parity += a.nup_src;
+          const int64_t r = a.spin == 0 ? (int64_t)a.dst_pother[r2] : src_idx;
+          const int64_t c = a.spin == 0 ? src_idx : (int64_t)a.dst_pother[c2];
+          const Ti x = tk.psi[r * a.src_dup + c];
+          out = (To)((parity & 1) ? -x : x);
+        }
+        tk.b0[i] = out;
+        tk.b1[i] = To(0);
+        tk.b2[i] = To(0);
+        sq += (double)out * (double)out;
+      }
+    }
+    const double weight = chain_allsum<double>(sq, red);
+    LanczosState *st = tk.st;
+    double scale[3] = {weight > 0.0 ? 1.0 / sqrt(weight) : 0.0, 0.0, 0.0};
+    double beta_j = 0.0, tnorm = 0.0;
+    int j = 0, done = weight > 0.0 ? 0 : 2;
+    if (threadIdx.x == 0) {
+      st->acc[0] = weight;
+      st->beta[0] = 0.0;
+    }
+    while (!done) {
+      const To *g = bufs[j % 3];
+      const To *prev = bufs[(j + 2) % 3];
+      To *out = bufs[(j + 1) % 3];
+      const To s_cur = (To)scale[j % 3], s_prev = (To)scale[(j + 2) % 3];
+      const To bj = (To)beta_j;
+      for (int64_t i = threadIdx.x; i < n; i += blockDim.x) S[i] = g[i];
+      __syncthreads();
+      // w1 = H v_j - beta_j v_{j-1} (padding columns are skipped: they stay 0)
+      To dot = To(0);  // per-thread partials in the vector type; FP64 across warps
+      for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+        const int64_t r = __float2int_rz(((float)i + 0.5f) * inv_stride);
+        const int pc = (int)(i - r * stride);
+        const int4 ci = __ldg(tb.small_cols + pc);
+        if (ci.x < 0) continue;
+        const To x = S[i];
+        const To *row = S + r * stride + ci.z;
+        const int deg = ci.w & 255, ncp = ci.w >> 8;
+        const int mu = (int)tb.m_up[ci.x] * tb.nmask;
+        To acc = (tb.e_up[ci.x] + tb.e_dw[r] + tb.W[mu + tb.m_dw[r]]) * x;
+        for (int e = 0; e < deg; ++e) {
+          const int o = ci.y + e * ncp;
+          acc = ch_fma<To>(__ldg(tb.ell_val + o), row[__ldg(tb.ell_col + o)], acc);
+        }
+        const int32_t d0 = __ldg(tb.rp_dw + r), d1 = __ldg(tb.rp_dw + r + 1);
+        for (int32_t k = d0; k < d1; ++k)
+          acc = ch_fma<To>(__ldg(tb.val_dw + k), S[(int64_t)__ldg(tb.col_dw + k) * stride + pc], acc);
+        const To v = x * s_cur;
+        To w1 = acc * s_cur;
+        if (j > 0) w1 = ch_fma<To>(-bj, prev[i] * s_prev, w1);
+        out[i] = w1;
+        dot = ch_fma<To>(v, w1, dot);
+      }
+      const double al = chain_allsum<To>(dot, red);
+      // w = w1 - alpha_j v_j, ||w||^2
+      const To alT = (To)al;
+      To ss = To(0);
+      for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+        const To w = ch_fma<To>(-alT, S[i] * s_cur, out[i]);
+        out[i] = w;
+        ss = ch_fma<To>(w, w, ss);
+      }
+      const double ss_tot = chain_allsum<To>(ss, red);
+      // scalar bookkeeping once, by thread 0
+      if (threadIdx.x == 0) {
+        const double be = sqrt(fmax(ss_tot, 0.0));
+        tnorm = fmax(tnorm, fmax(fabs(al), be));
+        st->alpha[j] = al;
+        st->beta[j + 1] = be;
+        s_scal[0] = be;
+        s_scal[1] = be > 0.0 ? 1.0 / be : 0.0;
+        s_done = be <= 1e-13 * tnorm ? 2 : (j + 1 >= tk.nsteps ? 3 : 0);
+      }
+      __syncthreads();
+      beta_j = s_scal[0];
+      scale[(j + 1) % 3] = s_scal[1];
+      done = s_done;
+      ++j;
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+      st->j = j;
+      st->done = done;
+    }
+    __syncthreads();
+  }
+}
+
+// Continued fractions of a batch of chains (grid.y = chain): the arithmetic
+// of k_cfrac, with the weight ||phi||^2 read from the chain's state.
+__global__ void k_cfrac_batch(const LanczosState *const *sts, const int *sgns, double e0,
+                              double beta, int nmats, double2 *G) {
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  const int c = blockIdx.y;
+  if (n >= nmats) return;
+  const LanczosState *st = sts[c];
+  const int k = st->j;
+  const double weight = st->acc[0];
+  double2 out = make_double2(0.0, 0.0);
+  if (k > 0 && weight != 0.0) {
+    const int sgn = sgns[c];
+    const double wn = (2.0 * n + 1.0) * M_PI / beta;
+    const double zr = e0, zi = sgn * wn;
+    double fr = zr - st->alpha[k - 1], fi = zi;
+    for (int m = k - 2; m >= 0; --m) {
+      const double b2 = st->beta[m + 1] * st->beta[m + 1];
+      const double inv = 1.0 / (fr * fr + fi * fi);
+      const double qr = b2 * fr * inv, qi = -b2 * fi * inv;
+      fr = zr - st->alpha[m] - qr;
+      fi = zi - qi;
+    }
+    const double inv = 1.0 / (fr * fr + fi * fi);
+    out.x = sgn * (weight * fr * inv);
+    out.y = sgn * (-weight * fi * inv);
+  }
+  G[(size_t)c * nmats + n] = out;
+}
 
 template <typename Ti, typename To>
 static ed_status one_chain(ed_sector s, const Ti *psi, int orb, int spin, int create, int nsteps,
@@ -166,7 +369,8 @@ static ed_status one_chain(ed_sector s, const Ti *psi, int orb, int spin, int cr
     }
   }
   if (rs == ED_OK && hw[0] > 0.0 && nmats > 0) {
-    k_cfrac<<<(nmats + 127) / 128, 128, 0, cs>>>(st, hw[0], e0, beta, nmats, create, dG);
+    // 32 frequencies per CTA: the FP64 recurrences spread over many SMs
+    k_cfrac<<<(nmats + 31) / 32, 32, 0, cs>>>(st, hw[0], e0, beta, nmats, create, dG);
     ed_count_launches(1);
     if (cudaGetLastError() != cudaSuccess) rs = ED_ERR_CUDA;
   }
@@ -270,6 +474,154 @@ ed_status ed_gf_prepare(ed_sector s, int spin, int create, int elem, cudaStream_
   ED_TRY(ed_neighbor_sector(s, spin, create, cs, &nb));
   if (nb && nb->dim > 0) ED_TRY(ed_build_items(nb, 1, elem));
   return ED_OK;
+}
+
+// True when the chain of (spin, create) can run in the batched launch: its
+// sector exists, has the element-parallel tables and at most CHAIN_MAX_DIM
+// padded elements (ed_gf_prepare must have run).
+bool ed_gf_batchable(ed_sector s, int spin, int create) {
+  const ed_sector nb = s->nb[spin][create > 0 ? 1 : 0];
+  if (!nb || nb->dim == 0) return true;  // an empty chain
+  return nb->bdim <= CHAIN_MAX_DIM && nb->small_cols != nullptr;
+}
+
+template <typename Ti, typename To>
+static ed_status chain_batch(ed_sector s, const Ti *psi, double e0, int nsteps, double beta,
+                             int nmats, int njobs, const int *orb, const int *spin,
+                             const int *create, double *host_G, double *weight, int *steps,
+                             int64_t *dim, cudaStream_t cs) {
+  std::vector<ChainTask<Ti, To>> tasks;
+  std::vector<int> job_of, sgn;
+  std::vector<size_t> off;
+  size_t bytes = 0;
+  for (int q = 0; q < njobs; ++q) {
+    weight[q] = 0.0;
+    steps[q] = 0;
+    dim[q] = 0;
+    if (nmats > 0) memset(host_G + 2 * (size_t)nmats * q, 0, 2 * sizeof(double) * nmats);
+    const ed_sector nb = s->nb[spin[q]][create[q] > 0 ? 1 : 0];
+    if (!nb || nb->dim == 0) continue;
+    dim[q] = nb->dim;
+    if (!nb->small_cols || nb->bdim > CHAIN_MAX_DIM) return ED_ERR_UNSUPPORTED;
+    ChainTask<Ti, To> t;
+    memset(&t, 0, sizeof(t));
+    t.tb = ed_hv_tables<To>(nb, 1);
+    t.a.dst_map = nb->bk[spin[q]].map;
+    t.a.dst_pother = nb->bi[1 - spin[q]].pidx;
+    t.a.dst_padinv = nb->padinv;
+    t.a.dst_stride = nb->bstride;
+    t.a.dst_dim = nb->bdim;
+    t.a.src_dup = s->sp[0].dim;
+    t.a.level = orb[q];  // impurity orbital alpha is level alpha
+    t.a.create = create[q];
+    t.a.spin = spin[q];
+    t.a.nup_src = s->nup;
+    t.psi = psi;
+    t.nsteps = nsteps;
+    off.push_back(bytes);
+    bytes += 3 * al256(nb->bdim * sizeof(To)) + al256(sizeof(LanczosState));
+    tasks.push_back(t);
+    job_of.push_back(q);
+    sgn.push_back(create[q]);
+  }
+  const int nt = (int)tasks.size();
+  if (nt == 0) return ED_OK;
+  const size_t o_tasks = bytes, o_sts = o_tasks + al256(nt * sizeof(ChainTask<Ti, To>));
+  const size_t o_sgn = o_sts + al256(nt * sizeof(LanczosState *));
+  const size_t o_G = o_sgn + al256(nt * sizeof(int));
+  const size_t o_next = o_G + al256((size_t)nt * std::max(nmats, 1) * sizeof(double2));
+  void *mem = nullptr;
+  ED_TRY(ed_dmalloc(&mem, o_next + 256, cs, "batched chains"));
+  char *base = (char *)mem;
+  std::vector<LanczosState *> sts(nt);
+  int64_t nmax = 0;
+  for (int i = 0; i < nt; ++i) {
+    char *p = base + off[i];
+    const size_t vb = al256(tasks[i].a.dst_dim * sizeof(To));
+    tasks[i].b0 = (To *)p;
+    tasks[i].b1 = (To *)(p + vb);
+    tasks[i].b2 = (To *)(p + 2 * vb);
+    tasks[i].st = sts[i] = (LanczosState *)(p + 3 * vb);
+    nmax = std::max<int64_t>(nmax, tasks[i].a.dst_dim);
+  }
+  ed_status rs = ED_OK;
+  auto h2d = [&](size_t o, const void *src, size_t n) {
+    if (rs == ED_OK && cudaMemcpyAsync(base + o, src, n, cudaMemcpyHostToDevice, cs) != cudaSuccess)
+      rs = ED_ERR_CUDA;
+  };
+  h2d(o_tasks, tasks.data(), nt * sizeof(ChainTask<Ti, To>));
+  h2d(o_sts, sts.data(), nt * sizeof(LanczosState *));
+  h2d(o_sgn, sgn.data(), nt * sizeof(int));
+  if (rs == ED_OK && cudaMemsetAsync(base + o_next, 0, sizeof(int), cs) != cudaSuccess) rs = ED_ERR_CUDA;
+  if (rs == ED_OK && cudaFuncSetAttribute(k_chain_batch<Ti, To>,
+                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)(CHAIN_MAX_DIM * sizeof(To))) != cudaSuccess)
+    rs = ED_ERR_CUDA;
+  if (rs == ED_OK) {
+    k_chain_batch<Ti, To><<<(unsigned)std::min(nt, 2 * 152), CHAIN_THREADS,
+                            (size_t)nmax * sizeof(To), cs>>>(
+        (const ChainTask<Ti, To> *)(base + o_tasks), nt, (int *)(base + o_next));
+    ed_count_launches(1);
+    if (nmats > 0) {
+      k_cfrac_batch<<<dim3((nmats + 31) / 32, nt), 32, 0, cs>>>(
+          (const LanczosState *const *)(base + o_sts), (const int *)(base + o_sgn), e0, beta, nmats,
+          (double2 *)(base + o_G));
+      ed_count_launches(1);
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+      ed_set_cuda_error(e, "batched chains launch", __FILE__, __LINE__);
+      rs = ED_ERR_CUDA;
+    }
+  }
+  std::vector<double> G((size_t)nt * 2 * std::max(nmats, 0));
+  std::vector<int32_t> hj(nt, 0);
+  std::vector<double> hw(nt, 0.0);
+  if (rs == ED_OK && nmats > 0 &&
+      cudaMemcpyAsync(G.data(), base + o_G, G.size() * sizeof(double), cudaMemcpyDeviceToHost,
+                      cs) != cudaSuccess)
+    rs = ED_ERR_CUDA;
+  for (int i = 0; i < nt && rs == ED_OK; ++i) {
+    if (cudaMemcpyAsync(&hj[i], &sts[i]->j, sizeof(int32_t), cudaMemcpyDeviceToHost, cs) !=
+            cudaSuccess ||
+        cudaMemcpyAsync(&hw[i], &sts[i]->acc[0], sizeof(double), cudaMemcpyDeviceToHost, cs) !=
+            cudaSuccess)
+      rs = ED_ERR_CUDA;
+  }
+  cudaError_t e = cudaStreamSynchronize(cs);
+  if (rs == ED_OK && e != cudaSuccess) {
+    ed_set_cuda_error(e, "batched chains", __FILE__, __LINE__);
+    rs = ED_ERR_CUDA;
+  }
+  ed_dfree(mem, cs);
+  if (rs != ED_OK) return rs;
+  for (int i = 0; i < nt; ++i) {
+    const int q = job_of[i];
+    weight[q] = hw[i];
+    steps[q] = hj[i];
+    if (nmats > 0)
+      memcpy(host_G + 2 * (size_t)nmats * q, G.data() + 2 * (size_t)nmats * i,
+             2 * sizeof(double) * nmats);
+  }
+  return ED_OK;
+}
+
+// The chains of a solve in one batched launch (see k_chain_batch); per job q:
+// host_G[q] (2 * nmats doubles, overwritten), weight, steps and the
+// dimension of its sector.  ED_ERR_UNSUPPORTED when a chain is not batchable.
+ed_status ed_gf_chain_batch(ed_sector s, ed_precision prec, const void *d_psi, double e0,
+                            int nsteps, double beta, int nmats, int njobs, const int *orb,
+                            const int *spin, const int *create, double *host_G, double *weight,
+                            int *steps, int64_t *dim, cudaStream_t cs) {
+  if (nsteps <= 0 || nsteps > ED_MAX_LANCZOS) return ED_ERR_ARG;
+  if (prec == ED_FP64)
+    return chain_batch<double, double>(s, (const double *)d_psi, e0, nsteps, beta, nmats, njobs, orb,
+                                       spin, create, host_G, weight, steps, dim, cs);
+  if (prec == ED_FP32)
+    return chain_batch<float, float>(s, (const float *)d_psi, e0, nsteps, beta, nmats, njobs, orb,
+                                     spin, create, host_G, weight, steps, dim, cs);
+  return chain_batch<double, float>(s, (const double *)d_psi, e0, nsteps, beta, nmats, njobs, orb,
+                                    spin, create, host_G, weight, steps, dim, cs);
 }
 
 extern "C" ed_status ed_gf_lanczos(ed_sector s, ed_precision prec, const void *d_psi, double e0,

@@ -183,55 +183,55 @@ __device__ void stage_tridiag(const LanczosState *st, int k, double *a, double *
   __syncthreads();
 }
 
-// Lowest eigenvalue of T_k by multisection: every thread evaluates the Sturm
-// count at one interior point; the bracket shrinks by blockDim+1 per round.
+// Lowest eigenvalue of T_k by multisection on one warp: each of the 32 lanes
+// evaluates the Sturm count at one interior point, the bracket shrinks by 33
+// per round.  (FP64 is the slow pipe on this part: 32 counts per round cost
+// far less than a CTA-wide section, at a few more rounds.)  Called by the
+// whole CTA; the result is returned to every thread.
 __device__ double lowest_eigenvalue(const double *a, const double *b, const double *b2, int k,
                                     double hint_hi, double hint_lo) {
-  __shared__ int first;
-  __shared__ double blo, bhi;
-  if (threadIdx.x == 0) {
+  __shared__ double s_theta;
+  if (threadIdx.x < 32) {
+    const int lane = threadIdx.x;
+    const unsigned full = 0xffffffffu;
+    // Gershgorin bracket
     double lo = 1e300, hi = -1e300;
-    for (int i = 0; i < k; ++i) {
-      double rad = (i > 0 ? fabs(b[i]) : 0.0) + (i + 1 < k ? fabs(b[i + 1]) : 0.0);
+    for (int i = lane; i < k; i += 32) {
+      const double rad = (i > 0 ? fabs(b[i]) : 0.0) + (i + 1 < k ? fabs(b[i + 1]) : 0.0);
       lo = fmin(lo, a[i] - rad);
       hi = fmax(hi, a[i] + rad);
     }
-    blo = lo;
-    bhi = hi;
+    for (int o = 16; o > 0; o >>= 1) {
+      lo = fmin(lo, __shfl_xor_sync(full, lo, o));
+      hi = fmax(hi, __shfl_xor_sync(full, hi, o));
+    }
+    // warm bracket [hint_lo, hint_hi] when it provably contains the minimum
+    if (hint_hi < hi && hint_lo > lo && hint_lo < hint_hi) {
+      int c = 0;
+      if (lane == 0) c = sturm_count(a, b2, k, hint_lo) == 0;
+      if (lane == 1) c = sturm_count(a, b2, k, hint_hi) >= 1;
+      const int c0 = __shfl_sync(full, c, 0), c1 = __shfl_sync(full, c, 1);
+      if (c0 && c1) {
+        lo = hint_lo;
+        hi = hint_hi;
+      }
+    }
+    for (int round = 0; round < 128; ++round) {
+      if (!(hi - lo > 4e-16 * fmax(1.0, fmax(fabs(lo), fabs(hi))))) break;
+      const double x = lo + (hi - lo) * (double)(lane + 1) / 33.0;
+      const bool below = x > lo && x < hi && sturm_count(a, b2, k, x) >= 1;
+      const unsigned m = __ballot_sync(full, below);
+      const int f = m ? __ffs(m) - 1 : 32;
+      const double nlo = f == 0 ? lo : lo + (hi - lo) * (double)f / 33.0;
+      double nhi = f == 32 ? hi : lo + (hi - lo) * (double)(f + 1) / 33.0;
+      if (nlo == lo && nhi == hi) nhi = lo;  // no progress possible: stop
+      lo = nlo;
+      hi = fmax(nhi, nlo);
+    }
+    if (lane == 0) s_theta = 0.5 * (lo + hi);
   }
   __syncthreads();
-  // warm bracket [hint_lo, hint_hi] when it provably contains the minimum
-  if (hint_hi < bhi && hint_lo > blo && hint_lo < hint_hi) {
-    __shared__ int ok;
-    if (threadIdx.x == 0)
-      ok = (sturm_count(a, b2, k, hint_lo) == 0 && sturm_count(a, b2, k, hint_hi) >= 1);
-    __syncthreads();
-    if (ok && threadIdx.x == 0) {
-      blo = hint_lo;
-      bhi = hint_hi;
-    }
-    __syncthreads();
-  }
-  const int T = blockDim.x;
-  for (int round = 0; round < 64; ++round) {
-    double lo = blo, hi = bhi;
-    if (!(hi - lo > 4e-16 * fmax(1.0, fmax(fabs(lo), fabs(hi))))) break;
-    if (threadIdx.x == 0) first = T;
-    __syncthreads();
-    double x = lo + (hi - lo) * (double)(threadIdx.x + 1) / (double)(T + 1);
-    if (x > lo && x < hi && sturm_count(a, b2, k, x) >= 1) atomicMin(&first, (int)threadIdx.x);
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      int f = first;
-      double nlo = f == 0 ? lo : lo + (hi - lo) * (double)f / (double)(T + 1);
-      double nhi = f == T ? hi : lo + (hi - lo) * (double)(f + 1) / (double)(T + 1);
-      if (nlo == lo && nhi == hi) nhi = lo;  // no progress possible: stop
-      blo = nlo;
-      bhi = fmax(nhi, nlo);
-    }
-    __syncthreads();
-  }
-  double th = 0.5 * (blo + bhi);
+  const double th = s_theta;
   __syncthreads();
   return th;
 }
@@ -282,12 +282,15 @@ __global__ void k_beta(LanczosState *st, const double *part, int64_t nparts) {
   // T_k, its squared off-diagonal, then (inverse iteration) pivots and y
   __shared__ double s_a[ED_MAX_LANCZOS], s_b[ED_MAX_LANCZOS], s_b2[ED_MAX_LANCZOS];
   __shared__ double s_rp[ED_MAX_LANCZOS], s_y[ED_MAX_LANCZOS];
+  __shared__ double s_be, s_hint[2];
   if (st->done) return;
   double s2 = cta_sum_parts(part, nparts, red);
   const int j = st->j;
-  const double al = st->alpha[j];
-  const double be = sqrt(fmax(s2, 0.0));
+  // scalar work once, by thread 0 (FP64 is the slow pipe)
   if (threadIdx.x == 0) {
+    const double al = st->alpha[j];
+    const double be = sqrt(fmax(s2, 0.0));
+    s_be = be;
     st->beta[j + 1] = be;
     st->scale[(j + 1) % 3] = be > 0.0 ? 1.0 / be : 0.0;
     st->tnorm = fmax(st->tnorm, fmax(fabs(al), be));
@@ -300,19 +303,26 @@ __global__ void k_beta(LanczosState *st, const double *part, int64_t nparts) {
   const bool want = st->tol > 0.0 && (stop != 0 || (k % st->check_every) == 0 || k <= 2);
   if (want) {
     stage_tridiag(st, k, s_a, s_b, s_b2);
-    double prev = st->theta;
-    double hi = (k > 1 && isfinite(prev)) ? prev : 1e300;
-    double dl = isfinite(st->acc[3]) ? fabs(st->acc[3]) : 0.0;
-    double lo = (k > 1 && isfinite(prev)) ? prev - fmax(8.0 * dl, 1e-9 * fmax(1.0, fabs(prev))) : -1e300;
-    double th = lowest_eigenvalue(s_a, s_b, s_b2, k, hi, lo);
+    const double prev = st->theta;
+    if (threadIdx.x == 0) {
+      const double dl = isfinite(st->acc[3]) ? fabs(st->acc[3]) : 0.0;
+      s_hint[0] = (k > 1 && isfinite(prev)) ? prev : 1e300;
+      s_hint[1] = (k > 1 && isfinite(prev)) ? prev - fmax(8.0 * dl, 1e-9 * fmax(1.0, fabs(prev)))
+                                             : -1e300;
+    }
+    __syncthreads();
+    const double th = lowest_eigenvalue(s_a, s_b, s_b2, k, s_hint[0], s_hint[1]);
     __shared__ int ritz;
     if (threadIdx.x == 0) {
+      const double be = s_be;
       double y2 = last_component_sq(s_a, s_b2, k, th);
       double rest = be * sqrt(y2);
       // The polynomial formula loses relative accuracy once the Ritz value
       // has converged; near convergence use inverse iteration instead.
       ritz = rest < 1e-6 * fmax(1.0, fabs(th));
       if (ritz) {
+        // the last component is tiny near convergence: three sweeps push the
+        // other eigencomponents well below it
         ritz_vector(s_a, s_b, k, th, 3, s_rp, s_b2, s_y);
         rest = be * fabs(s_y[k - 1]);
       }
@@ -753,7 +763,9 @@ static ed_status lanczos_solve(ed_sector s, int maxit, double tol, uint64_t seed
     ed_set_error_msg("page-locked stop flag allocation failed");
     return ED_ERR_OOM;
   }
-  const int check_every = n > (1 << 22) ? 1 : 4;
+  // Ritz-value tests cost FP64 latency on one warp: below 2^20 elements a
+  // Lanczos step is cheaper than a test, so test every 8 steps there
+  const int check_every = n > (1 << 22) ? 1 : (n > (1 << 20) ? 4 : 8);
   auto init = [&]() -> ed_status {
     if (start) {
       ED_TRY_CUDA(cudaMemcpyAsync(bufs[0], start, n * sizeof(T), cudaMemcpyDeviceToDevice, cs));

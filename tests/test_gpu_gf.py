@@ -113,6 +113,32 @@ def test_gf_multiorbital_asymmetric_sector(ed, spin):
     s.free()
 
 
+@pytest.mark.parametrize("gprec", ["fp64", "fp32"])
+def test_solve_batched_chains_against_oracle(ed, gprec):
+    """ed_solve on small sectors runs every chain of the solve in one batched
+    launch (one CTA per chain): Norb=2, N_up != N_dw, spin-dependent bath, so
+    the eight chains live in four sectors of different dimension.  Every
+    G_{orb,spin} against the oracle chains, and the same G twice."""
+    m = make_model(2, 3, U=2.4, Jh=0.4, seed=23)
+    m.e_bath[1] += 0.1
+    nup, ndw = 4, 3
+    ref = fock.Sector(m, nup, ndw)
+    ro = lanczos.ground_state(ref.matvec, ref.dim)
+    prec = "fp64" if gprec == "fp64" else "fp32_polish"
+    res, G = ed.solve(m, nup, ndw, precision=prec, gf_precision=gprec, nmats=64, beta=100.0,
+                      gf_steps=120)
+    assert abs(res["e0"] - ro["e0"]) < 1e-10 * abs(ro["e0"])
+    assert res["gf_chains"] == 8
+    tol = 1e-8 if gprec == "fp64" else 1e-5
+    for spin in range(2):
+        for orb in range(2):
+            Go = gf.impurity_gf(m, nup, ndw, ro["psi"], ro["e0"], orb, spin, nsteps=120, nmats=64)
+            assert np.abs(G[spin, orb] - Go).max() <= tol, (orb, spin)
+    _, G2 = ed.solve(m, nup, ndw, precision=prec, gf_precision=gprec, nmats=64, beta=100.0,
+                     gf_steps=120)
+    assert np.array_equal(G, G2)
+
+
 def test_gf_u0_closed_form(ed):
     m = make_model(1, 5, U=0.0, e_d=0.07, seed=31)
     s = ed.Sector(m, 3, 3)
