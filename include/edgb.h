@@ -183,7 +183,12 @@ typedef struct {
   uint64_t seed;         /* start vector: v0_i = u_i - 1/2, u_i = SplitMix64(seed)
                             output i, sector order, then normalised               */
   int32_t polish_steps;  /* FP64 Lanczos steps of ED_FP32_POLISH (0: 4)          */
-  int32_t want_vector;   /* 1: second pass, psi and its FP64 residual            */
+  int32_t want_vector;   /* 1: psi and its FP64 residual                         */
+  int32_t basis_mib;     /* Krylov basis kept on the device during the first
+                            pass, so that psi needs no second pass: 0 = up to
+                            40% of the free device memory, > 0 = at most this
+                            many MiB, -1 = none (always the second pass)      */
+  int32_t reserved;      /* 0                                                    */
 } ed_lanczos_opts;
 
 typedef struct {
@@ -199,7 +204,10 @@ typedef struct {
 
 /* Lanczos ground state of the sector (Sec. 6.6): plain Lanczos, Paige form,
  * no re-orthogonalisation; lowest eigenpair of the tridiagonal matrix by
- * Sturm multisection (FP64); second pass to form psi = sum_j y_j v_j.
+ * Sturm multisection (FP64); psi = sum_j y_j v_j from the Krylov basis kept
+ * during the first pass when it fits the basis_mib budget, else from the
+ * paper's second pass (the same recurrence run again); both give the same
+ * psi, bit for bit.
  * d_psi (nullable, requires want_vector) receives psi, normalised, in
  * sector order: double for ED_FP64 / ED_FP32_POLISH, float for ED_FP32.
  * Work vectors are allocated stream-ordered on the device and released

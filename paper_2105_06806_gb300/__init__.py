@@ -70,7 +70,8 @@ class ed_sector_info(C.Structure):
 
 class ed_lanczos_opts(C.Structure):
     _fields_ = [("precision", C.c_int), ("max_iter", C.c_int32), ("tol", C.c_double),
-                ("seed", C.c_uint64), ("polish_steps", C.c_int32), ("want_vector", C.c_int32)]
+                ("seed", C.c_uint64), ("polish_steps", C.c_int32), ("want_vector", C.c_int32),
+                ("basis_mib", C.c_int32), ("reserved", C.c_int32)]
 
 
 class ed_lanczos_result(C.Structure):
@@ -325,10 +326,11 @@ def residual_noalloc(sector: Sector, psi, stream=None):
 
 
 def lanczos_ground(sector: Sector, precision="fp64", max_iter=0, tol=0.0, seed=0x5EED,
-                   polish_steps=0, psi=None, want_vector=None, stream=None, allow_maxit=False):
+                   polish_steps=0, psi=None, want_vector=None, stream=None, allow_maxit=False,
+                   basis_mib=0):
     o = ed_lanczos_opts(_prec(precision), int(max_iter), float(tol), int(seed),
                         int(polish_steps), int(bool(psi is not None) if want_vector is None
-                                               else bool(want_vector)))
+                                               else bool(want_vector)), int(basis_mib), 0)
     r = ed_lanczos_result()
     st = lib().ed_lanczos_ground(sector.h, C.byref(o), C.byref(r),
                                  C.c_void_p(psi.data_ptr() if psi is not None else 0),
@@ -351,11 +353,11 @@ def gf_lanczos(sector: Sector, psi, e0, orb, spin, precision="fp64", nsteps=200,
 
 
 def solve_opts(precision="fp32_polish", gf_precision=None, nmats=512, beta=100.0,
-               gf_steps=200, max_iter=0, tol=0.0, seed=0x5EED, polish_steps=0):
+               gf_steps=200, max_iter=0, tol=0.0, seed=0x5EED, polish_steps=0, basis_mib=0):
     p = _prec(precision)
     gp = _prec(gf_precision) if gf_precision is not None else (FP64 if p == FP64 else FP32)
     return ed_solve_opts(ed_lanczos_opts(p, int(max_iter), float(tol), int(seed),
-                                         int(polish_steps), 0),
+                                         int(polish_steps), 0, int(basis_mib), 0),
                          int(gf_steps), int(nmats), float(beta), gp)
 
 

@@ -298,7 +298,8 @@ enum { HV_PLAIN = 0, HV_LANCZOS = 1, HV_SECOND = 2 };
 template <typename T>
 ed_status ed_launch_hv(ed_sector s, const HvTables<T> &tb, int mode, const T *v, T *w,
                        T *const *bufs, T *psi, LanczosState *state, double *part,
-                       int64_t *nparts, cudaStream_t st);
+                       int64_t *nparts, cudaStream_t st,
+                       T *const *basis = nullptr);
 
 int64_t ed_hv_num_parts(ed_sector s, int layout, int elem_size);
 template <typename T>

@@ -247,13 +247,14 @@ __global__ void k_alpha(LanczosState *st, const double *part, const int64_t npar
 
 template <typename T>
 __global__ void __launch_bounds__(AXPY_THREADS) k_axpy_norm(LanczosState *st, T *b0, T *b1, T *b2,
-                                                            int64_t n, double *part) {
+                                                            T *const *basis, int64_t n,
+                                                            double *part) {
   __shared__ double red[AXPY_THREADS / 32];
   if (st->done) return;
   const int j = st->j;
   T *bufs[3] = {b0, b1, b2};
-  const T *v = bufs[j % 3];
-  T *w = bufs[(j + 1) % 3];
+  const T *v = basis ? basis[j] : bufs[j % 3];
+  T *w = basis ? basis[j + 1] : bufs[(j + 1) % 3];
   const T s = (T)st->scale[j % 3];
   const T al = (T)st->alpha[j];
   T acc = T(0);
@@ -607,6 +608,40 @@ __global__ void k_resid_final(const double *part, int64_t nparts, double *out) {
   if (threadIdx.x == 0) out[1] = sqrt(b / out[2]);
 }
 
+// Ground state from a stored Krylov basis: psi = sum_{j<k} y_j (s_j v_j), in
+// j order and with the operations of the second pass (s_j = 1/beta_j, the
+// scale the first pass gave v_j), so psi is the one the second pass builds.
+template <typename T>
+__global__ void k_basis_coeffs(const LanczosState *st, int k, T *coef) {
+  for (int j = threadIdx.x; j < k; j += blockDim.x) {
+    double sj;
+    if (j == 0) sj = st->acc[0] > 0.0 ? 1.0 / sqrt(st->acc[0]) : 0.0;
+    else sj = st->beta[j] > 0.0 ? 1.0 / st->beta[j] : 0.0;
+    coef[j] = (T)st->y[j];
+    coef[ED_MAX_LANCZOS + 2 + j] = (T)sj;
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(AXPY_THREADS) k_basis_combine(T *const *basis, const T *coef,
+                                                                int k, T *psi, int64_t n) {
+  __shared__ const T *s_v[ED_MAX_LANCZOS + 2];
+  __shared__ T s_y[ED_MAX_LANCZOS + 2], s_s[ED_MAX_LANCZOS + 2];
+  for (int j = threadIdx.x; j < k; j += blockDim.x) {
+    s_v[j] = basis[j];
+    s_y[j] = coef[j];
+    s_s[j] = coef[ED_MAX_LANCZOS + 2 + j];
+  }
+  __syncthreads();
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += stride) {
+    T acc = T(0);
+#pragma unroll 8
+    for (int j = 0; j < k; ++j) acc = fmaT<T>(s_y[j], mulT<T>(s_v[j][i], s_s[j]), acc);
+    psi[i] = acc;
+  }
+}
+
 // ----------------------------------------------------------------- host driver
 
 struct Workspace {
@@ -642,12 +677,72 @@ struct StreamJoin {
   }
 };
 
+// Krylov basis kept on the device during the first pass, so that the ground
+// state needs no second pass (the paper's second pass trades a second run of
+// the recurrence for memory; this part has the memory).  Vectors are
+// allocated as the run reaches them, up to a byte budget; table[j] is the
+// device address of v_j.  Past the budget the run goes on in the three
+// rotating buffers (table[j] = rot[j % 3]) and the caller falls back to the
+// second pass.  v_0 stays in the workspace buffer where the start vector is
+// written; the rotation uses the other two and psi's buffer, which is only
+// written after the run.
+template <typename T>
+struct BasisStore {
+  T **d_table = nullptr;         // device table, maxit + 2 entries
+  std::vector<T *> table;        // host copy
+  std::vector<void *> owned;     // stored vectors v_1 .. v_{cap-1}
+  T *v0 = nullptr;               // workspace buffer of the start vector
+  T *rot[3] = {nullptr, nullptr, nullptr};  // rotation past the budget
+  int cap = 1;                   // v_j with j < cap are kept
+  bool full = false;             // budget reached: nothing more is stored
+  int filled = 0;                // table entries uploaded
+  size_t vbytes = 0, budget = 0, used = 0;
+  cudaStream_t st = nullptr;
+  ~BasisStore() {
+    for (void *p : owned) ed_dfree(p, st);
+  }
+  // table entries 0 .. upto exist on the device (ordered on cs)
+  ed_status ensure(int upto, cudaStream_t cs) {
+    st = cs;
+    upto = std::min<int>(upto, (int)table.size() - 1);
+    if (upto < filled) return ED_OK;
+    const int first = filled;
+    for (int j = filled; j <= upto; ++j) {
+      T *p = nullptr;
+      if (j == 0) {
+        p = v0;
+      } else if (!full && j == cap && used + vbytes <= budget) {
+        void *q = nullptr;
+        if (ed_dmalloc(&q, vbytes, cs, "Krylov basis") != ED_OK) {
+          cudaGetLastError();  // an allocation refused here only ends the storing
+          ed_set_error_msg("");
+        } else {
+          owned.push_back(q);
+          used += vbytes;
+          ED_TRY_CUDA(cudaMemsetAsync(q, 0, vbytes, cs));  // padding entries stay zero
+          p = (T *)q;
+          cap = j + 1;
+        }
+      }
+      if (!p) {
+        full = true;
+        p = rot[j % 3];
+      }
+      table[j] = p;
+    }
+    ED_TRY_CUDA(cudaMemcpyAsync(d_table + first, table.data() + first,
+                                (upto + 1 - first) * sizeof(T *), cudaMemcpyHostToDevice, cs));
+    filled = upto + 1;
+    return ED_OK;
+  }
+};
+
 // Runs Lanczos steps until the device state stops: chunks of `chunk` steps,
 // each chunk one CUDA graph launch, then a 4-byte read of the stop flag.
 template <typename T>
 static ed_status run_steps(ed_sector s, const HvTables<T> &tb, T *const *bufs, LanczosState *st,
                            double *part, double *part2, int64_t n, int maxit, cudaStream_t caller,
-                           int *steps_out, int32_t *h_flag) {
+                           int *steps_out, int32_t *h_flag, BasisStore<T> *bs = nullptr) {
   int64_t np1 = 0;
   const int64_t g2 = reduce_grid(n);
   int chunk = n < (1 << 20) ? 16 : 4;
@@ -663,10 +758,13 @@ static ed_status run_steps(ed_sector s, const HvTables<T> &tb, T *const *bufs, L
   ED_TRY_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
   ed_status rs = ED_OK;
   for (int it = 0; it < chunk && rs == ED_OK; ++it) {
-    rs = ed_launch_hv<T>(s, tb, HV_LANCZOS, nullptr, nullptr, bufs, nullptr, st, part, &np1, cs);
+    T *const *table = bs ? bs->d_table : nullptr;
+    rs = ed_launch_hv<T>(s, tb, HV_LANCZOS, nullptr, nullptr, bufs, nullptr, st, part, &np1, cs,
+                         table);
     if (rs != ED_OK) break;
     k_alpha<<<1, SCALAR_THREADS, 0, cs>>>(st, part, np1);
-    k_axpy_norm<T><<<(unsigned)g2, AXPY_THREADS, 0, cs>>>(st, bufs[0], bufs[1], bufs[2], n, part2);
+    k_axpy_norm<T><<<(unsigned)g2, AXPY_THREADS, 0, cs>>>(st, bufs[0], bufs[1], bufs[2], table, n,
+                                                          part2);
     k_beta<<<1, SCALAR_THREADS, 0, cs>>>(st, part2, g2);
   }
   cudaError_t ce = cudaStreamEndCapture(cs, &graph);
@@ -682,6 +780,10 @@ static ed_status run_steps(ed_sector s, const HvTables<T> &tb, T *const *bufs, L
   int launched = 0;
   ed_status out = ED_OK;
   while (launched < maxit) {
+    if (bs) {
+      out = bs->ensure(launched + chunk, cs);  // v_0 .. v_{launched+chunk}
+      if (out != ED_OK) break;
+    }
     cudaError_t e = cudaGraphLaunch(exec, cs);
     if (e != cudaSuccess) {
       ed_set_cuda_error(e, "cudaGraphLaunch", __FILE__, __LINE__);
@@ -728,15 +830,17 @@ static ed_status second_pass(ed_sector s, const HvTables<T> &tb, T *const *bufs,
 template <typename T>
 static ed_status lanczos_solve(ed_sector s, int maxit, double tol, uint64_t seed, const T *start,
                                bool want_vector, T *psi_out, LanczosState *h_state,
-                               cudaStream_t cs, int *matvecs) {
+                               cudaStream_t cs, int *matvecs, int basis_mib) {
   const int64_t n = s->bdim;  // padded block-major vectors
   ED_TRY(ed_build_items(s, 1, (int)sizeof(T)));
   const int64_t np1 = ed_hv_num_parts(s, 1, (int)sizeof(T));
   const int64_t g2 = reduce_grid(n);
   const int64_t nparts = std::max<int64_t>(np1, 3 * g2);
   size_t vb = align256(n * sizeof(T));
-  size_t bytes = 3 * vb + (want_vector ? vb : 0) + align256(sizeof(LanczosState)) +
-                 2 * align256(nparts * sizeof(double));
+  const size_t tbytes = align256((size_t)(maxit + 2) * sizeof(T *));
+  const size_t cbytes = align256(2 * (size_t)(ED_MAX_LANCZOS + 2) * sizeof(T));
+  size_t bytes = 3 * vb + (want_vector ? vb + tbytes + cbytes : 0) +
+                 align256(sizeof(LanczosState)) + 2 * align256(nparts * sizeof(double));
   Workspace ws;
   ED_TRY(ws.alloc(bytes, cs));
   char *p = (char *)ws.mem;
@@ -755,8 +859,32 @@ static ed_status lanczos_solve(ed_sector s, int maxit, double tol, uint64_t seed
   double *part = (double *)p;
   p += align256(nparts * sizeof(double));
   double *part2 = (double *)p;
+  p += align256(nparts * sizeof(double));
   // padding entries must stay zero in every vector
   ED_TRY_CUDA(cudaMemsetAsync(ws.mem, 0, (3 + (want_vector ? 1 : 0)) * vb, cs));
+  // with a vector wanted, the first pass keeps its Krylov basis while the
+  // budget allows (see BasisStore)
+  BasisStore<T> bs;
+  T *coef = nullptr;
+  if (want_vector) {
+    bs.d_table = (T **)p;
+    p += tbytes;
+    coef = (T *)p;
+    bs.table.assign(maxit + 2, nullptr);
+    bs.v0 = bufs[0];
+    bs.rot[0] = psi;
+    bs.rot[1] = bufs[1];
+    bs.rot[2] = bufs[2];
+    bs.vbytes = vb;
+    if (basis_mib < 0) {
+      bs.budget = 0;
+    } else if (basis_mib > 0) {
+      bs.budget = (size_t)basis_mib << 20;
+    } else {
+      size_t fr = 0, tot = 0;
+      bs.budget = cudaMemGetInfo(&fr, &tot) == cudaSuccess ? (size_t)(0.4 * (double)fr) : 0;
+    }
+  }
 
   PinnedFlag flag;
   if (!flag.p) {
@@ -783,7 +911,9 @@ static ed_status lanczos_solve(ed_sector s, int maxit, double tol, uint64_t seed
   ED_TRY(init());
   HvTables<T> tb = ed_hv_tables<T>(s, 1);
   int launched = 0;
-  ED_TRY(run_steps<T>(s, tb, bufs, st, part, part2, n, maxit, cs, &launched, flag.p));
+  ED_TRY(run_steps<T>(s, tb, bufs, st, part, part2, n, maxit, cs, &launched, flag.p,
+                      want_vector ? &bs : nullptr));
+  bs.st = cs;  // the stored vectors are released after their last reader below
   ED_TRY_CUDA(cudaMemcpyAsync(h_state, st, sizeof(LanczosState), cudaMemcpyDeviceToHost, cs));
   ED_TRY_CUDA(cudaStreamSynchronize(cs));
   const int k = h_state->j;
@@ -791,10 +921,18 @@ static ed_status lanczos_solve(ed_sector s, int maxit, double tol, uint64_t seed
   if (want_vector && k > 0) {
     k_tridiag_vector<<<1, TRIDIAG_THREADS, 5 * sizeof(double) * ED_MAX_LANCZOS, cs>>>(st, k);
     ED_LAUNCHED(1);
-    // restart the recurrence bookkeeping for the second pass
-    ED_TRY(init());
-    ED_TRY(second_pass<T>(s, tb, bufs, psi, st, k, n, cs));
-    mv += k - 1;
+    if (k <= bs.cap) {
+      // v_0 .. v_{k-1} are all stored: one pass over them
+      k_basis_coeffs<T><<<1, 256, 0, cs>>>(st, k, coef);
+      ED_LAUNCHED(1);
+      k_basis_combine<T><<<(unsigned)g2, AXPY_THREADS, 0, cs>>>(bs.d_table, coef, k, psi, n);
+      ED_LAUNCHED(1);
+    } else {
+      // restart the recurrence bookkeeping for the second pass
+      ED_TRY(init());
+      ED_TRY(second_pass<T>(s, tb, bufs, psi, st, k, n, cs));
+      mv += k - 1;
+    }
     // normalise psi into the output
     k_norm2<T><<<(unsigned)g2, AXPY_THREADS, 0, cs>>>(psi, n, part2);
     ED_LAUNCHED(1);
@@ -866,7 +1004,8 @@ ed_status ed_lanczos_ground_impl(ed_sector s, const ed_lanczos_opts *o, ed_lancz
     Workspace psi;   // block-major ground state
     if (want) ED_TRY(psi.alloc(n * sizeof(double), cs));
     double *bpsi = (double *)psi.mem;
-    ED_TRY(lanczos_solve<double>(s, maxit, tol, o->seed, nullptr, want, bpsi, h, cs, &mv));
+    ED_TRY(lanczos_solve<double>(s, maxit, tol, o->seed, nullptr, want, bpsi, h, cs, &mv,
+                                 o->basis_mib));
     fill_result(*h, res);
     if (want) {
       double e, r;
@@ -879,7 +1018,8 @@ ed_status ed_lanczos_ground_impl(ed_sector s, const ed_lanczos_opts *o, ed_lancz
     Workspace psi32;
     if (want) ED_TRY(psi32.alloc(n * sizeof(float), cs));
     float *fpsi = (float *)psi32.mem;
-    ED_TRY(lanczos_solve<float>(s, maxit, tol, o->seed, nullptr, want, fpsi, h, cs, &mv));
+    ED_TRY(lanczos_solve<float>(s, maxit, tol, o->seed, nullptr, want, fpsi, h, cs, &mv,
+                                o->basis_mib));
     fill_result(*h, res);
     if (want) {
       // FP64 copy of the FP32 ground state (normalised in FP64)
@@ -900,7 +1040,7 @@ ed_status ed_lanczos_ground_impl(ed_sector s, const ed_lanczos_opts *o, ed_lancz
         std::vector<char> h2buf(sizeof(LanczosState));
         LanczosState *h2 = (LanczosState *)h2buf.data();
         ED_TRY(lanczos_solve<double>(s, steps, 1e-300, 0, (const double *)start.mem, true,
-                                     (double *)psi64.mem, h2, cs, &mv));
+                                     (double *)psi64.mem, h2, cs, &mv, o->basis_mib));
         res->e0 = h2->theta;
         res->polish_iterations = h2->j;
         double e, r;

@@ -167,6 +167,7 @@ struct HvLaunch {
   const T *v;
   T *w;
   T *b0, *b1, *b2;
+  T *const *basis;  // Lanczos mode: vector j at basis[j] (else b[j % 3])
   T *psi;
   LanczosState *st;
   double *part;
@@ -600,6 +601,11 @@ __global__ void __launch_bounds__(HV_THREADS, EDGB_MIN_CTAS) k_hv(HvLaunch<T> a)
     g = bufs[j % 3];
     prev = bufs[(j + 2) % 3];
     out = bufs[(j + 1) % 3];
+    if (MODE == HV_LANCZOS && a.basis) {
+      g = a.basis[j];
+      prev = a.basis[j > 0 ? j - 1 : 0];
+      out = a.basis[j + 1];
+    }
     s_cur = (T)st->scale[j % 3];
     s_prev = (T)st->scale[(j + 2) % 3];
     beta_j = (T)st->beta[j];
@@ -723,6 +729,11 @@ __global__ void __launch_bounds__(HVS_THREADS) k_hv_small(HvLaunch<T> a) {
     g = m3 == 0 ? a.b0 : (m3 == 1 ? a.b1 : a.b2);
     out = m3 == 0 ? a.b1 : (m3 == 1 ? a.b2 : a.b0);
     prev = m3 == 0 ? a.b2 : (m3 == 1 ? a.b0 : a.b1);
+    if (MODE == HV_LANCZOS && a.basis) {
+      g = a.basis[j];
+      prev = a.basis[j > 0 ? j - 1 : 0];
+      out = a.basis[j + 1];
+    }
     s_cur = (T)st->scale[j % 3];
     s_prev = (T)st->scale[(j + 2) % 3];
     beta_j = (T)st->beta[j];
@@ -823,7 +834,7 @@ static ed_status launch_mode(const HvLaunch<T> &a, cudaStream_t st) {
 template <typename T>
 ed_status ed_launch_hv(ed_sector s, const HvTables<T> &tb, int mode, const T *v, T *w,
                        T *const *bufs, T *psi, LanczosState *state, double *part,
-                       int64_t *nparts, cudaStream_t st) {
+                       int64_t *nparts, cudaStream_t st, T *const *basis) {
   ED_TRY(ed_hv_prepare<T>());
   HvLaunch<T> a;
   a.tb = tb;
@@ -835,6 +846,7 @@ ed_status ed_launch_hv(ed_sector s, const HvTables<T> &tb, int mode, const T *v,
   a.b0 = bufs ? bufs[0] : nullptr;
   a.b1 = bufs ? bufs[1] : nullptr;
   a.b2 = bufs ? bufs[2] : nullptr;
+  a.basis = basis;
   a.psi = psi;
   a.st = state;
   a.part = part;
@@ -845,10 +857,10 @@ ed_status ed_launch_hv(ed_sector s, const HvTables<T> &tb, int mode, const T *v,
 
 template ed_status ed_launch_hv<float>(ed_sector, const HvTables<float> &, int, const float *,
                                        float *, float *const *, float *, LanczosState *, double *,
-                                       int64_t *, cudaStream_t);
+                                       int64_t *, cudaStream_t, float *const *);
 template ed_status ed_launch_hv<double>(ed_sector, const HvTables<double> &, int, const double *,
                                         double *, double *const *, double *, LanczosState *,
-                                        double *, int64_t *, cudaStream_t);
+                                        double *, int64_t *, cudaStream_t, double *const *);
 
 static ed_status matvec_layout(ed_sector s, ed_precision prec, const void *d_v, void *d_w,
                                int64_t n, void *stream, int layout) {

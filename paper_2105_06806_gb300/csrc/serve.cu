@@ -92,6 +92,10 @@ static int64_t estimate_bytes(const OwnedRequest &r) {
   int64_t b = d * (4 * elem + 8 + (r.opts.lanczos.precision == ED_FP32_POLISH ? 5 * 8 : 8));
   const int64_t chains = std::min(8, 4 * r.model.norb);
   if (r.opts.nmats > 0) b += chains * dn * 3 * gelem;
+  // the Krylov basis kept by the ground state: at most basis_mib MiB, about
+  // 128 vectors for a typical run
+  if (r.opts.lanczos.basis_mib > 0)
+    b += std::min<int64_t>((int64_t)r.opts.lanczos.basis_mib << 20, d * elem * 128);
   return b + (32ll << 20);
 }
 
@@ -211,6 +215,10 @@ extern "C" ed_status ed_submit(ed_server s, const ed_request *req, uint64_t *tic
   r->nup = req->nup;
   r->ndw = req->ndw;
   r->opts = req->opts;
+  // requests share the device: unless the request says otherwise, each keeps
+  // at most 2 GiB of Krylov basis (beyond that its ground state uses the
+  // second pass)
+  if (r->opts.lanczos.basis_mib == 0) r->opts.lanczos.basis_mib = 2048;
   r->mem_estimate = estimate_bytes(*r);
   {
     std::lock_guard<std::mutex> lk(s->mu);

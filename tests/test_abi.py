@@ -47,7 +47,8 @@ def test_status_strings_without_gpu():
 STRUCTS = {
     "ed_model": ["norb", "nbath", "U", "Ust", "Jh", "Jx", "Jp", "e_imp", "e_bath", "v_bath"],
     "ed_sector_info": ["ns", "dim_up", "dim", "device_bytes", "blocked_stride", "blocked_dim"],
-    "ed_lanczos_opts": ["precision", "max_iter", "tol", "seed", "polish_steps", "want_vector"],
+    "ed_lanczos_opts": ["precision", "max_iter", "tol", "seed", "polish_steps", "want_vector",
+                        "basis_mib"],
     "ed_lanczos_result": ["e0", "residual_estimate", "iterations", "matvecs"],
     "ed_gf_info": ["weight_hole", "steps_particle", "steps_hole"],
     "ed_solve_opts": ["lanczos", "gf_steps", "nmats", "beta", "gf_precision"],

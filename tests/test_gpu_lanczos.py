@@ -122,3 +122,29 @@ def test_ns16_fp32_polish_against_fp64_gpu(ed):
     assert abs(rp["e0"] - e) <= 1e-10 * abs(e)
     assert r64["residual"] < 1e-6 and rp["residual"] < 1e-4
     s.free()
+
+
+@pytest.mark.parametrize("case", ["ns8_fp64", "norb2_ns10_fp32_polish"])
+def test_kept_basis_equals_second_pass(ed, case):
+    """psi from the Krylov basis kept during the first pass, from the second
+    pass (basis_mib = -1), and from a budget that holds only part of the
+    basis (1 MiB: the run falls back to the second pass) are the same, bit
+    for bit; keeping the basis saves the k - 1 products of the second pass."""
+    if case == "ns8_fp64":
+        m, nup, ndw, prec = workload_ns8().model, 4, 4, "fp64"
+    else:
+        m, nup, ndw, prec = make_model(2, 4, U=3.0, Jh=0.5, seed=6), 5, 5, "fp32_polish"
+    s = ed.Sector(m, nup, ndw)
+    dt = torch.float64
+    out = {}
+    for mib in (0, -1, 1):
+        psi = torch.empty(s.dim, dtype=dt, device="cuda")
+        r = ed.lanczos_ground(s, prec, psi=psi, basis_mib=mib)
+        out[mib] = (r, psi)
+    (ra, pa), (rb, pb), (rc, pc) = out[0], out[-1], out[1]
+    assert ra["e0"] == rb["e0"] == rc["e0"]
+    assert torch.equal(pa, pb) and torch.equal(pa, pc)
+    assert ra["residual"] == rb["residual"]
+    assert rb["matvecs"] - ra["matvecs"] >= ra["iterations"] - 1
+    assert rc["matvecs"] == rb["matvecs"]
+    s.free()
