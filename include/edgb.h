@@ -161,16 +161,22 @@ ed_status ed_matvec(ed_sector s, ed_precision prec, const void *d_v, void *d_w, 
 ed_status ed_matvec_blocked(ed_sector s, ed_precision prec, const void *d_v, void *d_w,
                             int64_t n, void *stream);
 
-/* Which product kernel serves the block-major layout of s (builds the
- * block-major work tables if they do not exist yet; synchronous):
+/* Which product kernel serves the block-major layout of s in precision prec
+ * (builds the block-major work tables if they do not exist yet; synchronous):
  *   ED_KERNEL_TILED       rows of a work item staged in shared memory, H_up
  *                         from an ELL table, H_dw from neighbour rows;
  *   ED_KERNEL_ELEMENTWISE one thread per vector element (sectors of at most
- *                         2^20 padded elements).
- * ED_ERR_ARG for a null handle or output. */
+ *                         2^20 padded elements);
+ *   ED_KERNEL_TWO_PASS    the tiled kernel without H_dw, then an H_dw pass over
+ *                         column chunks (sectors whose largest dw block x up
+ *                         block slice of a vector exceeds 160 MiB: the
+ *                         neighbour rows of one pass would not stay in L2).
+ * The result is the same w = H v bit for bit whichever kernel runs.
+ * ED_ERR_ARG for a null handle or output or an unknown precision. */
 #define ED_KERNEL_TILED 0
 #define ED_KERNEL_ELEMENTWISE 1
-ed_status ed_sector_blocked_kernel(ed_sector s, int32_t *kernel);
+#define ED_KERNEL_TWO_PASS 2
+ed_status ed_sector_blocked_kernel(ed_sector s, ed_precision prec, int32_t *kernel);
 ed_status ed_sector_permute(ed_sector s, ed_precision prec, int32_t to_blocked,
                             const void *d_in, int64_t n_in, void *d_out, int64_t n_out,
                             void *stream);

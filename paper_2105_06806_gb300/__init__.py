@@ -144,7 +144,7 @@ def lib():
             "ed_sector_free": [vp],
             "ed_matvec": [vp, C.c_int, vp, vp, i64, vp],
             "ed_matvec_blocked": [vp, C.c_int, vp, vp, i64, vp],
-            "ed_sector_blocked_kernel": [vp, C.POINTER(i32)],
+            "ed_sector_blocked_kernel": [vp, C.c_int, C.POINTER(i32)],
             "ed_sector_permute": [vp, C.c_int, i32, vp, i64, vp, i64, vp],
             "ed_lanczos_ground": [vp, C.POINTER(ed_lanczos_opts), C.POINTER(ed_lanczos_result),
                                   vp, vp],
@@ -270,12 +270,13 @@ class Sector:
         out["col"], out["val"] = out["col"][:nnz], out["val"][:nnz]
         return out
 
-    def blocked_kernel(self):
-        """Product kernel of the block-major layout: "tiled" or "elementwise"
-        (ed_sector_blocked_kernel)."""
+    def blocked_kernel(self, precision="fp32"):
+        """Product kernel of the block-major layout in `precision`: "tiled",
+        "elementwise" or "two_pass" (ed_sector_blocked_kernel)."""
         k = C.c_int32()
-        _check(lib().ed_sector_blocked_kernel(self.h, C.byref(k)), "ed_sector_blocked_kernel")
-        return {0: "tiled", 1: "elementwise"}[k.value]
+        _check(lib().ed_sector_blocked_kernel(self.h, _prec(precision), C.byref(k)),
+               "ed_sector_blocked_kernel")
+        return {0: "tiled", 1: "elementwise", 2: "two_pass"}[k.value]
 
     def wtable(self):
         nm = 1 << self.model.norb

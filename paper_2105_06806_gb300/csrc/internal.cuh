@@ -122,10 +122,19 @@ struct HvItem {
   int32_t ncp;             // ELL row length (padded block width)
 };
 
+// Work item of the H_dw pass of the two-pass product: rows [r0, r0 + nr) of
+// one dw block x padded columns [c0p, c0p + nc) of one up block (nc real
+// columns, c0p a multiple of 4).
+struct DwItem {
+  int32_t r0, nr, c0p, nc;
+};
+
 struct ItemList {
   HvItem *d_items = nullptr;
   int64_t nitems = 0;
   size_t smem = 0;
+  DwItem *d_ditems = nullptr;  // non-null: two-pass product (block pairs larger than L2)
+  int64_t nditems = 0;
 };
 
 struct ed_sector_s {
@@ -267,6 +276,8 @@ struct HvTables {
   int64_t stride;   // row length of the vector layout
   const int32_t *ell_col;
   const T *ell_val;
+  const DwItem *ditems;    // non-null: two-pass product (H_up pass, then H_dw pass)
+  int64_t nditems;
   const int4 *small_cols;  // non-null: element-parallel product (small sectors)
   int64_t small_grid;      // its CTAs (= block partials of the Lanczos mode)
 };

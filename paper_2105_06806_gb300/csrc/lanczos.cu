@@ -755,6 +755,8 @@ static ed_status run_steps(ed_sector s, const HvTables<T> &tb, T *const *bufs, L
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   ED_TRY(ed_hv_prepare<T>());
+  // product kernels per step: two for the two-pass product, else one
+  const int64_t hv_per_step = (tb.ditems && !tb.small_cols) ? 2 : 1;
   ED_TRY_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
   ed_status rs = ED_OK;
   for (int it = 0; it < chunk && rs == ED_OK; ++it) {
@@ -768,7 +770,9 @@ static ed_status run_steps(ed_sector s, const HvTables<T> &tb, T *const *bufs, L
     k_beta<<<1, SCALAR_THREADS, 0, cs>>>(st, part2, g2);
   }
   cudaError_t ce = cudaStreamEndCapture(cs, &graph);
-  ed_count_launches(-(int64_t)chunk);  // the captured launches run inside the graph
+  // the captured product launches run inside the graph: count them per replay
+  const int64_t hv_launches = hv_per_step * chunk;
+  ed_count_launches(-hv_launches);
   if (rs != ED_OK) {
     if (graph) cudaGraphDestroy(graph);
     return rs;
@@ -790,7 +794,7 @@ static ed_status run_steps(ed_sector s, const HvTables<T> &tb, T *const *bufs, L
       out = ED_ERR_CUDA;
       break;
     }
-    ed_count_launches(4 * chunk);
+    ed_count_launches(hv_launches + 3 * (int64_t)chunk);
     launched += chunk;
     e = cudaMemcpyAsync(h_flag, &st->done, sizeof(int32_t), cudaMemcpyDeviceToHost, cs);
     if (e == cudaSuccess) e = cudaStreamSynchronize(cs);

@@ -65,6 +65,23 @@ struct Tile<double> {
   static constexpr int CU = 4, RT = 2;
   using V = double2;
 };
+// register tile of a given height (the H_up pass of the two-pass product uses
+// 2 FP32 rows per thread: half the staged rows, two CTAs per SM on wide blocks)
+template <typename T, int RTX>
+struct TileOf;
+template <>
+struct TileOf<float, 4> {
+  using V = float4;
+};
+template <>
+struct TileOf<float, 2> {
+  using V = float2;
+};
+template <>
+struct TileOf<double, 2> {
+  using V = double2;
+};
+constexpr int RT_PASSA = 2;
 
 // four consecutive values of a 16-byte aligned row segment
 __device__ __forceinline__ void load4(const float *p, float *y) {
@@ -136,6 +153,8 @@ HvTables<double> ed_hv_tables<double>(ed_sector s, int layout) {
   t.items = il.d_items;
   t.nitems = il.nitems;
   t.smem = il.smem;
+  t.ditems = il.d_ditems;
+  t.nditems = il.nditems;
   t.stride = layout == 0 ? s->sp[0].dim : s->bstride;
   t.ell_col = layout == 0 ? nullptr : s->ell_col;
   t.ell_val = layout == 0 ? nullptr : s->ell_v64;
@@ -153,6 +172,8 @@ HvTables<float> ed_hv_tables<float>(ed_sector s, int layout) {
   t.items = il.d_items;
   t.nitems = il.nitems;
   t.smem = il.smem;
+  t.ditems = il.d_ditems;
+  t.nditems = il.nditems;
   t.stride = layout == 0 ? s->sp[0].dim : s->bstride;
   t.ell_col = layout == 0 ? nullptr : s->ell_col;
   t.ell_val = layout == 0 ? nullptr : s->ell_v32;
@@ -174,6 +195,10 @@ struct HvLaunch {
 };
 
 constexpr int HV_THREADS = 512;
+// H_dw pass of the two-pass product (k_hv_dw)
+constexpr int DW_THREADS = 256;
+constexpr int DW_ROWS = 32;    // rows of an item
+constexpr int DW_COLS = 512;   // columns of an item (a multiple of 4)
 constexpr size_t HV_SMEM_TWO = 88 * 1024;   // two CTAs per SM (with the static tables)
 constexpr size_t HV_SMEM_MAX = 190 * 1024;  // one CTA per SM (very wide blocks)
 constexpr int HV_MAXROWS = 64;              // rows of an item (G * RT <= 16 * 4)
@@ -353,11 +378,59 @@ static ed_status build_small_cols(ed_sector s, cudaStream_t cs) {
   return ED_OK;
 }
 
+// Two-pass product: used when the largest (dw block x up block) slice of a
+// vector exceeds EDGB_TWO_PASS_MB, so that the neighbour rows the one-pass
+// kernel reads for H_dw no longer stay in L2.  The H_dw pass then walks
+// column chunks of DW_COLS through all rows of a dw block.
+#ifndef EDGB_TWO_PASS_MB
+#define EDGB_TWO_PASS_MB 160
+#endif
+static bool two_pass_wanted(ed_sector s, int elem) {
+  if (s->small_cols) return false;
+  const std::vector<int64_t> &ob_dw = s->bi[1].offset;
+  int64_t max_rows = 0, max_cols = 0;
+  for (size_t k = 0; k + 1 < ob_dw.size(); ++k) max_rows = std::max(max_rows, ob_dw[k + 1] - ob_dw[k]);
+  for (size_t k = 0; k + 1 < s->up_off_pad.size(); ++k)
+    max_cols = std::max(max_cols, s->up_off_pad[k + 1] - s->up_off_pad[k]);
+  return max_rows * max_cols * elem > ((int64_t)EDGB_TWO_PASS_MB << 20);
+}
+
+static ed_status build_dw_items(ed_sector s, ItemList &il, int elem, cudaStream_t cs) {
+  if (il.d_ditems || !two_pass_wanted(s, elem)) return ED_OK;
+  const std::vector<int64_t> &ob_dw = s->bi[1].offset, &ob_up = s->bi[0].offset;
+  std::vector<DwItem> items;
+  for (size_t bd = 0; bd + 1 < ob_dw.size(); ++bd) {
+    const int64_t R0 = ob_dw[bd], R1 = ob_dw[bd + 1];
+    for (size_t bu = 0; bu + 1 < ob_up.size(); ++bu) {
+      const int64_t nc = ob_up[bu + 1] - ob_up[bu], p0 = s->up_off_pad[bu];
+      for (int64_t c = 0; c < nc; c += DW_COLS)
+        for (int64_t r = R0; r < R1; r += DW_ROWS)
+          items.push_back(DwItem{(int32_t)r, (int32_t)std::min<int64_t>(DW_ROWS, R1 - r),
+                                 (int32_t)(p0 + c), (int32_t)std::min<int64_t>(DW_COLS, nc - c)});
+    }
+  }
+  DwItem *d = nullptr;
+  ED_TRY(ed_dmalloc((void **)&d, std::max<size_t>(items.size(), 1) * sizeof(DwItem), cs,
+                    "H_dw work items"));
+  cudaError_t e = cudaSuccess;
+  if (!items.empty())
+    e = cudaMemcpyAsync(d, items.data(), items.size() * sizeof(DwItem), cudaMemcpyHostToDevice, cs);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(cs);
+  if (e != cudaSuccess) {
+    ed_set_cuda_error(e, "H_dw work items upload", __FILE__, __LINE__);
+    ed_dfree(d, cs);
+    return ED_ERR_CUDA;
+  }
+  il.nditems = (int64_t)items.size();
+  il.d_ditems = d;
+  s->device_bytes += (int64_t)(items.size() * sizeof(DwItem));
+  return ED_OK;
+}
+
 // Rows of an item and the shared-memory bytes of one row group: the CTA is
 // split into G groups of P threads (P = the item's columns rounded up to a
 // warp, at most the CTA); group q owns rows q*RT .. q*RT+RT-1.
-static void item_shape(int64_t nc, int elem, int64_t *rows, size_t *bytes_per_group) {
-  const int RT = elem == 4 ? Tile<float>::RT : Tile<double>::RT;
+static void item_shape(int64_t nc, int elem, int RT, int64_t *rows, size_t *bytes_per_group) {
   const int64_t ntile = (nc + 3) / 4;
   const int64_t P = ntile >= HV_THREADS ? HV_THREADS : round_up(ntile, 32);
   const int64_t G = HV_THREADS / P;
@@ -387,7 +460,10 @@ ed_status ed_build_items(ed_sector s, int layout, int elem) {
     op_up = s->up_off_pad;
     ob_dw = s->bi[1].offset;
   }
-  const int RT = elem == 4 ? Tile<float>::RT : Tile<double>::RT;
+  // the H_up pass of the two-pass product stages RT_PASSA rows per thread
+  const int RT = (layout == 1 && two_pass_wanted(s, elem))
+                     ? RT_PASSA
+                     : (elem == 4 ? Tile<float>::RT : Tile<double>::RT);
   std::vector<HvItem> items;
   size_t smem = 0;
   for (size_t bd = 0; bd + 1 < ob_dw.size(); ++bd) {
@@ -399,7 +475,7 @@ ed_status ed_build_items(ed_sector s, int layout, int elem) {
       if (nc <= 0) continue;
       int64_t R;
       size_t per_group;
-      item_shape(nc, elem, &R, &per_group);
+      item_shape(nc, elem, RT, &R, &per_group);
       // shared memory holds ceil(R/RT) row groups; shrink R until it fits
       while (R > RT && (size_t)((R + RT - 1) / RT) * per_group > HV_SMEM_TWO) R -= RT;
       R = std::min<int64_t>(R, R1 - R0);
@@ -431,6 +507,7 @@ ed_status ed_build_items(ed_sector s, int layout, int elem) {
   il.smem = smem;
   il.d_items = d_items;
   s->device_bytes += (int64_t)(items.size() * sizeof(HvItem));
+  if (layout == 1) ED_TRY(build_dw_items(s, il, elem, cs));
   return ED_OK;
 }
 
@@ -457,14 +534,14 @@ __device__ __forceinline__ int stage_pos(int c, int q4) { return (c & 3) * q4 + 
 // One tile: 4 consecutive columns cb..cb+3 x RT rows of the thread's row
 // group.  FULL: all RT rows exist and all 4 columns are inside the block
 // (no predication).  BLK: block-major layout (ELL table, aligned vectors).
-template <typename T, bool FULL, bool BLK>
+template <typename T, bool FULL, bool BLK, bool NODW, int RTX>
 __device__ __forceinline__ void hv_tile(const HvTables<T> &tb, const HvItem &it, const T *g,
                                         const T *smq, bool staged, int lr0, int nrt, int cb,
                                         const int32_t *s_dn, const int32_t *s_dcol,
                                         const T *s_dval, const int32_t *s_mdw, const T *s_edw,
-                                        T (&acc)[4][Tile<T>::RT]) {
-  constexpr int RT = Tile<T>::RT;
-  using VT = typename Tile<T>::V;
+                                        T (&acc)[4][RTX]) {
+  constexpr int RT = RTX;
+  using VT = typename TileOf<T, RTX>::V;
   const int64_t stride = tb.stride;
   const int r0 = it.r0, c0 = it.c0, nc = it.nc;
   const int q4 = (nc + 3) >> 2;
@@ -535,7 +612,8 @@ __device__ __forceinline__ void hv_tile(const HvTables<T> &tb, const HvItem &it,
       }
     }
   }
-  // H_dw: neighbour rows at the same 4 columns
+  // H_dw: neighbour rows at the same 4 columns (the second pass does it when NODW)
+  if (NODW) return;
 #pragma unroll
   for (int i = 0; i < RT; ++i) {
     if (!FULL && i >= nrt) continue;
@@ -573,9 +651,12 @@ __device__ __forceinline__ void hv_tile(const HvTables<T> &tb, const HvItem &it,
   }
 }
 
-template <typename T, int MODE, bool BLK>
+// PASSA: first pass of the two-pass product (block pairs larger than L2): the
+// diagonal and H_up only, written unscaled to the output vector; k_hv_dw adds
+// H_dw and applies the epilogue.
+template <typename T, int MODE, bool BLK, bool PASSA = false, int RTX = Tile<T>::RT>
 __global__ void __launch_bounds__(HV_THREADS, EDGB_MIN_CTAS) k_hv(HvLaunch<T> a) {
-  constexpr int RT = Tile<T>::RT;
+  constexpr int RT = RTX;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double red[HV_THREADS / 32];
   __shared__ int32_t s_dcol[HV_MAXROWS * ED_MAX_NS];
@@ -643,7 +724,8 @@ __global__ void __launch_bounds__(HV_THREADS, EDGB_MIN_CTAS) k_hv(HvLaunch<T> a)
     s_dn[lr] = d1 - d0;
     s_mdw[lr] = tb.m_dw[r];
     s_edw[lr] = tb.e_dw[r];
-    for (int32_t k = d0; k < d1; ++k) {
+    if (!PASSA)
+      for (int32_t k = d0; k < d1; ++k) {
       s_dcol[lr * ED_MAX_NS + (k - d0)] = __ldg(tb.col_dw + k);
       s_dval[lr * ED_MAX_NS + (k - d0)] = __ldg(tb.val_dw + k);
     }
@@ -664,11 +746,11 @@ __global__ void __launch_bounds__(HV_THREADS, EDGB_MIN_CTAS) k_hv(HvLaunch<T> a)
       T acc[4][RT];
       const bool full = nrt == RT && cb + 4 <= nc;
       if (full)
-        hv_tile<T, true, BLK>(tb, it, g, smq, staged, lr0, nrt, cb, s_dn, s_dcol, s_dval, s_mdw,
-                              s_edw, acc);
+        hv_tile<T, true, BLK, PASSA, RT>(tb, it, g, smq, staged, lr0, nrt, cb, s_dn, s_dcol,
+                                         s_dval, s_mdw, s_edw, acc);
       else
-        hv_tile<T, false, BLK>(tb, it, g, smq, staged, lr0, nrt, cb, s_dn, s_dcol, s_dval, s_mdw,
-                               s_edw, acc);
+        hv_tile<T, false, BLK, PASSA, RT>(tb, it, g, smq, staged, lr0, nrt, cb, s_dn, s_dcol,
+                                          s_dval, s_mdw, s_edw, acc);
       // epilogue
 #pragma unroll
       for (int i = 0; i < RT; ++i) {
@@ -679,7 +761,7 @@ __global__ void __launch_bounds__(HV_THREADS, EDGB_MIN_CTAS) k_hv(HvLaunch<T> a)
           const int c = cb + u;
           if (c >= nc) continue;
           const int64_t gi = rowbase + c;
-          if (MODE == HV_PLAIN) {
+          if (MODE == HV_PLAIN || PASSA) {
             out[gi] = acc[u][i];
           } else {
             const T xv = staged ? smq[(size_t)stage_pos(c, ncp >> 2) * RT + i] : g[gi];
@@ -693,6 +775,130 @@ __global__ void __launch_bounds__(HV_THREADS, EDGB_MIN_CTAS) k_hv(HvLaunch<T> a)
               out[gi] = fma_t<T>(-alpha_j, v, w1);
               a.psi[gi] = fma_t<T>(y_j, v, a.psi[gi]);
             }
+          }
+        }
+      }
+    }
+  }
+  if (MODE == HV_LANCZOS && !PASSA) {
+    double smv = block_sum<T>((double)dot, red);
+    if (threadIdx.x == 0) a.part[blockIdx.x] = smv;
+  }
+}
+
+// Second pass of the two-pass product: out += H_dw v over DwItems (rows of
+// one dw block x a column chunk of one up block), then the epilogue of k_hv.
+// Items run column chunk by column chunk through all rows of a dw block, so
+// the chunk's strip of v (rows of the dw block x chunk columns) is the L2
+// working set of the neighbour-row reads.  Each accumulator continues from
+// the first pass's value and adds the H_dw terms in the same order as k_hv,
+// so the product equals the one-pass product bit for bit.
+
+template <typename T, int MODE>
+__global__ void __launch_bounds__(DW_THREADS) k_hv_dw(HvLaunch<T> a) {
+  constexpr int RT = Tile<T>::RT;
+  __shared__ double red[DW_THREADS / 32];
+  __shared__ int32_t s_dcol[DW_ROWS * ED_MAX_NS];
+  __shared__ T s_dval[DW_ROWS * ED_MAX_NS];
+  __shared__ int32_t s_dn[DW_ROWS];
+  const HvTables<T> &tb = a.tb;
+  int j = 0;
+  T s_cur = T(1), s_prev = T(0), beta_j = T(0), alpha_j = T(0), y_j = T(0);
+  const T *g;
+  const T *prev = nullptr;
+  T *out;
+  if (MODE == HV_PLAIN) {
+    g = a.v;
+    out = a.w;
+  } else {
+    const LanczosState *st = a.st;
+    if (MODE == HV_LANCZOS && st->done) return;
+    j = st->j;
+    const int m3 = j % 3;
+    g = m3 == 0 ? a.b0 : (m3 == 1 ? a.b1 : a.b2);
+    out = m3 == 0 ? a.b1 : (m3 == 1 ? a.b2 : a.b0);
+    prev = m3 == 0 ? a.b2 : (m3 == 1 ? a.b0 : a.b1);
+    if (MODE == HV_LANCZOS && a.basis) {
+      g = a.basis[j];
+      prev = a.basis[j > 0 ? j - 1 : 0];
+      out = a.basis[j + 1];
+    }
+    s_cur = (T)st->scale[m3];
+    s_prev = (T)st->scale[(j + 2) % 3];
+    beta_j = (T)st->beta[j];
+    if (MODE == HV_SECOND) {
+      alpha_j = (T)st->alpha[j];
+      y_j = (T)st->y[j];
+    }
+  }
+  const DwItem it = tb.ditems[blockIdx.x];
+  const int64_t stride = tb.stride;
+  for (int lr = threadIdx.x; lr < it.nr; lr += blockDim.x) {
+    const int64_t r = it.r0 + lr;
+    const int32_t d0 = __ldg(tb.rp_dw + r), d1 = __ldg(tb.rp_dw + r + 1);
+    s_dn[lr] = d1 - d0;
+    for (int32_t k = d0; k < d1; ++k) {
+      s_dcol[lr * ED_MAX_NS + (k - d0)] = __ldg(tb.col_dw + k);
+      s_dval[lr * ED_MAX_NS + (k - d0)] = __ldg(tb.val_dw + k);
+    }
+  }
+  __syncthreads();
+  const int ntile = (it.nc + 3) >> 2, ngrp = (it.nr + RT - 1) / RT;
+  T dot = T(0);
+  for (int idx = threadIdx.x; idx < ngrp * ntile; idx += blockDim.x) {
+    const int q = idx / ntile, cb = (idx - q * ntile) * 4;
+    const int lr0 = q * RT, nrt = min(RT, it.nr - lr0);
+    const int64_t col0 = (int64_t)it.c0p + cb;
+    T acc[RT][4];
+#pragma unroll
+    for (int i = 0; i < RT; ++i)
+      if (i < nrt) load4(out + (int64_t)(it.r0 + lr0 + i) * stride + col0, acc[i]);
+#pragma unroll
+    for (int i = 0; i < RT; ++i) {
+      if (i >= nrt) continue;
+      const int n = s_dn[lr0 + i];
+      const int32_t *dc = s_dcol + (lr0 + i) * ED_MAX_NS;
+      const T *dv = s_dval + (lr0 + i) * ED_MAX_NS;
+      int t = 0;
+      for (; t + 2 <= n; t += 2) {
+        T y[2][4];
+        load4(g + (int64_t)dc[t] * stride + col0, y[0]);
+        load4(g + (int64_t)dc[t + 1] * stride + col0, y[1]);
+#pragma unroll
+        for (int q2 = 0; q2 < 2; ++q2) {
+          const T h = dv[t + q2];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) acc[i][u] = fma_t<T>(h, y[q2][u], acc[i][u]);
+        }
+      }
+      for (; t < n; ++t) {
+        T y[4];
+        load4(g + (int64_t)dc[t] * stride + col0, y);
+        const T h = dv[t];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) acc[i][u] = fma_t<T>(h, y[u], acc[i][u]);
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < RT; ++i) {
+      if (i >= nrt) continue;
+      const int64_t rowbase = (int64_t)(it.r0 + lr0 + i) * stride + col0;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        if (cb + u >= it.nc) continue;  // padding is not written
+        const int64_t gi = rowbase + u;
+        if (MODE == HV_PLAIN) {
+          out[gi] = acc[i][u];
+        } else {
+          const T v = mul_t<T>(g[gi], s_cur);
+          T w1 = mul_t<T>(acc[i][u], s_cur);
+          if (j > 0) w1 = fma_t<T>(-beta_j, mul_t<T>(prev[gi], s_prev), w1);
+          if (MODE == HV_LANCZOS) {
+            out[gi] = w1;
+            dot = fma_t<T>(v, w1, dot);
+          } else {
+            out[gi] = fma_t<T>(-alpha_j, v, w1);
+            a.psi[gi] = fma_t<T>(y_j, v, a.psi[gi]);
           }
         }
       }
@@ -787,7 +993,8 @@ __global__ void __launch_bounds__(HVS_THREADS) k_hv_small(HvLaunch<T> a) {
 int64_t ed_hv_num_parts(ed_sector s, int layout, int elem_size) {
   if (ed_build_items(s, layout, elem_size) != ED_OK) return 0;
   if (layout == 1 && s->small_cols) return (s->bdim + HVS_THREADS - 1) / HVS_THREADS;
-  return s->items[layout][elem_size == 8 ? 1 : 0].nitems;
+  const ItemList &il = s->items[layout][elem_size == 8 ? 1 : 0];
+  return il.d_ditems ? il.nditems : il.nitems;
 }
 
 // Opt the product kernels into large dynamic shared memory, once per device
@@ -800,6 +1007,14 @@ static ed_status prepare_layout() {
                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)HV_SMEM_MAX));
   ED_TRY_CUDA(cudaFuncSetAttribute(k_hv<T, HV_SECOND, BLK>,
                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)HV_SMEM_MAX));
+  if (BLK) {
+    ED_TRY_CUDA(cudaFuncSetAttribute(k_hv<T, HV_PLAIN, true, true, RT_PASSA>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)HV_SMEM_MAX));
+    ED_TRY_CUDA(cudaFuncSetAttribute(k_hv<T, HV_LANCZOS, true, true, RT_PASSA>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)HV_SMEM_MAX));
+    ED_TRY_CUDA(cudaFuncSetAttribute(k_hv<T, HV_SECOND, true, true, RT_PASSA>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)HV_SMEM_MAX));
+  }
   return ED_OK;
 }
 
@@ -821,12 +1036,17 @@ template ed_status ed_hv_prepare<double>();
 
 template <typename T, int MODE>
 static ed_status launch_mode(const HvLaunch<T> &a, cudaStream_t st) {
-  if (a.tb.small_cols)
+  if (a.tb.small_cols) {
     k_hv_small<T, MODE><<<(unsigned)a.tb.small_grid, HVS_THREADS, 0, st>>>(a);
-  else if (a.tb.ell_col)
+  } else if (a.tb.ditems) {
+    k_hv<T, MODE, true, true, RT_PASSA><<<(unsigned)a.tb.nitems, HV_THREADS, a.tb.smem, st>>>(a);
+    ED_LAUNCHED(1);
+    k_hv_dw<T, MODE><<<(unsigned)a.tb.nditems, DW_THREADS, 0, st>>>(a);
+  } else if (a.tb.ell_col) {
     k_hv<T, MODE, true><<<(unsigned)a.tb.nitems, HV_THREADS, a.tb.smem, st>>>(a);
-  else
+  } else {
     k_hv<T, MODE, false><<<(unsigned)a.tb.nitems, HV_THREADS, a.tb.smem, st>>>(a);
+  }
   ED_LAUNCHED(1);
   return ED_OK;
 }
@@ -838,7 +1058,7 @@ ed_status ed_launch_hv(ed_sector s, const HvTables<T> &tb, int mode, const T *v,
   ED_TRY(ed_hv_prepare<T>());
   HvLaunch<T> a;
   a.tb = tb;
-  if (nparts) *nparts = tb.small_cols ? tb.small_grid : tb.nitems;
+  if (nparts) *nparts = tb.small_cols ? tb.small_grid : (tb.ditems ? tb.nditems : tb.nitems);
   if (tb.nitems == 0 || tb.dup == 0) return ED_OK;
   if (!tb.items) return ED_ERR_ARG;
   a.v = v;
@@ -894,9 +1114,12 @@ extern "C" ed_status ed_matvec_blocked(ed_sector s, ed_precision prec, const voi
   return matvec_layout(s, prec, d_v, d_w, n, stream, 1);
 }
 
-extern "C" ed_status ed_sector_blocked_kernel(ed_sector s, int32_t *kernel) {
+extern "C" ed_status ed_sector_blocked_kernel(ed_sector s, ed_precision prec, int32_t *kernel) {
   if (!s || !kernel) return ED_ERR_ARG;
-  ED_TRY(ed_build_items(s, 1, 4));
-  *kernel = s->small_cols ? ED_KERNEL_ELEMENTWISE : ED_KERNEL_TILED;
+  if (prec != ED_FP64 && prec != ED_FP32 && prec != ED_FP32_POLISH) return ED_ERR_ARG;
+  const int elem = prec == ED_FP64 ? 8 : 4;
+  ED_TRY(ed_build_items(s, 1, elem));
+  *kernel = s->small_cols ? ED_KERNEL_ELEMENTWISE
+            : (s->items[1][elem == 8 ? 1 : 0].d_ditems ? ED_KERNEL_TWO_PASS : ED_KERNEL_TILED);
   return ED_OK;
 }

@@ -395,7 +395,10 @@ static void sector_destroy(ed_sector s, cudaStream_t st) {
     ed_dfree(s->bi[sp].d_code2blk, st);
     ed_dfree(s->bi[sp].pidx, st);
     ed_dfree(s->bi[sp].inv, st);
-    for (int e = 0; e < 2; ++e) ed_dfree(s->items[sp][e].d_items, st);
+    for (int e = 0; e < 2; ++e) {
+      ed_dfree(s->items[sp][e].d_items, st);
+      ed_dfree(s->items[sp][e].d_ditems, st);
+    }
   }
   ed_dfree(s->colpos, st);
   ed_dfree(s->padinv, st);

@@ -190,7 +190,7 @@ KERNEL_CASES = [
 def test_blocked_kernels_against_oracle(ed, ci, prec):
     m, nup, ndw, kind = KERNEL_CASES[ci]
     s = ed.Sector(m, nup, ndw)
-    assert s.blocked_kernel() == kind
+    assert s.blocked_kernel(prec) == kind
     ref = fock.Sector(m, nup, ndw)
     rng = np.random.default_rng(200 + ci)
     dt = torch.float64 if prec == "fp64" else torch.float32
@@ -213,6 +213,51 @@ def test_blocked_kernels_against_oracle(ed, ci, prec):
     # is overwritten exactly at the D sector entries)
     nb = wb.double().cpu().numpy()
     assert np.count_nonzero(np.isnan(nb)) == s.blocked_dim - ref.dim
+    s.free()
+
+
+@pytest.mark.parametrize("maker,prec", [(workload_ns16, "fp64"), (workload_ns18, "fp32")])
+def test_two_pass_full_size_sampled(ed, maker, prec):
+    """Sectors whose block pairs exceed L2 take the two-pass block-major
+    product (H_up pass, then H_dw pass over column chunks): the full-size
+    product in the launch configuration of the Lanczos runs, checked on
+    sampled outputs against the oracle (input a closed-form function of the
+    sector index)."""
+    wl = maker(0)
+    m = wl.model
+    s = ed.Sector(m, wl.nup, wl.ndw)
+    assert s.blocked_kernel(prec) == "two_pass"
+    dup, ddw, n = s.dim_up, s.dim_dw, s.dim
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    v = torch.empty(n, device="cuda", dtype=dt)
+    step = 1 << 27
+    for o in range(0, n, step):
+        idx = torch.arange(o, min(n, o + step), device="cuda", dtype=torch.float64)
+        v[o:o + len(idx)] = (torch.sin(0.37 * idx) + torch.cos(0.011 * idx)).to(dt)
+    del idx
+    vb = torch.empty(s.blocked_dim, device="cuda", dtype=dt)
+    ed.permute(s, v, vb, True, prec)
+    wb = torch.empty_like(vb)
+    ed.matvec_blocked(s, vb, wb, prec)
+    del vb
+    w = v  # reuse the memory: v is no longer needed on the device
+    ed.permute(s, wb, w, False, prec)
+    del wb
+    torch.cuda.synchronize()
+    ref = _lite_sector(m, wl.nup, wl.ndw)
+
+    def vf(r, c):
+        i = int(r) * int(dup) + int(c)
+        x = np.sin(0.37 * i) + np.cos(0.011 * i)
+        return float(np.float32(x)) if prec == "fp32" else float(x)
+    rng = np.random.default_rng(9)
+    rows = np.concatenate([[0, ddw - 1, ddw // 2], rng.integers(0, ddw, 40)])
+    cols = np.concatenate([[0, dup - 1, dup // 3], rng.integers(0, dup, 40)])
+    want = _sampled_reference(ref, vf, rows, cols)
+    flat = torch.tensor(rows.astype(np.int64) * dup + cols.astype(np.int64), device="cuda")
+    got = w[flat].double().cpu().numpy()
+    tol = 1e-12 if prec == "fp64" else 2e-5
+    assert np.abs(got - want).max() <= tol * max(1.0, np.abs(want).max())
     s.free()
 
 
