@@ -81,7 +81,15 @@ template <>
 struct TileOf<double, 2> {
   using V = double2;
 };
-constexpr int RT_PASSA = 2;
+#ifndef EDGB_PASSA_RT
+#define EDGB_PASSA_RT 2
+#endif
+#ifndef EDGB_PASSA_THREADS
+#define EDGB_PASSA_THREADS 512
+#endif
+template <typename T>
+constexpr int rt_passa() { return sizeof(T) == 4 ? EDGB_PASSA_RT : 2; }
+constexpr int PASSA_THREADS = EDGB_PASSA_THREADS;
 
 // four consecutive values of a 16-byte aligned row segment
 __device__ __forceinline__ void load4(const float *p, float *y) {
@@ -430,10 +438,11 @@ static ed_status build_dw_items(ed_sector s, ItemList &il, int elem, cudaStream_
 // Rows of an item and the shared-memory bytes of one row group: the CTA is
 // split into G groups of P threads (P = the item's columns rounded up to a
 // warp, at most the CTA); group q owns rows q*RT .. q*RT+RT-1.
-static void item_shape(int64_t nc, int elem, int RT, int64_t *rows, size_t *bytes_per_group) {
+static void item_shape(int64_t nc, int elem, int RT, int threads, int64_t *rows,
+                       size_t *bytes_per_group) {
   const int64_t ntile = (nc + 3) / 4;
-  const int64_t P = ntile >= HV_THREADS ? HV_THREADS : round_up(ntile, 32);
-  const int64_t G = HV_THREADS / P;
+  const int64_t P = ntile >= threads ? threads : round_up(ntile, 32);
+  const int64_t G = threads / P;
   *rows = G * RT;
   *bytes_per_group = (size_t)round_up(nc, 4) * RT * elem;
 }
@@ -460,10 +469,11 @@ ed_status ed_build_items(ed_sector s, int layout, int elem) {
     op_up = s->up_off_pad;
     ob_dw = s->bi[1].offset;
   }
-  // the H_up pass of the two-pass product stages RT_PASSA rows per thread
-  const int RT = (layout == 1 && two_pass_wanted(s, elem))
-                     ? RT_PASSA
-                     : (elem == 4 ? Tile<float>::RT : Tile<double>::RT);
+  // the H_up pass of the two-pass product has its own tile height and CTA size
+  const bool passa = layout == 1 && two_pass_wanted(s, elem);
+  const int RT = passa ? (elem == 4 ? rt_passa<float>() : rt_passa<double>())
+                       : (elem == 4 ? Tile<float>::RT : Tile<double>::RT);
+  const int threads = passa ? PASSA_THREADS : HV_THREADS;
   std::vector<HvItem> items;
   size_t smem = 0;
   for (size_t bd = 0; bd + 1 < ob_dw.size(); ++bd) {
@@ -475,10 +485,11 @@ ed_status ed_build_items(ed_sector s, int layout, int elem) {
       if (nc <= 0) continue;
       int64_t R;
       size_t per_group;
-      item_shape(nc, elem, RT, &R, &per_group);
+      item_shape(nc, elem, RT, threads, &R, &per_group);
       // shared memory holds ceil(R/RT) row groups; shrink R until it fits
       while (R > RT && (size_t)((R + RT - 1) / RT) * per_group > HV_SMEM_TWO) R -= RT;
-      R = std::min<int64_t>(R, R1 - R0);
+      // the per-row lists of an item live in arrays of HV_MAXROWS rows
+      R = std::min<int64_t>(std::min<int64_t>(R, HV_MAXROWS), R1 - R0);
       const size_t need = (size_t)((R + RT - 1) / RT) * per_group;
       if (need <= HV_SMEM_MAX) smem = std::max(smem, need);
       const int32_t deg = layout == 0 ? 0 : s->ell_deg[bu];
@@ -613,9 +624,8 @@ __device__ __forceinline__ void hv_tile(const HvTables<T> &tb, const HvItem &it,
     }
   }
   // H_dw: neighbour rows at the same 4 columns (the second pass does it when NODW)
-  if (NODW) return;
 #pragma unroll
-  for (int i = 0; i < RT; ++i) {
+  for (int i = 0; i < (NODW ? 0 : RT); ++i) {
     if (!FULL && i >= nrt) continue;
     const int n = s_dn[lr0 + i];
     const int32_t *dc = s_dcol + (lr0 + i) * ED_MAX_NS;
@@ -654,11 +664,12 @@ __device__ __forceinline__ void hv_tile(const HvTables<T> &tb, const HvItem &it,
 // PASSA: first pass of the two-pass product (block pairs larger than L2): the
 // diagonal and H_up only, written unscaled to the output vector; k_hv_dw adds
 // H_dw and applies the epilogue.
-template <typename T, int MODE, bool BLK, bool PASSA = false, int RTX = Tile<T>::RT>
-__global__ void __launch_bounds__(HV_THREADS, EDGB_MIN_CTAS) k_hv(HvLaunch<T> a) {
+template <typename T, int MODE, bool BLK, bool PASSA = false, int RTX = Tile<T>::RT,
+          int NT = HV_THREADS>
+__global__ void __launch_bounds__(NT, NT >= 1024 ? 1 : EDGB_MIN_CTAS) k_hv(HvLaunch<T> a) {
   constexpr int RT = RTX;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ double red[HV_THREADS / 32];
+  __shared__ double red[NT / 32];
   __shared__ int32_t s_dcol[HV_MAXROWS * ED_MAX_NS];
   __shared__ T s_dval[HV_MAXROWS * ED_MAX_NS];
   __shared__ int32_t s_dn[HV_MAXROWS], s_mdw[HV_MAXROWS];
@@ -1008,11 +1019,11 @@ static ed_status prepare_layout() {
   ED_TRY_CUDA(cudaFuncSetAttribute(k_hv<T, HV_SECOND, BLK>,
                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)HV_SMEM_MAX));
   if (BLK) {
-    ED_TRY_CUDA(cudaFuncSetAttribute(k_hv<T, HV_PLAIN, true, true, RT_PASSA>,
+    ED_TRY_CUDA(cudaFuncSetAttribute(k_hv<T, HV_PLAIN, true, true, rt_passa<T>(), PASSA_THREADS>,
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)HV_SMEM_MAX));
-    ED_TRY_CUDA(cudaFuncSetAttribute(k_hv<T, HV_LANCZOS, true, true, RT_PASSA>,
+    ED_TRY_CUDA(cudaFuncSetAttribute(k_hv<T, HV_LANCZOS, true, true, rt_passa<T>(), PASSA_THREADS>,
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)HV_SMEM_MAX));
-    ED_TRY_CUDA(cudaFuncSetAttribute(k_hv<T, HV_SECOND, true, true, RT_PASSA>,
+    ED_TRY_CUDA(cudaFuncSetAttribute(k_hv<T, HV_SECOND, true, true, rt_passa<T>(), PASSA_THREADS>,
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)HV_SMEM_MAX));
   }
   return ED_OK;
@@ -1039,7 +1050,8 @@ static ed_status launch_mode(const HvLaunch<T> &a, cudaStream_t st) {
   if (a.tb.small_cols) {
     k_hv_small<T, MODE><<<(unsigned)a.tb.small_grid, HVS_THREADS, 0, st>>>(a);
   } else if (a.tb.ditems) {
-    k_hv<T, MODE, true, true, RT_PASSA><<<(unsigned)a.tb.nitems, HV_THREADS, a.tb.smem, st>>>(a);
+    k_hv<T, MODE, true, true, rt_passa<T>(), PASSA_THREADS>
+        <<<(unsigned)a.tb.nitems, PASSA_THREADS, a.tb.smem, st>>>(a);
     ED_LAUNCHED(1);
     k_hv_dw<T, MODE><<<(unsigned)a.tb.nditems, DW_THREADS, 0, st>>>(a);
   } else if (a.tb.ell_col) {
