@@ -288,6 +288,14 @@ def run_ours(args):
     serving = None
     if rank == 0 and args.serving > 0:
         serving = run_serving(E, args.serving, args.serving_max_ns, args.serving_rate)
+        if args.serving_rate <= 0:
+            # the same stream with Poisson arrivals at 0.8 x the saturation rate:
+            # latency of a loaded but not saturated server
+            lam = round(0.8 * serving["solves_per_s"], 1)
+            serving["poisson_0p8"] = run_serving(E, args.serving, args.serving_max_ns, lam)
+            if args.serving_max_ns < 16:
+                # the configured stream draws Ns up to 16 (D up to 1.66e8)
+                serving["full_ns16"] = run_serving(E, args.serving, 16, 0.0)
 
     value, iters_s, t_max = combine_ranks(dist, tot_bytes, tot_it, t_s)
     if rank != 0:
