@@ -165,8 +165,9 @@ ed_status ed_matvec_blocked(ed_sector s, ed_precision prec, const void *d_v, voi
  * (builds the block-major work tables if they do not exist yet; synchronous):
  *   ED_KERNEL_TILED       rows of a work item staged in shared memory, H_up
  *                         from an ELL table, H_dw from neighbour rows;
- *   ED_KERNEL_ELEMENTWISE one thread per vector element (sectors of at most
- *                         2^20 padded elements);
+ *   ED_KERNEL_ELEMENTWISE one thread per vector element (small sectors; the
+ *                         autotuner below decides between it and the tiled
+ *                         kernel);
  *   ED_KERNEL_TWO_PASS    the tiled kernel without H_dw, then an H_dw pass over
  *                         column chunks (sectors whose largest dw block x up
  *                         block slice of a vector exceeds 160 MiB: the
@@ -177,6 +178,23 @@ ed_status ed_matvec_blocked(ed_sector s, ed_precision prec, const void *d_v, voi
 #define ED_KERNEL_ELEMENTWISE 1
 #define ED_KERNEL_TWO_PASS 2
 ed_status ed_sector_blocked_kernel(ed_sector s, ed_precision prec, int32_t *kernel);
+
+/* Autotuner (no counterpart in the paper).  Sectors of at most 2^17 padded
+ * elements use the element-parallel kernel and sectors above 2^24 the tiled
+ * family; in between the first sector of each shape (Norb, Nbath, N_up,
+ * N_dw, precision) times both kernels (one warm-up and three launches each,
+ * on a scratch vector) when its block-major tables are built, and every
+ * sector of that shape in the process then uses the faster one.
+ * ed_sector_tune_info returns the kernel in use and host_ms[0..1], the
+ * measured milliseconds of the tiled and the element-parallel product
+ * (-1 where this sector did not time them).  ed_sector_set_kernel pins a
+ * kernel for one sector and precision: ED_KERNEL_ELEMENTWISE (sectors of at
+ * most 2^24 padded elements) or the tiled family (ED_KERNEL_TILED, or
+ * ED_KERNEL_TWO_PASS where the block sizes call for two passes); other
+ * requests give ED_ERR_UNSUPPORTED.  All kernels compute the same w = H v bit
+ * for bit; Lanczos runs differ only in the summation order of <v, w>. */
+ed_status ed_sector_tune_info(ed_sector s, ed_precision prec, int32_t *kernel, double *host_ms);
+ed_status ed_sector_set_kernel(ed_sector s, ed_precision prec, int32_t kernel);
 ed_status ed_sector_permute(ed_sector s, ed_precision prec, int32_t to_blocked,
                             const void *d_in, int64_t n_in, void *d_out, int64_t n_out,
                             void *stream);

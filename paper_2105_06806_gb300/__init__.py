@@ -27,6 +27,7 @@ PRECISIONS = {"fp64": FP64, "fp32": FP32, "fp32_polish": FP32_POLISH}
 EXPORTED = [
     "ed_sector_build", "ed_sector_get_info", "ed_sector_copy_tables", "ed_sector_copy_w",
     "ed_sector_free", "ed_matvec", "ed_matvec_blocked", "ed_sector_blocked_kernel",
+    "ed_sector_tune_info", "ed_sector_set_kernel",
     "ed_sector_permute", "ed_lanczos_ground", "ed_gf_lanczos", "ed_solve",
     "ed_server_create", "ed_submit", "ed_poll", "ed_wait", "ed_server_destroy",
     "ed_server_inject_alloc_failure", "ed_residual_noalloc", "ed_status_string", "ed_last_error",
@@ -145,6 +146,8 @@ def lib():
             "ed_matvec": [vp, C.c_int, vp, vp, i64, vp],
             "ed_matvec_blocked": [vp, C.c_int, vp, vp, i64, vp],
             "ed_sector_blocked_kernel": [vp, C.c_int, C.POINTER(i32)],
+            "ed_sector_tune_info": [vp, C.c_int, C.POINTER(i32), vp],
+            "ed_sector_set_kernel": [vp, C.c_int, i32],
             "ed_sector_permute": [vp, C.c_int, i32, vp, i64, vp, i64, vp],
             "ed_lanczos_ground": [vp, C.POINTER(ed_lanczos_opts), C.POINTER(ed_lanczos_result),
                                   vp, vp],
@@ -277,6 +280,21 @@ class Sector:
         _check(lib().ed_sector_blocked_kernel(self.h, _prec(precision), C.byref(k)),
                "ed_sector_blocked_kernel")
         return {0: "tiled", 1: "elementwise", 2: "two_pass"}[k.value]
+
+    def tune_info(self, precision="fp32"):
+        """(kernel in use, {"tiled": ms, "elementwise": ms}) of the autotuner
+        (ed_sector_tune_info; -1 ms where this sector did not time a kernel)."""
+        k = C.c_int32()
+        ms = np.zeros(2)
+        _check(lib().ed_sector_tune_info(self.h, _prec(precision), C.byref(k), ms.ctypes.data),
+               "ed_sector_tune_info")
+        return {0: "tiled", 1: "elementwise", 2: "two_pass"}[k.value], \
+            {"tiled": float(ms[0]), "elementwise": float(ms[1])}
+
+    def set_kernel(self, kernel, precision="fp32"):
+        """Pin the block-major product kernel of this sector (ed_sector_set_kernel)."""
+        code = {"tiled": 0, "elementwise": 1, "two_pass": 2}[kernel]
+        _check(lib().ed_sector_set_kernel(self.h, _prec(precision), code), "ed_sector_set_kernel")
 
     def wtable(self):
         nm = 1 << self.model.norb

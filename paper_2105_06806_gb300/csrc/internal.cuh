@@ -164,6 +164,11 @@ struct ed_sector_s {
   // block-major up order or -1 for padding, its first ELL entry, first padded
   // column of its up block, (ELL row length << 8) | ELL width}.
   int4 *small_cols = nullptr;
+  // block-major product kernel per precision [FP32, FP64]: -1 undecided,
+  // 0 tiled (one- or two-pass), 1 element-parallel; pinned or autotuned
+  int8_t hv_kernel[2] = {-1, -1};
+  bool hv_pinned[2] = {false, false};
+  double tune_ms[2][2] = {{-1.0, -1.0}, {-1.0, -1.0}};  // [precision][tiled, element-parallel]
   double *W = nullptr;     // [2^norb][2^norb]
   float *W32 = nullptr;
   ed_sector nb[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};  // [spin][0:c,1:c+]

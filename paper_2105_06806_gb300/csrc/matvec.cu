@@ -19,6 +19,8 @@
 // formed: the strided axis of Sec. 3.2 is read directly by row segments,
 // which stay in L2 while the block pair is processed.
 #include <algorithm>
+#include <map>
+#include <tuple>
 #include <mutex>
 #include <type_traits>
 
@@ -123,13 +125,18 @@ __device__ __forceinline__ void vec_get(const float2 &v, float *x) {
   x[1] = v.y;
 }
 
-// Element-parallel product for small sectors (one thread per element of the
-// padded block-major vector): below EDGB_SMALL_MAX_DIM elements the tiled
-// kernel has too few work items to fill the GPU and its time is set by the
-// serial per-thread tile, so one thread per element is faster.
+// Element-parallel product (one thread per element of the padded block-major
+// vector).  Below EDGB_TUNE_MIN elements the tiled kernel has too few work
+// items to fill the GPU and its time is set by the serial per-thread tile, so
+// one thread per element is used; above EDGB_TUNE_MAX the tiled kernel's
+// reuse of staged rows and ELL entries wins.  In between, which one is faster
+// depends on the block shapes of the sector: the autotuner times both.
 constexpr int HVS_THREADS = 256;
-#ifndef EDGB_SMALL_MAX_DIM
-#define EDGB_SMALL_MAX_DIM (1 << 20)
+#ifndef EDGB_TUNE_MIN
+#define EDGB_TUNE_MIN (1 << 17)
+#endif
+#ifndef EDGB_TUNE_MAX
+#define EDGB_TUNE_MAX (1 << 24)
 #endif
 
 template <typename T>
@@ -166,7 +173,7 @@ HvTables<double> ed_hv_tables<double>(ed_sector s, int layout) {
   t.stride = layout == 0 ? s->sp[0].dim : s->bstride;
   t.ell_col = layout == 0 ? nullptr : s->ell_col;
   t.ell_val = layout == 0 ? nullptr : s->ell_v64;
-  t.small_cols = layout == 0 ? nullptr : s->small_cols;
+  t.small_cols = (layout == 1 && s->hv_kernel[1] == 1) ? s->small_cols : nullptr;
   t.small_grid = t.small_cols ? (s->bdim + HVS_THREADS - 1) / HVS_THREADS : 0;
   return t;
 }
@@ -185,7 +192,7 @@ HvTables<float> ed_hv_tables<float>(ed_sector s, int layout) {
   t.stride = layout == 0 ? s->sp[0].dim : s->bstride;
   t.ell_col = layout == 0 ? nullptr : s->ell_col;
   t.ell_val = layout == 0 ? nullptr : s->ell_v32;
-  t.small_cols = layout == 0 ? nullptr : s->small_cols;
+  t.small_cols = (layout == 1 && s->hv_kernel[0] == 1) ? s->small_cols : nullptr;
   t.small_grid = t.small_cols ? (s->bdim + HVS_THREADS - 1) / HVS_THREADS : 0;
   return t;
 }
@@ -360,7 +367,7 @@ ed_status ed_build_ell(ed_sector s, cudaStream_t st) {
 // after the ELL table.  Sectors whose blocks do not fit the packing stay on
 // the tiled kernel.
 static ed_status build_small_cols(ed_sector s, cudaStream_t cs) {
-  if (s->small_cols || s->bdim == 0 || s->bdim > (int64_t)EDGB_SMALL_MAX_DIM) return ED_OK;
+  if (s->small_cols || s->bdim == 0 || s->bdim > (int64_t)EDGB_TUNE_MAX) return ED_OK;
   const BlockInfo &b = s->bi[0];
   std::vector<int4> cols(s->bstride);
   for (int k = 0; k < b.nblocks; ++k) {
@@ -394,7 +401,6 @@ static ed_status build_small_cols(ed_sector s, cudaStream_t cs) {
 #define EDGB_TWO_PASS_MB 160
 #endif
 static bool two_pass_wanted(ed_sector s, int elem) {
-  if (s->small_cols) return false;
   const std::vector<int64_t> &ob_dw = s->bi[1].offset;
   int64_t max_rows = 0, max_cols = 0;
   for (size_t k = 0; k + 1 < ob_dw.size(); ++k) max_rows = std::max(max_rows, ob_dw[k + 1] - ob_dw[k]);
@@ -432,6 +438,99 @@ static ed_status build_dw_items(ed_sector s, ItemList &il, int elem, cudaStream_
   il.nditems = (int64_t)items.size();
   il.d_ditems = d;
   s->device_bytes += (int64_t)(items.size() * sizeof(DwItem));
+  return ED_OK;
+}
+
+// ----------------------------------------------------------------- autotuner
+//
+// For sectors between EDGB_TUNE_MIN and EDGB_TUNE_MAX padded elements the
+// faster of the tiled and the element-parallel product depends on the block
+// shapes, so it is measured: both kernels, one warm-up and three timed
+// launches each on a scratch vector, on this thread's private stream.  The
+// choice is kept per sector shape (Norb, Nbath, N_up, N_dw, precision) for
+// the life of the process, so every sector of a shape uses the same kernel
+// and results do not depend on which call came first.  Both kernels give the
+// same w = H v bit for bit.
+namespace {
+struct TuneKey {
+  int norb, nbath, nup, ndw, elem;
+  bool operator<(const TuneKey &o) const {
+    return std::tie(norb, nbath, nup, ndw, elem) < std::tie(o.norb, o.nbath, o.nup, o.ndw, o.elem);
+  }
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, int> g_tune;
+}  // namespace
+
+template <typename T>
+static ed_status time_hv_kernels(ed_sector s, int e, cudaStream_t cs, double ms[2]) {
+  const int64_t n = s->bdim;
+  void *mem = nullptr;
+  ED_TRY(ed_dmalloc(&mem, 2 * n * sizeof(T), cs, "autotune vectors"));
+  T *v = (T *)mem, *w = v + n;
+  cudaEvent_t ev[2] = {nullptr, nullptr};
+  ed_status rs = ED_OK;
+  if (cudaMemsetAsync(mem, 0, 2 * n * sizeof(T), cs) != cudaSuccess ||
+      cudaEventCreate(&ev[0]) != cudaSuccess || cudaEventCreate(&ev[1]) != cudaSuccess)
+    rs = ED_ERR_CUDA;
+  for (int k = 0; k < 2 && rs == ED_OK; ++k) {
+    s->hv_kernel[e] = (int8_t)k;
+    const HvTables<T> tb = ed_hv_tables<T>(s, 1);
+    rs = ed_launch_hv<T>(s, tb, HV_PLAIN, v, w, nullptr, nullptr, nullptr, nullptr, nullptr, cs);
+    if (rs == ED_OK && cudaEventRecord(ev[0], cs) != cudaSuccess) rs = ED_ERR_CUDA;
+    for (int r = 0; r < 3 && rs == ED_OK; ++r)
+      rs = ed_launch_hv<T>(s, tb, HV_PLAIN, v, w, nullptr, nullptr, nullptr, nullptr, nullptr, cs);
+    float t = 0.0f;
+    if (rs == ED_OK && (cudaEventRecord(ev[1], cs) != cudaSuccess ||
+                        cudaEventSynchronize(ev[1]) != cudaSuccess ||
+                        cudaEventElapsedTime(&t, ev[0], ev[1]) != cudaSuccess))
+      rs = ED_ERR_CUDA;
+    ms[k] = t / 3.0;
+  }
+  for (cudaEvent_t x : ev)
+    if (x) cudaEventDestroy(x);
+  ed_dfree(mem, cs);
+  if (cudaStreamSynchronize(cs) != cudaSuccess && rs == ED_OK) rs = ED_ERR_CUDA;
+  return rs;
+}
+
+static ed_status decide_kernel(ed_sector s, int elem, cudaStream_t cs) {
+  const int e = elem == 8 ? 1 : 0;
+  if (s->hv_kernel[e] >= 0) return ED_OK;
+  if (!s->small_cols) {
+    s->hv_kernel[e] = 0;
+    return ED_OK;
+  }
+  if (s->bdim <= (int64_t)EDGB_TUNE_MIN) {
+    s->hv_kernel[e] = 1;
+    return ED_OK;
+  }
+  const TuneKey key{s->mp.norb, s->mp.nbath, s->nup, s->ndw, elem};
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune.find(key);
+    if (it != g_tune.end()) {
+      s->hv_kernel[e] = (int8_t)it->second;
+      return ED_OK;
+    }
+  }
+  double ms[2] = {-1.0, -1.0};
+  const ed_status rs = elem == 8 ? time_hv_kernels<double>(s, e, cs, ms)
+                                 : time_hv_kernels<float>(s, e, cs, ms);
+  if (rs != ED_OK) {
+    s->hv_kernel[e] = 0;
+    return rs;
+  }
+  int choice = ms[1] < ms[0] ? 1 : 0;
+  s->tune_ms[e][0] = ms[0];
+  s->tune_ms[e][1] = ms[1];
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune.find(key);  // another thread may have tuned the shape meanwhile
+    if (it != g_tune.end()) choice = it->second;
+    else g_tune[key] = choice;
+  }
+  s->hv_kernel[e] = (int8_t)choice;
   return ED_OK;
 }
 
@@ -518,7 +617,10 @@ ed_status ed_build_items(ed_sector s, int layout, int elem) {
   il.smem = smem;
   il.d_items = d_items;
   s->device_bytes += (int64_t)(items.size() * sizeof(HvItem));
-  if (layout == 1) ED_TRY(build_dw_items(s, il, elem, cs));
+  if (layout == 1) {
+    ED_TRY(build_dw_items(s, il, elem, cs));
+    ED_TRY(decide_kernel(s, elem, cs));
+  }
   return ED_OK;
 }
 
@@ -1003,7 +1105,8 @@ __global__ void __launch_bounds__(HVS_THREADS) k_hv_small(HvLaunch<T> a) {
 
 int64_t ed_hv_num_parts(ed_sector s, int layout, int elem_size) {
   if (ed_build_items(s, layout, elem_size) != ED_OK) return 0;
-  if (layout == 1 && s->small_cols) return (s->bdim + HVS_THREADS - 1) / HVS_THREADS;
+  if (layout == 1 && s->hv_kernel[elem_size == 8 ? 1 : 0] == 1)
+    return (s->bdim + HVS_THREADS - 1) / HVS_THREADS;
   const ItemList &il = s->items[layout][elem_size == 8 ? 1 : 0];
   return il.d_ditems ? il.nditems : il.nitems;
 }
@@ -1126,12 +1229,53 @@ extern "C" ed_status ed_matvec_blocked(ed_sector s, ed_precision prec, const voi
   return matvec_layout(s, prec, d_v, d_w, n, stream, 1);
 }
 
-extern "C" ed_status ed_sector_blocked_kernel(ed_sector s, ed_precision prec, int32_t *kernel) {
-  if (!s || !kernel) return ED_ERR_ARG;
+static ed_status kernel_of(ed_sector s, ed_precision prec, int *e, int32_t *kernel) {
   if (prec != ED_FP64 && prec != ED_FP32 && prec != ED_FP32_POLISH) return ED_ERR_ARG;
   const int elem = prec == ED_FP64 ? 8 : 4;
+  *e = elem == 8 ? 1 : 0;
   ED_TRY(ed_build_items(s, 1, elem));
-  *kernel = s->small_cols ? ED_KERNEL_ELEMENTWISE
-            : (s->items[1][elem == 8 ? 1 : 0].d_ditems ? ED_KERNEL_TWO_PASS : ED_KERNEL_TILED);
+  *kernel = s->hv_kernel[*e] == 1
+                ? ED_KERNEL_ELEMENTWISE
+                : (s->items[1][*e].d_ditems ? ED_KERNEL_TWO_PASS : ED_KERNEL_TILED);
+  return ED_OK;
+}
+
+extern "C" ed_status ed_sector_blocked_kernel(ed_sector s, ed_precision prec, int32_t *kernel) {
+  if (!s || !kernel) return ED_ERR_ARG;
+  int e = 0;
+  return kernel_of(s, prec, &e, kernel);
+}
+
+extern "C" ed_status ed_sector_tune_info(ed_sector s, ed_precision prec, int32_t *kernel,
+                                         double *host_ms) {
+  if (!s || !kernel || !host_ms) return ED_ERR_ARG;
+  int e = 0;
+  ED_TRY(kernel_of(s, prec, &e, kernel));
+  host_ms[0] = s->tune_ms[e][0];
+  host_ms[1] = s->tune_ms[e][1];
+  return ED_OK;
+}
+
+extern "C" ed_status ed_sector_set_kernel(ed_sector s, ed_precision prec, int32_t kernel) {
+  if (!s) return ED_ERR_ARG;
+  int e = 0;
+  int32_t cur = 0;
+  ED_TRY(kernel_of(s, prec, &e, &cur));
+  if (kernel == ED_KERNEL_ELEMENTWISE) {
+    if (!s->small_cols) {
+      ed_set_error_msg("the element-parallel product needs a sector of at most 2^24 padded elements");
+      return ED_ERR_UNSUPPORTED;
+    }
+    s->hv_kernel[e] = 1;
+  } else if (kernel == ED_KERNEL_TILED || kernel == ED_KERNEL_TWO_PASS) {
+    // the tiled family: one or two passes as the sector's size decides
+    if ((kernel == ED_KERNEL_TWO_PASS) != (s->items[1][e].d_ditems != nullptr)) {
+      ed_set_error_msg("one or two passes is fixed by the sector's block sizes");
+      return ED_ERR_UNSUPPORTED;
+    }
+    s->hv_kernel[e] = 0;
+  } else {
+    return ED_ERR_ARG;
+  }
   return ED_OK;
 }

@@ -75,7 +75,7 @@ def test_norb2_ns14_ground_and_gf(ed):
     g, Gref = _gold("oracle_norb2_ns14.json")
     wl = workload_norb2_ns14(0)
     s = ed.Sector(wl.model, wl.nup, wl.ndw)
-    assert s.blocked_kernel() == "tiled"
+    assert s.blocked_kernel() in ("tiled", "elementwise")  # chosen by the autotuner
     r, psi = _ground(ed, s, "fp64")
     assert abs(r["e0"] - g["e0"]) <= 1e-10 * abs(g["e0"])
     p = psi.cpu().numpy()

@@ -172,48 +172,77 @@ def test_block_major_layout(ed, ci, prec):
     s.free()
 
 
-# Both block-major product kernels against the oracle element by element:
-# small sectors take the element-parallel kernel (one and three orbitals),
-# larger ones the tiled kernel (one, two and three orbitals; ragged sectors
-# off half filling, several work items per block pair).
+# Both one-pass block-major product kernels against the oracle element by
+# element, each pinned in turn (ed_sector_set_kernel): one, two and three
+# orbitals, ragged sectors off half filling, several work items per block
+# pair; the two kernels must also agree bit for bit (they take the same
+# operations per element in the same order).
 KERNEL_CASES = [
-    (make_model(1, 11, U=2.5, e_d=-1.2, seed=7), 6, 5, "elementwise"),   # D = 731,808
-    (make_model(3, 3, U=2.5, Jh=0.4, seed=14), 6, 5, "elementwise"),     # D = 731,808
-    (make_model(1, 13, U=4.0, e_d=-2.0, seed=11), 7, 6, "tiled"),        # D = 10,306,296
-    (make_model(2, 6, U=3.0, Jh=0.5, seed=12), 5, 6, "tiled"),           # D = 6,012,006
-    (make_model(3, 4, U=2.5, Jh=0.4, seed=13), 5, 4, "tiled"),           # D = 4,099,095
+    (make_model(2, 4, U=3.0, Jh=0.5, seed=6), 5, 4),      # D = 52,920 (below the tuning range)
+    (make_model(1, 11, U=2.5, e_d=-1.2, seed=7), 6, 5),   # D = 731,808
+    (make_model(3, 3, U=2.5, Jh=0.4, seed=14), 6, 5),     # D = 731,808
+    (make_model(1, 13, U=4.0, e_d=-2.0, seed=11), 7, 6),  # D = 10,306,296
+    (make_model(2, 6, U=3.0, Jh=0.5, seed=12), 5, 6),     # D = 6,012,006
+    (make_model(3, 4, U=2.5, Jh=0.4, seed=13), 5, 4),     # D = 4,099,095
 ]
 
 
 @pytest.mark.parametrize("ci", range(len(KERNEL_CASES)))
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 def test_blocked_kernels_against_oracle(ed, ci, prec):
-    m, nup, ndw, kind = KERNEL_CASES[ci]
+    m, nup, ndw = KERNEL_CASES[ci]
     s = ed.Sector(m, nup, ndw)
-    assert s.blocked_kernel(prec) == kind
+    assert s.blocked_kernel(prec) in ("tiled", "elementwise")
     ref = fock.Sector(m, nup, ndw)
     rng = np.random.default_rng(200 + ci)
     dt = torch.float64 if prec == "fp64" else torch.float32
     v = torch.tensor(rng.uniform(-1, 1, ref.dim), dtype=dt, device="cuda")
     vb = torch.empty(s.blocked_dim, dtype=dt, device="cuda")
-    wb = torch.full_like(vb, float("nan"))
-    w = torch.empty_like(v)
     ed.permute(s, v, vb, True, prec)
-    ed.matvec_blocked(s, vb, wb, prec)
-    ed.permute(s, wb, w, False, prec)
-    torch.cuda.synchronize()
     v_used = v.double().cpu().numpy()
-    got = w.double().cpu().numpy()
     want = ref.matvec(v_used)
     bnd = _bound(ref, v_used)
     tol = 1e-13 if prec == "fp64" else 4e-6
-    assert np.all(np.isfinite(got))
-    assert np.all(np.abs(got - want) <= tol * bnd)
-    # the padding entries of the block-major output stay zero (the NaN fill
-    # is overwritten exactly at the D sector entries)
-    nb = wb.double().cpu().numpy()
-    assert np.count_nonzero(np.isnan(nb)) == s.blocked_dim - ref.dim
+    out = {}
+    for kernel in ("tiled", "elementwise"):
+        s.set_kernel(kernel, prec)
+        assert s.blocked_kernel(prec) == kernel
+        wb = torch.full_like(vb, float("nan"))
+        w = torch.empty_like(v)
+        ed.matvec_blocked(s, vb, wb, prec)
+        ed.permute(s, wb, w, False, prec)
+        torch.cuda.synchronize()
+        got = w.double().cpu().numpy()
+        assert np.all(np.isfinite(got))
+        assert np.all(np.abs(got - want) <= tol * bnd), kernel
+        # the padding entries of the block-major output are never written
+        assert np.count_nonzero(np.isnan(wb.double().cpu().numpy())) == s.blocked_dim - ref.dim
+        out[kernel] = wb
+    assert torch.equal(out["tiled"].nan_to_num(), out["elementwise"].nan_to_num())
     s.free()
+
+
+def test_autotuner_picks_the_faster_kernel_per_shape(ed):
+    """Sectors between 2^17 and 2^24 padded elements: the first sector of a
+    shape times both kernels and uses the faster; a second sector of the same
+    shape (other parameters) inherits the choice without timing."""
+    shape = (2, 5, 6, 5)  # Norb=2, Nbath=5 (Ns=12), sector (6,5): D = 731,808
+    m1 = make_model(shape[0], shape[1], U=2.0, Jh=0.3, seed=41)
+    m2 = make_model(shape[0], shape[1], U=3.5, Jh=0.6, seed=42)
+    s1 = ed.Sector(m1, shape[2], shape[3])
+    k1, ms1 = s1.tune_info("fp32")
+    s2 = ed.Sector(m2, shape[2], shape[3])
+    k2, ms2 = s2.tune_info("fp32")
+    assert k1 == k2 and k1 in ("tiled", "elementwise")
+    assert ms2 == {"tiled": -1.0, "elementwise": -1.0}
+    if ms1["tiled"] >= 0:  # this process had not tuned the shape before
+        assert ms1["elementwise"] > 0 and ms1["tiled"] > 0
+        assert k1 == ("elementwise" if ms1["elementwise"] < ms1["tiled"] else "tiled")
+    # below the tuning range the element-parallel kernel is used without timing
+    s3 = ed.Sector(make_model(1, 7, U=2.0, seed=43), 4, 4)
+    assert s3.tune_info("fp32") == ("elementwise", {"tiled": -1.0, "elementwise": -1.0})
+    for s in (s1, s2, s3):
+        s.free()
 
 
 @pytest.mark.parametrize("maker,prec", [(workload_ns16, "fp64"), (workload_ns18, "fp32")])
