@@ -180,16 +180,17 @@ ed_status ed_matvec_blocked(ed_sector s, ed_precision prec, const void *d_v, voi
 ed_status ed_sector_blocked_kernel(ed_sector s, ed_precision prec, int32_t *kernel);
 
 /* Autotuner (no counterpart in the paper).  Sectors of at most 2^17 padded
- * elements use the element-parallel kernel and sectors above 2^24 the tiled
- * family; in between the first sector of each shape (Norb, Nbath, N_up,
- * N_dw, precision) times both kernels (one warm-up and three launches each,
- * on a scratch vector) when its block-major tables are built, and every
- * sector of that shape in the process then uses the faster one.
+ * elements use the element-parallel kernel; above that the first sector of
+ * each shape (Norb, Nbath, N_up, N_dw, precision) times the tiled family and
+ * the element-parallel kernel (one warm-up and three launches each, on two
+ * scratch vectors of the sector's size) when its block-major tables are
+ * built, and every sector of that shape in the process then uses the faster
+ * one.
  * ed_sector_tune_info returns the kernel in use and host_ms[0..1], the
  * measured milliseconds of the tiled and the element-parallel product
  * (-1 where this sector did not time them).  ed_sector_set_kernel pins a
- * kernel for one sector and precision: ED_KERNEL_ELEMENTWISE (sectors of at
- * most 2^24 padded elements) or the tiled family (ED_KERNEL_TILED, or
+ * kernel for one sector and precision: ED_KERNEL_ELEMENTWISE or the tiled
+ * family (ED_KERNEL_TILED, or
  * ED_KERNEL_TWO_PASS where the block sizes call for two passes); other
  * requests give ED_ERR_UNSUPPORTED.  All kernels compute the same w = H v bit
  * for bit; Lanczos runs differ only in the summation order of <v, w>. */

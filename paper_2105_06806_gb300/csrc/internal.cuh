@@ -285,6 +285,7 @@ struct HvTables {
   int64_t nditems;
   const int4 *small_cols;  // non-null: element-parallel product (small sectors)
   int64_t small_grid;      // its CTAs (= block partials of the Lanczos mode)
+  int32_t small_chunk;     // its elements per thread
 };
 // layout 0: sector (paper) order; 1: block-major order
 template <typename T>

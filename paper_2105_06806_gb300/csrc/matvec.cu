@@ -126,18 +126,40 @@ __device__ __forceinline__ void vec_get(const float2 &v, float *x) {
 }
 
 // Element-parallel product (one thread per element of the padded block-major
-// vector).  Below EDGB_TUNE_MIN elements the tiled kernel has too few work
-// items to fill the GPU and its time is set by the serial per-thread tile, so
-// one thread per element is used; above EDGB_TUNE_MAX the tiled kernel's
-// reuse of staged rows and ELL entries wins.  In between, which one is faster
-// depends on the block shapes of the sector: the autotuner times both.
+// vector, striding for large sectors).  Below EDGB_TUNE_MIN elements the
+// tiled kernel has too few work items to fill the GPU and its time is set by
+// the serial per-thread tile, so the element-parallel kernel is used; above
+// it, which one is faster depends on the block shapes and the precision (the
+// tiled kernel reuses staged rows and ELL entries, the element-parallel one
+// keeps more loads in flight): the autotuner times both.
 constexpr int HVS_THREADS = 256;
 #ifndef EDGB_TUNE_MIN
 #define EDGB_TUNE_MIN (1 << 17)
 #endif
-#ifndef EDGB_TUNE_MAX
-#define EDGB_TUNE_MAX (1 << 24)
+// Elements per thread of the element-parallel product: 1 up to
+// EDGB_SMALL_PARTS CTAs, then K, so that the grid (= the Lanczos partials)
+// stays within EDGB_SMALL_PARTS.  CTA b takes the K consecutive 256-element
+// chunks b*K .. b*K+K-1: CTAs are dispatched in order, so the part of the
+// vector in flight stays a compact window of (resident CTAs) x K chunks, and
+// the H_dw neighbour rows that nearby rows share are still in L2 when they
+// are read again.  (A grid-stride loop over one resident wave measured 1.9x
+// slower at 2.4e9 elements: its CTAs drift apart and the window spreads over
+// the whole vector.)  One CTA sums the partials every Lanczos step: at
+// D = 1.66e8 an FP32 step takes 3.2 ms with 2^16 partials, 3.7 ms with
+// 2.2e5 and 5.3 ms with 6.5e5 (one element per thread), while the product
+// itself stays within 4% of one element per thread at every size.
+#ifndef EDGB_SMALL_PARTS
+#define EDGB_SMALL_PARTS (1 << 16)
 #endif
+static int64_t small_chunk_of(int64_t n) {
+  const int64_t nblk = (n + HVS_THREADS - 1) / HVS_THREADS;
+  return std::max<int64_t>(1, (nblk + EDGB_SMALL_PARTS - 1) / EDGB_SMALL_PARTS);
+}
+static int64_t small_grid_of(int64_t n) {
+  const int64_t nblk = (n + HVS_THREADS - 1) / HVS_THREADS;
+  const int64_t k = small_chunk_of(n);
+  return (nblk + k - 1) / k;
+}
 
 template <typename T>
 static void fill_tables(HvTables<T> &t, const SpinTables &u, const SpinTables &d, const T *vu,
@@ -174,7 +196,8 @@ HvTables<double> ed_hv_tables<double>(ed_sector s, int layout) {
   t.ell_col = layout == 0 ? nullptr : s->ell_col;
   t.ell_val = layout == 0 ? nullptr : s->ell_v64;
   t.small_cols = (layout == 1 && s->hv_kernel[1] == 1) ? s->small_cols : nullptr;
-  t.small_grid = t.small_cols ? (s->bdim + HVS_THREADS - 1) / HVS_THREADS : 0;
+  t.small_grid = t.small_cols ? small_grid_of(s->bdim) : 0;
+  t.small_chunk = (int32_t)small_chunk_of(s->bdim);
   return t;
 }
 template <>
@@ -193,7 +216,8 @@ HvTables<float> ed_hv_tables<float>(ed_sector s, int layout) {
   t.ell_col = layout == 0 ? nullptr : s->ell_col;
   t.ell_val = layout == 0 ? nullptr : s->ell_v32;
   t.small_cols = (layout == 1 && s->hv_kernel[0] == 1) ? s->small_cols : nullptr;
-  t.small_grid = t.small_cols ? (s->bdim + HVS_THREADS - 1) / HVS_THREADS : 0;
+  t.small_grid = t.small_cols ? small_grid_of(s->bdim) : 0;
+  t.small_chunk = (int32_t)small_chunk_of(s->bdim);
   return t;
 }
 
@@ -367,7 +391,7 @@ ed_status ed_build_ell(ed_sector s, cudaStream_t st) {
 // after the ELL table.  Sectors whose blocks do not fit the packing stay on
 // the tiled kernel.
 static ed_status build_small_cols(ed_sector s, cudaStream_t cs) {
-  if (s->small_cols || s->bdim == 0 || s->bdim > (int64_t)EDGB_TUNE_MAX) return ED_OK;
+  if (s->small_cols || s->bdim == 0) return ED_OK;
   const BlockInfo &b = s->bi[0];
   std::vector<int4> cols(s->bstride);
   for (int k = 0; k < b.nblocks; ++k) {
@@ -443,14 +467,14 @@ static ed_status build_dw_items(ed_sector s, ItemList &il, int elem, cudaStream_
 
 // ----------------------------------------------------------------- autotuner
 //
-// For sectors between EDGB_TUNE_MIN and EDGB_TUNE_MAX padded elements the
-// faster of the tiled and the element-parallel product depends on the block
-// shapes, so it is measured: both kernels, one warm-up and three timed
-// launches each on a scratch vector, on this thread's private stream.  The
-// choice is kept per sector shape (Norb, Nbath, N_up, N_dw, precision) for
-// the life of the process, so every sector of a shape uses the same kernel
-// and results do not depend on which call came first.  Both kernels give the
-// same w = H v bit for bit.
+// For sectors above EDGB_TUNE_MIN padded elements the faster of the tiled
+// family (one or two passes) and the element-parallel product depends on the
+// block shapes and the precision, so it is measured: both kernels, one
+// warm-up and three timed launches each (alternating) on a scratch vector,
+// on this thread's private stream.  The choice is kept per sector shape
+// (Norb, Nbath, N_up, N_dw, precision) for the life of the process, so every
+// sector of a shape uses the same kernel and results do not depend on which
+// call came first.  Both kernels give the same w = H v bit for bit.
 namespace {
 struct TuneKey {
   int norb, nbath, nup, ndw, elem;
@@ -473,20 +497,23 @@ static ed_status time_hv_kernels(ed_sector s, int e, cudaStream_t cs, double ms[
   if (cudaMemsetAsync(mem, 0, 2 * n * sizeof(T), cs) != cudaSuccess ||
       cudaEventCreate(&ev[0]) != cudaSuccess || cudaEventCreate(&ev[1]) != cudaSuccess)
     rs = ED_ERR_CUDA;
-  for (int k = 0; k < 2 && rs == ED_OK; ++k) {
-    s->hv_kernel[e] = (int8_t)k;
-    const HvTables<T> tb = ed_hv_tables<T>(s, 1);
-    rs = ed_launch_hv<T>(s, tb, HV_PLAIN, v, w, nullptr, nullptr, nullptr, nullptr, nullptr, cs);
-    if (rs == ED_OK && cudaEventRecord(ev[0], cs) != cudaSuccess) rs = ED_ERR_CUDA;
-    for (int r = 0; r < 3 && rs == ED_OK; ++r)
-      rs = ed_launch_hv<T>(s, tb, HV_PLAIN, v, w, nullptr, nullptr, nullptr, nullptr, nullptr, cs);
-    float t = 0.0f;
-    if (rs == ED_OK && (cudaEventRecord(ev[1], cs) != cudaSuccess ||
-                        cudaEventSynchronize(ev[1]) != cudaSuccess ||
-                        cudaEventElapsedTime(&t, ev[0], ev[1]) != cudaSuccess))
-      rs = ED_ERR_CUDA;
-    ms[k] = t / 3.0;
-  }
+  // one warm-up launch of each kernel, then three rounds that alternate the
+  // two, so that a clock that is still ramping up favours neither
+  ms[0] = ms[1] = 0.0;
+  for (int r = -1; r < 3 && rs == ED_OK; ++r)
+    for (int k = 0; k < 2 && rs == ED_OK; ++k) {
+      s->hv_kernel[e] = (int8_t)k;
+      const HvTables<T> tb = ed_hv_tables<T>(s, 1);
+      if (cudaEventRecord(ev[0], cs) != cudaSuccess) rs = ED_ERR_CUDA;
+      if (rs == ED_OK)
+        rs = ed_launch_hv<T>(s, tb, HV_PLAIN, v, w, nullptr, nullptr, nullptr, nullptr, nullptr, cs);
+      float t = 0.0f;
+      if (rs == ED_OK && (cudaEventRecord(ev[1], cs) != cudaSuccess ||
+                          cudaEventSynchronize(ev[1]) != cudaSuccess ||
+                          cudaEventElapsedTime(&t, ev[0], ev[1]) != cudaSuccess))
+        rs = ED_ERR_CUDA;
+      if (r >= 0) ms[k] += t / 3.0;
+    }
   for (cudaEvent_t x : ev)
     if (x) cudaEventDestroy(x);
   ed_dfree(mem, cs);
@@ -1028,7 +1055,7 @@ __global__ void __launch_bounds__(DW_THREADS) k_hv_dw(HvLaunch<T> a) {
 // order as in k_hv: the diagonal, the H_up entries in ELL order, the H_dw
 // entries in CSR order, then the same epilogue; the Lanczos mode leaves one
 // partial of <v_j, w1> per CTA.
-template <typename T, int MODE>
+template <typename T, int MODE, bool CHUNKED>
 __global__ void __launch_bounds__(HVS_THREADS) k_hv_small(HvLaunch<T> a) {
   __shared__ double red[HVS_THREADS / 32];
   const HvTables<T> &tb = a.tb;
@@ -1062,9 +1089,19 @@ __global__ void __launch_bounds__(HVS_THREADS) k_hv_small(HvLaunch<T> a) {
     }
   }
   const int64_t stride = tb.stride;
-  const int64_t gi = blockIdx.x * (int64_t)HVS_THREADS + threadIdx.x;
   T dot = T(0);
-  if (gi < tb.ddw * stride) {
+  double dot_sum = 0.0;  // the per-thread sum, flushed from T every 16 elements
+  const int64_t n = tb.ddw * stride;
+  // one element per thread unless CHUNKED (separate instances: the chunk loop
+  // costs registers, and the small sectors run at full occupancy without it)
+  const int K = CHUNKED ? tb.small_chunk : 1;
+  for (int k = 0; k < K; ++k) {
+    const int64_t gi = ((int64_t)blockIdx.x * K + k) * HVS_THREADS + threadIdx.x;
+    if (gi >= n) break;
+    if (CHUNKED && MODE == HV_LANCZOS && (k & 15) == 15) {
+      dot_sum += (double)dot;
+      dot = T(0);
+    }
     const int64_t r = gi / stride;
     const int pc = (int)(gi - r * stride);
     const int4 ci = __ldg(tb.small_cols + pc);
@@ -1089,7 +1126,7 @@ __global__ void __launch_bounds__(HVS_THREADS) k_hv_small(HvLaunch<T> a) {
         if (j > 0) w1 = fma_t<T>(-beta_j, mul_t<T>(prev[gi], s_prev), w1);
         if (MODE == HV_LANCZOS) {
           out[gi] = w1;
-          dot = mul_t<T>(v, w1);
+          dot = fma_t<T>(v, w1, dot);
         } else {
           out[gi] = fma_t<T>(-alpha_j, v, w1);
           a.psi[gi] = fma_t<T>(y_j, v, a.psi[gi]);
@@ -1098,15 +1135,14 @@ __global__ void __launch_bounds__(HVS_THREADS) k_hv_small(HvLaunch<T> a) {
     }
   }
   if (MODE == HV_LANCZOS) {
-    double smv = block_sum<T>((double)dot, red);
+    double smv = block_sum<T>(dot_sum + (double)dot, red);
     if (threadIdx.x == 0) a.part[blockIdx.x] = smv;
   }
 }
 
 int64_t ed_hv_num_parts(ed_sector s, int layout, int elem_size) {
   if (ed_build_items(s, layout, elem_size) != ED_OK) return 0;
-  if (layout == 1 && s->hv_kernel[elem_size == 8 ? 1 : 0] == 1)
-    return (s->bdim + HVS_THREADS - 1) / HVS_THREADS;
+  if (layout == 1 && s->hv_kernel[elem_size == 8 ? 1 : 0] == 1) return small_grid_of(s->bdim);
   const ItemList &il = s->items[layout][elem_size == 8 ? 1 : 0];
   return il.d_ditems ? il.nditems : il.nitems;
 }
@@ -1151,7 +1187,10 @@ template ed_status ed_hv_prepare<double>();
 template <typename T, int MODE>
 static ed_status launch_mode(const HvLaunch<T> &a, cudaStream_t st) {
   if (a.tb.small_cols) {
-    k_hv_small<T, MODE><<<(unsigned)a.tb.small_grid, HVS_THREADS, 0, st>>>(a);
+    if (a.tb.small_chunk > 1)
+      k_hv_small<T, MODE, true><<<(unsigned)a.tb.small_grid, HVS_THREADS, 0, st>>>(a);
+    else
+      k_hv_small<T, MODE, false><<<(unsigned)a.tb.small_grid, HVS_THREADS, 0, st>>>(a);
   } else if (a.tb.ditems) {
     k_hv<T, MODE, true, true, rt_passa<T>(), PASSA_THREADS>
         <<<(unsigned)a.tb.nitems, PASSA_THREADS, a.tb.smem, st>>>(a);
@@ -1263,7 +1302,7 @@ extern "C" ed_status ed_sector_set_kernel(ed_sector s, ed_precision prec, int32_
   ED_TRY(kernel_of(s, prec, &e, &cur));
   if (kernel == ED_KERNEL_ELEMENTWISE) {
     if (!s->small_cols) {
-      ed_set_error_msg("the element-parallel product needs a sector of at most 2^24 padded elements");
+      ed_set_error_msg("this sector's blocks do not fit the element-parallel column table");
       return ED_ERR_UNSUPPORTED;
     }
     s->hv_kernel[e] = 1;

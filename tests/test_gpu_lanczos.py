@@ -124,6 +124,34 @@ def test_ns16_fp32_polish_against_fp64_gpu(ed):
     s.free()
 
 
+def test_chunked_elementwise_lanczos_against_tiled(ed):
+    """Ns=15 (D = 41,409,225): the element-parallel product takes 3 elements
+    per thread here (its Lanczos partials are capped at 2^16), so the
+    Lanczos inner product sums chunks of the vector per thread.  Ground
+    energies with that kernel pinned agree with the tiled kernel's (whose
+    products are pinned against the oracle) in FP64, FP32 and FP32 + polish,
+    and the FP64 runs satisfy the residual bound."""
+    m = make_model(1, 14, U=3.0, e_d=-1.5, seed=31)
+    s = ed.Sector(m, 7, 7)
+    assert s.blocked_dim > 256 * (1 << 16)
+    res = {}
+    for kernel in ("tiled", "elementwise"):
+        for p in ("fp32", "fp64"):
+            try:
+                s.set_kernel(kernel, p)
+            except ed.EDError:  # the tiled family takes two passes here
+                s.set_kernel("two_pass", p)
+        res[kernel] = {p: ed.lanczos_ground(s, p) for p in ("fp64", "fp32", "fp32_polish")}
+    a, b = res["tiled"], res["elementwise"]
+    e = a["fp64"]["e0"]
+    assert a["fp64"]["residual"] < 1e-6 and b["fp64"]["residual"] < 1e-6
+    assert abs(b["fp64"]["e0"] - e) <= 1e-10 * abs(e)
+    assert abs(b["fp32"]["e0"] - e) <= 1e-6 * abs(e)
+    assert abs(b["fp32_polish"]["e0"] - e) <= 1e-10 * abs(e)
+    assert abs(a["fp32_polish"]["e0"] - e) <= 1e-10 * abs(e)
+    s.free()
+
+
 @pytest.mark.parametrize("case", ["ns8_fp64", "norb2_ns10_fp32_polish"])
 def test_kept_basis_equals_second_pass(ed, case):
     """psi from the Krylov basis kept during the first pass, from the second

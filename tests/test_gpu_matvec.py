@@ -223,7 +223,7 @@ def test_blocked_kernels_against_oracle(ed, ci, prec):
 
 
 def test_autotuner_picks_the_faster_kernel_per_shape(ed):
-    """Sectors between 2^17 and 2^24 padded elements: the first sector of a
+    """Sectors above 2^17 padded elements: the first sector of a
     shape times both kernels and uses the faster; a second sector of the same
     shape (other parameters) inherits the choice without timing."""
     shape = (2, 5, 6, 5)  # Norb=2, Nbath=5 (Ns=12), sector (6,5): D = 731,808
@@ -245,17 +245,22 @@ def test_autotuner_picks_the_faster_kernel_per_shape(ed):
         s.free()
 
 
-@pytest.mark.parametrize("maker,prec", [(workload_ns16, "fp64"), (workload_ns18, "fp32")])
-def test_two_pass_full_size_sampled(ed, maker, prec):
-    """Sectors whose block pairs exceed L2 take the two-pass block-major
-    product (H_up pass, then H_dw pass over column chunks): the full-size
-    product in the launch configuration of the Lanczos runs, checked on
-    sampled outputs against the oracle (input a closed-form function of the
-    sector index)."""
+@pytest.mark.parametrize("maker,prec,kernel", [
+    (workload_ns16, "fp64", "two_pass"), (workload_ns16, "fp64", "elementwise"),
+    (workload_ns18, "fp32", "two_pass"), (workload_ns18, "fp32", "elementwise")])
+def test_full_size_sampled(ed, maker, prec, kernel):
+    """The full-size products of the Lanczos runs, checked on sampled outputs
+    against the oracle (input a closed-form function of the sector index):
+    the two-pass block-major product (H_up pass, then H_dw pass over column
+    chunks; taken where the block pairs exceed L2) and the element-parallel
+    product with several chunks of 256 elements per CTA (10 at Ns=16, 141
+    at Ns=18), the two kernels the autotuner chooses between at these
+    sizes."""
     wl = maker(0)
     m = wl.model
     s = ed.Sector(m, wl.nup, wl.ndw)
-    assert s.blocked_kernel(prec) == "two_pass"
+    s.set_kernel(kernel, prec)
+    assert s.blocked_kernel(prec) == kernel
     dup, ddw, n = s.dim_up, s.dim_dw, s.dim
     dt = torch.float64 if prec == "fp64" else torch.float32
     v = torch.empty(n, device="cuda", dtype=dt)
