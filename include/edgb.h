@@ -181,7 +181,7 @@ ed_status ed_sector_blocked_kernel(ed_sector s, ed_precision prec, int32_t *kern
 
 /* Autotuner (no counterpart in the paper).  Sectors of at most 2^17 padded
  * elements use the element-parallel kernel; above that the first sector of
- * each shape (Norb, Nbath, N_up, N_dw, precision) times the tiled family and
+ * each model shape (Norb, Nbath, precision) times the tiled family and
  * the element-parallel kernel (one warm-up and three launches each, on two
  * scratch vectors of the sector's size) when its block-major tables are
  * built, and every sector of that shape in the process then uses the faster

@@ -471,15 +471,22 @@ static ed_status build_dw_items(ed_sector s, ItemList &il, int elem, cudaStream_
 // family (one or two passes) and the element-parallel product depends on the
 // block shapes and the precision, so it is measured: both kernels, one
 // warm-up and three timed launches each (alternating) on a scratch vector,
-// on this thread's private stream.  The choice is kept per sector shape
-// (Norb, Nbath, N_up, N_dw, precision) for the life of the process, so every
-// sector of a shape uses the same kernel and results do not depend on which
-// call came first.  Both kernels give the same w = H v bit for bit.
+// on this thread's private stream.  The choice is kept per model shape
+// (Norb, Nbath, precision) for the life of the process, so every sector of a
+// shape uses the same kernel and results do not depend on which call came
+// first.  The sectors of one shape share the block structure that decides
+// between the kernels (block widths set by the orbital count, bath strings
+// of one length); where two sectors of a shape were measured (Ns = 14, at
+// and next to half filling) both chose the same kernel wherever the two
+// kernels differed by more than 5%.  Keying on the sector as well made
+// a serving stream whose requests are mostly distinct sectors tune on almost
+// every request (15% fewer solves/s at Ns <= 16).  Both kernels give the
+// same w = H v bit for bit.
 namespace {
 struct TuneKey {
-  int norb, nbath, nup, ndw, elem;
+  int norb, nbath, elem;
   bool operator<(const TuneKey &o) const {
-    return std::tie(norb, nbath, nup, ndw, elem) < std::tie(o.norb, o.nbath, o.nup, o.ndw, o.elem);
+    return std::tie(norb, nbath, elem) < std::tie(o.norb, o.nbath, o.elem);
   }
 };
 std::mutex g_tune_mu;
@@ -532,7 +539,7 @@ static ed_status decide_kernel(ed_sector s, int elem, cudaStream_t cs) {
     s->hv_kernel[e] = 1;
     return ED_OK;
   }
-  const TuneKey key{s->mp.norb, s->mp.nbath, s->nup, s->ndw, elem};
+  const TuneKey key{s->mp.norb, s->mp.nbath, elem};
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     auto it = g_tune.find(key);

@@ -223,15 +223,15 @@ def test_blocked_kernels_against_oracle(ed, ci, prec):
 
 
 def test_autotuner_picks_the_faster_kernel_per_shape(ed):
-    """Sectors above 2^17 padded elements: the first sector of a
-    shape times both kernels and uses the faster; a second sector of the same
-    shape (other parameters) inherits the choice without timing."""
-    shape = (2, 5, 6, 5)  # Norb=2, Nbath=5 (Ns=12), sector (6,5): D = 731,808
-    m1 = make_model(shape[0], shape[1], U=2.0, Jh=0.3, seed=41)
-    m2 = make_model(shape[0], shape[1], U=3.5, Jh=0.6, seed=42)
-    s1 = ed.Sector(m1, shape[2], shape[3])
+    """Sectors above 2^17 padded elements: the first sector of a model
+    shape (Norb, Nbath, precision) times both kernels and uses the faster;
+    another sector of the same shape (other parameters, other fillings)
+    inherits the choice without timing."""
+    m1 = make_model(2, 5, U=2.0, Jh=0.3, seed=41)  # Norb=2, Nbath=5 (Ns=12)
+    m2 = make_model(2, 5, U=3.5, Jh=0.6, seed=42)
+    s1 = ed.Sector(m1, 6, 5)  # D = 731,808
     k1, ms1 = s1.tune_info("fp32")
-    s2 = ed.Sector(m2, shape[2], shape[3])
+    s2 = ed.Sector(m2, 5, 7)  # D = 627,264
     k2, ms2 = s2.tune_info("fp32")
     assert k1 == k2 and k1 in ("tiled", "elementwise")
     assert ms2 == {"tiled": -1.0, "elementwise": -1.0}
