@@ -768,6 +768,8 @@ __device__ __forceinline__ void hv_tile(const HvTables<T> &tb, const HvItem &it,
     const T *dv = s_dval + (lr0 + i) * ED_MAX_NS;
     int t = 0;
     if (BLK) {
+      // two neighbour rows in flight (four measured 5% slower: spills at the
+      // 64-register cap)
       for (; t + 2 <= n; t += 2) {
         T y[2][4];
 #pragma unroll
@@ -813,33 +815,44 @@ __global__ void __launch_bounds__(NT, NT >= 1024 ? 1 : EDGB_MIN_CTAS) k_hv(HvLau
   T *sm = reinterpret_cast<T *>(smem_raw);
   const HvTables<T> &tb = a.tb;
 
-  int j = 0;
-  T s_cur = T(1), s_prev = T(0), beta_j = T(0), alpha_j = T(0), y_j = T(0);
+  // Epilogue state of the Lanczos modes, kept in shared memory and read in
+  // the epilogue only: held in registers across the tile it made the
+  // Lanczos-mode kernel spill at the 64-register cap (152 bytes; the FP32
+  // Lanczos step at D = 1.66e8 went from 2.60 to 2.46 ms without them).
+  struct EpState {
+    T *out;
+    const T *prev;
+    T s_cur, s_prev, beta_j, alpha_j, y_j;
+    int j;
+  };
+  __shared__ EpState ep_s;
   const T *g;
-  const T *prev = nullptr;
-  T *out;
+  T *out_plain = nullptr;
   if (MODE == HV_PLAIN) {
     g = a.v;
-    out = a.w;
+    out_plain = a.w;
   } else {
     const LanczosState *st = a.st;
     if (MODE == HV_LANCZOS && st->done) return;
-    j = st->j;
+    const int j = st->j;
     T *bufs[3] = {a.b0, a.b1, a.b2};
     g = bufs[j % 3];
-    prev = bufs[(j + 2) % 3];
-    out = bufs[(j + 1) % 3];
-    if (MODE == HV_LANCZOS && a.basis) {
-      g = a.basis[j];
-      prev = a.basis[j > 0 ? j - 1 : 0];
-      out = a.basis[j + 1];
-    }
-    s_cur = (T)st->scale[j % 3];
-    s_prev = (T)st->scale[(j + 2) % 3];
-    beta_j = (T)st->beta[j];
-    if (MODE == HV_SECOND) {
-      alpha_j = (T)st->alpha[j];
-      y_j = (T)st->y[j];
+    if (MODE == HV_LANCZOS && a.basis) g = a.basis[j];
+    if (threadIdx.x == 0) {
+      EpState e;
+      e.j = j;
+      e.prev = bufs[(j + 2) % 3];
+      e.out = bufs[(j + 1) % 3];
+      if (MODE == HV_LANCZOS && a.basis) {
+        e.prev = a.basis[j > 0 ? j - 1 : 0];
+        e.out = a.basis[j + 1];
+      }
+      e.s_cur = (T)st->scale[j % 3];
+      e.s_prev = (T)st->scale[(j + 2) % 3];
+      e.beta_j = (T)st->beta[j];
+      e.alpha_j = MODE == HV_SECOND ? (T)st->alpha[j] : T(0);
+      e.y_j = MODE == HV_SECOND ? (T)st->y[j] : T(0);
+      ep_s = e;
     }
   }
 
@@ -899,6 +912,8 @@ __global__ void __launch_bounds__(NT, NT >= 1024 ? 1 : EDGB_MIN_CTAS) k_hv(HvLau
         hv_tile<T, false, BLK, PASSA, RT>(tb, it, g, smq, staged, lr0, nrt, cb, s_dn, s_dcol,
                                           s_dval, s_mdw, s_edw, acc);
       // epilogue
+      const volatile EpState &ep = ep_s;
+      T *const out = MODE == HV_PLAIN ? out_plain : ep.out;
 #pragma unroll
       for (int i = 0; i < RT; ++i) {
         if (i >= nrt) continue;
@@ -911,16 +926,17 @@ __global__ void __launch_bounds__(NT, NT >= 1024 ? 1 : EDGB_MIN_CTAS) k_hv(HvLau
           if (MODE == HV_PLAIN || PASSA) {
             out[gi] = acc[u][i];
           } else {
+            const T s_cur = ep.s_cur;
             const T xv = staged ? smq[(size_t)stage_pos(c, ncp >> 2) * RT + i] : g[gi];
             const T v = mul_t<T>(xv, s_cur);
             T w1 = mul_t<T>(acc[u][i], s_cur);
-            if (j > 0) w1 = fma_t<T>(-beta_j, mul_t<T>(prev[gi], s_prev), w1);
+            if (ep.j > 0) w1 = fma_t<T>(-ep.beta_j, mul_t<T>(ep.prev[gi], ep.s_prev), w1);
             if (MODE == HV_LANCZOS) {
               out[gi] = w1;
               dot = fma_t<T>(v, w1, dot);
             } else {
-              out[gi] = fma_t<T>(-alpha_j, v, w1);
-              a.psi[gi] = fma_t<T>(y_j, v, a.psi[gi]);
+              out[gi] = fma_t<T>(-ep.alpha_j, v, w1);
+              a.psi[gi] = fma_t<T>(ep.y_j, v, a.psi[gi]);
             }
           }
         }
