@@ -152,8 +152,8 @@ ed_status ed_matvec(ed_sector s, ed_precision prec, const void *d_v, void *d_w, 
  * blocked_dim = D_dw * blocked_stride).
  *
  * ed_matvec_blocked: w = H v with v, w block-major vectors of
- * n = blocked_dim elements (same element types as ed_matvec); the padding
- * of w is not written.  ed_sector_permute: converts between a sector-order
+ * n = blocked_dim elements (same element types as ed_matvec), both 16-byte
+ * aligned (ED_ERR_ARG otherwise); the padding of w is not written.  ed_sector_permute: converts between a sector-order
  * D-vector and a block-major vector (to_blocked = 1: sector -> blocked,
  * padding written as zero); n_in / n_out are the element counts of the two
  * arrays; d_in and d_out must not overlap.  Both return ED_ERR_ARG when a

@@ -110,6 +110,13 @@ __device__ __forceinline__ void load4(const double *p, double *y) {
   y[3] = b.y;
 }
 
+__device__ __forceinline__ void store4(float *p, const float *y) {
+  *reinterpret_cast<float4 *>(p) = make_float4(y[0], y[1], y[2], y[3]);
+}
+__device__ __forceinline__ void store4(double *p, const double *y) {
+  reinterpret_cast<double2 *>(p)[0] = make_double2(y[0], y[1]);
+  reinterpret_cast<double2 *>(p)[1] = make_double2(y[2], y[3]);
+}
 __device__ __forceinline__ void vec_get(const float4 &v, float *x) {
   x[0] = v.x;
   x[1] = v.y;
@@ -935,33 +942,71 @@ __global__ void __launch_bounds__(NT, NT >= 1024 ? 1 : EDGB_MIN_CTAS) k_hv(HvLau
       else
         hv_tile<T, false, BLK, PASSA, RT>(tb, it, g, smq, staged, lr0, nrt, cb, s_dn, s_dcol,
                                           s_dval, s_mdw, s_edw, acc);
-      // epilogue
+      // epilogue: one 16-byte store (and, in the Lanczos modes, one 16-byte
+      // load of v_{j-1}) per row of a full tile in the block-major layout,
+      // whose rows and blocks are padded to multiples of 4 elements (the
+      // sector-order layout is not aligned: element accesses there)
+      const bool vec = BLK && full;
       const volatile EpState &ep = ep_s;
       T *const out = MODE == HV_PLAIN ? out_plain : ep.out;
+      if (MODE == HV_PLAIN || PASSA) {
 #pragma unroll
-      for (int i = 0; i < RT; ++i) {
-        if (i >= nrt) continue;
-        const int64_t rowbase = (int64_t)(r0 + lr0 + i) * stride + cp0;
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const int c = cb + u;
-          if (c >= nc) continue;
-          const int64_t gi = rowbase + c;
-          if (MODE == HV_PLAIN || PASSA) {
-            out[gi] = acc[u][i];
+        for (int i = 0; i < RT; ++i) {
+          if (i >= nrt) continue;
+          T *o = out + (int64_t)(r0 + lr0 + i) * stride + cp0 + cb;
+          if (vec) {
+            const T res[4] = {acc[0][i], acc[1][i], acc[2][i], acc[3][i]};
+            store4(o, res);
           } else {
-            const T s_cur = ep.s_cur;
-            const T xv = staged ? smq[(size_t)stage_pos(c, ncp >> 2) * RT + i] : g[gi];
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+              if (cb + u < nc) o[u] = acc[u][i];
+          }
+        }
+      } else {
+        // the step's scalars, read from shared memory once per tile
+        const T s_cur = ep.s_cur, s_prev = ep.s_prev, beta_j = ep.beta_j;
+        const T alpha_j = ep.alpha_j, y_j = ep.y_j;
+        const T *const prev = ep.prev;
+        const bool has_prev = ep.j > 0;
+#pragma unroll
+        for (int i = 0; i < RT; ++i) {
+          if (i >= nrt) continue;
+          const int64_t rb = (int64_t)(r0 + lr0 + i) * stride + cp0 + cb;
+          T pv[4] = {T(0), T(0), T(0), T(0)};
+          if (has_prev) {
+            if (vec) {
+              load4(prev + rb, pv);
+            } else {
+#pragma unroll
+              for (int u = 0; u < 4; ++u)
+                if (cb + u < nc) pv[u] = prev[rb + u];
+            }
+          }
+          T res[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int c = cb + u;
+            res[u] = T(0);
+            if (!full && c >= nc) continue;
+            const T xv = staged ? smq[(size_t)stage_pos(c, ncp >> 2) * RT + i] : g[rb + u];
             const T v = mul_t<T>(xv, s_cur);
             T w1 = mul_t<T>(acc[u][i], s_cur);
-            if (ep.j > 0) w1 = fma_t<T>(-ep.beta_j, mul_t<T>(ep.prev[gi], ep.s_prev), w1);
+            if (has_prev) w1 = fma_t<T>(-beta_j, mul_t<T>(pv[u], s_prev), w1);
             if (MODE == HV_LANCZOS) {
-              out[gi] = w1;
+              res[u] = w1;
               dot = fma_t<T>(v, w1, dot);
             } else {
-              out[gi] = fma_t<T>(-ep.alpha_j, v, w1);
-              a.psi[gi] = fma_t<T>(ep.y_j, v, a.psi[gi]);
+              res[u] = fma_t<T>(-alpha_j, v, w1);
+              a.psi[rb + u] = fma_t<T>(y_j, v, a.psi[rb + u]);
             }
+          }
+          if (vec) {
+            store4(out + rb, res);
+          } else {
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+              if (cb + u < nc) out[rb + u] = res[u];
           }
         }
       }
@@ -1288,6 +1333,14 @@ static ed_status matvec_layout(ed_sector s, ed_precision prec, const void *d_v, 
   if (!s || !d_v || !d_w || d_v == d_w) return ED_ERR_ARG;
   if (n != (layout == 0 ? s->dim : s->bdim)) {
     ed_set_error_msg("vector length does not match the sector layout");
+    return ED_ERR_ARG;
+  }
+  // block-major rows are read and written as 16-byte vectors; sector-order
+  // elements need their natural alignment
+  const uintptr_t amask = layout == 1 ? 15 : (prec == ED_FP64 ? 7 : 3);
+  if (((uintptr_t)d_v | (uintptr_t)d_w) & amask) {
+    ed_set_error_msg(layout == 1 ? "block-major vectors must be 16-byte aligned"
+                                 : "vectors must be aligned to their element size");
     return ED_ERR_ARG;
   }
   cudaStream_t st = (cudaStream_t)stream;

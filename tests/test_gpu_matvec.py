@@ -309,4 +309,10 @@ def test_vector_length_checked(ed):
         ed.matvec(s, vb, torch.zeros_like(vb))
     with pytest.raises(ed.EDError):
         ed.permute(s, v, torch.zeros_like(v), True)
+    # block-major vectors are accessed as 16-byte vectors: an offset view of
+    # the right length is rejected on the host
+    big = torch.zeros(s.blocked_dim + 1, dtype=torch.float64, device="cuda")
+    with pytest.raises(ed.EDError) as e:
+        ed.matvec_blocked(s, big[1:], torch.zeros_like(vb))
+    assert e.value.status == ed.ED_ERR_ARG
     s.free()
