@@ -286,6 +286,7 @@ struct HvTables {
   const int4 *small_cols;  // non-null: element-parallel product (small sectors)
   int64_t small_grid;      // its CTAs (= block partials of the Lanczos mode)
   int32_t small_chunk;     // its elements per thread
+  bool passa_wide;         // two-pass product: the wide shape of the H_up pass
 };
 // layout 0: sector (paper) order; 1: block-major order
 template <typename T>

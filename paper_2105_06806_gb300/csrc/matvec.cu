@@ -67,8 +67,16 @@ struct Tile<double> {
   static constexpr int CU = 4, RT = 2;
   using V = double2;
 };
-// register tile of a given height (the H_up pass of the two-pass product uses
-// 2 FP32 rows per thread: half the staged rows, two CTAs per SM on wide blocks)
+// register tile of a given height; the H_up pass of the two-pass product
+// has two shapes, chosen per sector by its widest up block:
+//  - narrow blocks (at most EDGB_PASSA_WIDE padded columns): 2 FP32 rows per
+//    thread in 512-thread CTAs, two CTAs per SM;
+//  - wide blocks: 4 FP32 rows per thread in 1024-thread CTAs, one CTA per SM,
+//    the 4 staged rows of a column read with one 16-byte load.
+// Measured per product: three orbitals at Ns=18 (8000-column blocks), FP32,
+// 25.0 ms wide against 26.8 ms narrow; one orbital at Ns=16 (6436 columns)
+// 1.50 ms either way; two orbitals at Ns=16 (4900 columns), FP64, 5.85 ms
+// narrow against 6.47 ms wide.  FP64 keeps 2 rows per thread in both shapes.
 template <typename T, int RTX>
 struct TileOf;
 template <>
@@ -83,15 +91,13 @@ template <>
 struct TileOf<double, 2> {
   using V = double2;
 };
-#ifndef EDGB_PASSA_RT
-#define EDGB_PASSA_RT 2
+#ifndef EDGB_PASSA_WIDE
+#define EDGB_PASSA_WIDE 6000
 #endif
-#ifndef EDGB_PASSA_THREADS
-#define EDGB_PASSA_THREADS 512
-#endif
-template <typename T>
-constexpr int rt_passa() { return sizeof(T) == 4 ? EDGB_PASSA_RT : 2; }
-constexpr int PASSA_THREADS = EDGB_PASSA_THREADS;
+template <typename T, bool WIDE>
+constexpr int rt_passa() { return sizeof(T) == 4 && WIDE ? 4 : 2; }
+template <bool WIDE>
+constexpr int passa_threads() { return WIDE ? 1024 : 512; }
 
 // four consecutive values of a 16-byte aligned row segment
 __device__ __forceinline__ void load4(const float *p, float *y) {
@@ -168,6 +174,8 @@ static int64_t small_grid_of(int64_t n) {
   return (nblk + k - 1) / k;
 }
 
+static bool passa_is_wide(ed_sector s);
+
 template <typename T>
 static void fill_tables(HvTables<T> &t, const SpinTables &u, const SpinTables &d, const T *vu,
                         const T *vd, const T *eu, const T *e_d, const T *W, int norb) {
@@ -205,6 +213,7 @@ HvTables<double> ed_hv_tables<double>(ed_sector s, int layout) {
   t.small_cols = (layout == 1 && s->hv_kernel[1] == 1) ? s->small_cols : nullptr;
   t.small_grid = t.small_cols ? small_grid_of(s->bdim) : 0;
   t.small_chunk = (int32_t)small_chunk_of(s->bdim);
+  t.passa_wide = layout == 1 && passa_is_wide(s);
   return t;
 }
 template <>
@@ -225,6 +234,7 @@ HvTables<float> ed_hv_tables<float>(ed_sector s, int layout) {
   t.small_cols = (layout == 1 && s->hv_kernel[0] == 1) ? s->small_cols : nullptr;
   t.small_grid = t.small_cols ? small_grid_of(s->bdim) : 0;
   t.small_chunk = (int32_t)small_chunk_of(s->bdim);
+  t.passa_wide = layout == 1 && passa_is_wide(s);
   return t;
 }
 
@@ -440,6 +450,14 @@ static bool two_pass_wanted(ed_sector s, int elem) {
   return max_rows * max_cols * elem > ((int64_t)EDGB_TWO_PASS_MB << 20);
 }
 
+// the H_up pass shape of this sector (see rt_passa)
+static bool passa_is_wide(ed_sector s) {
+  int64_t w = 0;
+  for (size_t k = 0; k + 1 < s->up_off_pad.size(); ++k)
+    w = std::max<int64_t>(w, s->up_off_pad[k + 1] - s->up_off_pad[k]);
+  return w > (int64_t)EDGB_PASSA_WIDE;
+}
+
 static ed_status build_dw_items(ed_sector s, ItemList &il, int elem, cudaStream_t cs) {
   if (il.d_ditems || !two_pass_wanted(s, elem)) return ED_OK;
   const std::vector<int64_t> &ob_dw = s->bi[1].offset, &ob_up = s->bi[0].offset;
@@ -611,9 +629,11 @@ ed_status ed_build_items(ed_sector s, int layout, int elem) {
   }
   // the H_up pass of the two-pass product has its own tile height and CTA size
   const bool passa = layout == 1 && two_pass_wanted(s, elem);
-  const int RT = passa ? (elem == 4 ? rt_passa<float>() : rt_passa<double>())
+  const bool wide = passa_is_wide(s);
+  const int RT = passa ? (elem == 4 ? (wide ? rt_passa<float, true>() : rt_passa<float, false>())
+                                    : (wide ? rt_passa<double, true>() : rt_passa<double, false>()))
                        : (elem == 4 ? Tile<float>::RT : Tile<double>::RT);
-  const int threads = passa ? PASSA_THREADS : HV_THREADS;
+  const int threads = passa ? (wide ? passa_threads<true>() : passa_threads<false>()) : HV_THREADS;
   std::vector<HvItem> items;
   size_t smem = 0;
   for (size_t bd = 0; bd + 1 < ob_dw.size(); ++bd) {
@@ -1241,6 +1261,18 @@ int64_t ed_hv_num_parts(ed_sector s, int layout, int elem_size) {
 
 // Opt the product kernels into large dynamic shared memory, once per device
 // (outside any stream capture).
+template <typename T, bool WIDE>
+static ed_status prepare_passa() {
+  constexpr int RT = rt_passa<T, WIDE>(), NT = passa_threads<WIDE>();
+  ED_TRY_CUDA(cudaFuncSetAttribute(k_hv<T, HV_PLAIN, true, true, RT, NT>,
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)HV_SMEM_MAX));
+  ED_TRY_CUDA(cudaFuncSetAttribute(k_hv<T, HV_LANCZOS, true, true, RT, NT>,
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)HV_SMEM_MAX));
+  ED_TRY_CUDA(cudaFuncSetAttribute(k_hv<T, HV_SECOND, true, true, RT, NT>,
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)HV_SMEM_MAX));
+  return ED_OK;
+}
+
 template <typename T, bool BLK>
 static ed_status prepare_layout() {
   ED_TRY_CUDA(cudaFuncSetAttribute(k_hv<T, HV_PLAIN, BLK>,
@@ -1250,12 +1282,8 @@ static ed_status prepare_layout() {
   ED_TRY_CUDA(cudaFuncSetAttribute(k_hv<T, HV_SECOND, BLK>,
                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)HV_SMEM_MAX));
   if (BLK) {
-    ED_TRY_CUDA(cudaFuncSetAttribute(k_hv<T, HV_PLAIN, true, true, rt_passa<T>(), PASSA_THREADS>,
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)HV_SMEM_MAX));
-    ED_TRY_CUDA(cudaFuncSetAttribute(k_hv<T, HV_LANCZOS, true, true, rt_passa<T>(), PASSA_THREADS>,
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)HV_SMEM_MAX));
-    ED_TRY_CUDA(cudaFuncSetAttribute(k_hv<T, HV_SECOND, true, true, rt_passa<T>(), PASSA_THREADS>,
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)HV_SMEM_MAX));
+    ED_TRY((prepare_passa<T, true>()));
+    ED_TRY((prepare_passa<T, false>()));
   }
   return ED_OK;
 }
@@ -1284,8 +1312,12 @@ static ed_status launch_mode(const HvLaunch<T> &a, cudaStream_t st) {
     else
       k_hv_small<T, MODE, false><<<(unsigned)a.tb.small_grid, HVS_THREADS, 0, st>>>(a);
   } else if (a.tb.ditems) {
-    k_hv<T, MODE, true, true, rt_passa<T>(), PASSA_THREADS>
-        <<<(unsigned)a.tb.nitems, PASSA_THREADS, a.tb.smem, st>>>(a);
+    if (a.tb.passa_wide)
+      k_hv<T, MODE, true, true, rt_passa<T, true>(), passa_threads<true>()>
+          <<<(unsigned)a.tb.nitems, passa_threads<true>(), a.tb.smem, st>>>(a);
+    else
+      k_hv<T, MODE, true, true, rt_passa<T, false>(), passa_threads<false>()>
+          <<<(unsigned)a.tb.nitems, passa_threads<false>(), a.tb.smem, st>>>(a);
     ED_LAUNCHED(1);
     k_hv_dw<T, MODE><<<(unsigned)a.tb.nditems, DW_THREADS, 0, st>>>(a);
   } else if (a.tb.ell_col) {
