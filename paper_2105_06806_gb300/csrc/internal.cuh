@@ -308,6 +308,7 @@ struct LanczosState {
   double beta[ED_MAX_LANCZOS + 1];
   double y[ED_MAX_LANCZOS];
   double acc[4];      // scratch reductions
+  double cvv;         // <v_j, v_{j-1}>, from the update of the previous step
 };
 
 // Modes of the fused product kernel.

@@ -8,7 +8,8 @@
 // says the recurrence has stopped):
 //   k_hv<LANCZOS>   w1 = H v_j - beta_j v_{j-1}, block partials of <v_j, w1>
 //   k_alpha         alpha_j = sum of partials (fixed order)
-//   k_axpy_norm     w = w1 - alpha_j v_j, block partials of ||w||^2
+//   k_axpy_norm     w = H v_j - beta_j v_{j-1} - alpha_j v_j, block partials of
+//                   ||w||^2 and <w, v_j>
 //   k_beta          beta_{j+1}, lazy scale of v_{j+1} = w / beta_{j+1},
 //                   Ritz value, residual estimate, stop test
 // Vectors rotate over three buffers (v_j in buffer j%3) and carry a lazy
@@ -238,40 +239,65 @@ __device__ double lowest_eigenvalue(const double *a, const double *b, const doub
 
 // ----------------------------------------------------------------- kernels
 
+// alpha_j = <v_j, H v_j - beta_j v_{j-1}> = <v_j, H v_j> - beta_j <v_j, v_{j-1}>:
+// the product leaves the partials of <v_j, H v_j>; <v_j, v_{j-1}> comes from
+// the previous step's update (k_axpy_norm, k_beta).
 __global__ void k_alpha(LanczosState *st, const double *part, const int64_t nparts) {
   __shared__ double red[SCALAR_THREADS / 32];
   if (st->done) return;
   double s = cta_sum_parts(part, nparts, red);
-  if (threadIdx.x == 0) st->alpha[st->j] = s;
+  if (threadIdx.x == 0) {
+    const int j = st->j;
+    st->alpha[j] = j > 0 ? s - st->beta[j] * st->cvv : s;
+  }
 }
 
+// w = H v_j - beta_j v_{j-1} - alpha_j v_j in place of H v_j (the product's
+// output), with block partials of ||w||^2 (part[0, g)) and of <w, v_j>
+// (part[g, 2g), g = gridDim.x) for the next step's <v_{j+1}, v_j>.  The
+// operations per element are those of the second pass's product epilogue,
+// so both passes form the same vectors bit for bit.
 template <typename T>
 __global__ void __launch_bounds__(AXPY_THREADS) k_axpy_norm(LanczosState *st, T *b0, T *b1, T *b2,
                                                             T *const *basis, int64_t n,
                                                             double *part) {
-  __shared__ double red[AXPY_THREADS / 32];
+  __shared__ double red[2][AXPY_THREADS / 32];
   if (st->done) return;
   const int j = st->j;
   T *bufs[3] = {b0, b1, b2};
   const T *v = basis ? basis[j] : bufs[j % 3];
+  const T *prev = basis ? basis[j > 0 ? j - 1 : 0] : bufs[(j + 2) % 3];
   T *w = basis ? basis[j + 1] : bufs[(j + 1) % 3];
   const T s = (T)st->scale[j % 3];
+  const T s_prev = (T)st->scale[(j + 2) % 3];
   const T al = (T)st->alpha[j];
-  T acc = T(0);
+  const T be = (T)st->beta[j];
+  T acc = T(0), cvv = T(0);
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += stride) {
-    T x = fmaT<T>(-al, mulT<T>(v[i], s), w[i]);
+    T x = w[i];
+    if (j > 0) x = fmaT<T>(-be, mulT<T>(prev[i], s_prev), x);
+    const T vi = mulT<T>(v[i], s);
+    x = fmaT<T>(-al, vi, x);
     w[i] = x;
     acc = fmaT<T>(x, x, acc);
+    cvv = fmaT<T>(x, vi, cvv);
   }
-  double d = warp_sum((double)acc);
+  double d = warp_sum((double)acc), c = warp_sum((double)cvv);
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  if (lane == 0) red[wid] = d;
+  if (lane == 0) {
+    red[0][wid] = d;
+    red[1][wid] = c;
+  }
   __syncthreads();
   if (threadIdx.x == 0) {
-    double tot = 0.0;
-    for (int k = 0; k < AXPY_THREADS / 32; ++k) tot += red[k];
+    double tot = 0.0, totc = 0.0;
+    for (int k = 0; k < AXPY_THREADS / 32; ++k) {
+      tot += red[0][k];
+      totc += red[1][k];
+    }
     part[blockIdx.x] = tot;
+    part[gridDim.x + blockIdx.x] = totc;
   }
 }
 
@@ -286,6 +312,7 @@ __global__ void k_beta(LanczosState *st, const double *part, int64_t nparts) {
   __shared__ double s_be, s_hint[2];
   if (st->done) return;
   double s2 = cta_sum_parts(part, nparts, red);
+  const double c2 = cta_sum_parts(part + nparts, nparts, red);  // <w, v_j>
   const int j = st->j;
   // scalar work once, by thread 0 (FP64 is the slow pipe)
   if (threadIdx.x == 0) {
@@ -293,6 +320,7 @@ __global__ void k_beta(LanczosState *st, const double *part, int64_t nparts) {
     const double be = sqrt(fmax(s2, 0.0));
     s_be = be;
     st->beta[j + 1] = be;
+    st->cvv = be > 0.0 ? c2 / be : 0.0;
     st->scale[(j + 1) % 3] = be > 0.0 ? 1.0 / be : 0.0;
     st->tnorm = fmax(st->tnorm, fmax(fabs(al), be));
     stop = 0;
@@ -426,6 +454,7 @@ __global__ void k_state_init(LanczosState *st, const double *part, int64_t npart
     st->scale[1] = 0.0;
     st->scale[2] = 0.0;
     st->beta[0] = 0.0;
+    st->cvv = 0.0;
     st->acc[0] = s;
     st->acc[1] = st->acc[2] = 0.0;
     st->acc[3] = INFINITY;

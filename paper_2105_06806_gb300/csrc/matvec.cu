@@ -984,7 +984,50 @@ __global__ void __launch_bounds__(NT, NT >= 1024 ? 1 : EDGB_MIN_CTAS) k_hv(HvLau
           }
         }
       } else {
-        // the step's scalars, read from shared memory once per tile
+        if (MODE == HV_LANCZOS) {
+          // w1 = H v_j (the update kernel subtracts beta_j v_{j-1} and
+          // alpha_j v_j); each column's RT staged rows of v_j in one 16-byte
+          // shared load for <v_j, w1>
+          const T s_cur = ep.s_cur;
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int c = cb + u;
+            T xr[RT];
+            if (staged) {
+              vec_get(*reinterpret_cast<const typename TileOf<T, RTX>::V *>(
+                          smq + (size_t)stage_pos(c, ncp >> 2) * RT),
+                      xr);
+            } else {
+#pragma unroll
+              for (int i = 0; i < RT; ++i)
+                xr[i] = (i < nrt && (full || c < nc))
+                            ? g[(int64_t)(r0 + lr0 + i) * stride + cp0 + c]
+                            : T(0);
+            }
+#pragma unroll
+            for (int i = 0; i < RT; ++i) {
+              if (i >= nrt || (!full && c >= nc)) continue;
+              const T w1 = mul_t<T>(acc[u][i], s_cur);
+              acc[u][i] = w1;
+              dot = fma_t<T>(mul_t<T>(xr[i], s_cur), w1, dot);
+            }
+          }
+#pragma unroll
+          for (int i = 0; i < RT; ++i) {
+            if (i >= nrt) continue;
+            T *o = out + (int64_t)(r0 + lr0 + i) * stride + cp0 + cb;
+            if (vec) {
+              const T res[4] = {acc[0][i], acc[1][i], acc[2][i], acc[3][i]};
+              store4(o, res);
+            } else {
+#pragma unroll
+              for (int u = 0; u < 4; ++u)
+                if (cb + u < nc) o[u] = acc[u][i];
+            }
+          }
+          continue;
+        }
+        // second pass: the step's scalars, read from shared memory once per tile
         const T s_cur = ep.s_cur, s_prev = ep.s_prev, beta_j = ep.beta_j;
         const T alpha_j = ep.alpha_j, y_j = ep.y_j;
         const T *const prev = ep.prev;
@@ -1144,7 +1187,8 @@ __global__ void __launch_bounds__(DW_THREADS) k_hv_dw(HvLaunch<T> a) {
         } else {
           const T v = mul_t<T>(g[gi], s_cur);
           T w1 = mul_t<T>(acc[i][u], s_cur);
-          if (j > 0) w1 = fma_t<T>(-beta_j, mul_t<T>(prev[gi], s_prev), w1);
+          if (MODE == HV_SECOND && j > 0)  // the Lanczos step does this in its update
+            w1 = fma_t<T>(-beta_j, mul_t<T>(prev[gi], s_prev), w1);
           if (MODE == HV_LANCZOS) {
             out[gi] = w1;
             dot = fma_t<T>(v, w1, dot);
@@ -1235,7 +1279,8 @@ __global__ void __launch_bounds__(HVS_THREADS) k_hv_small(HvLaunch<T> a) {
       } else {
         const T v = mul_t<T>(x, s_cur);
         T w1 = mul_t<T>(acc, s_cur);
-        if (j > 0) w1 = fma_t<T>(-beta_j, mul_t<T>(prev[gi], s_prev), w1);
+        if (MODE == HV_SECOND && j > 0)  // the Lanczos step does this in its update
+          w1 = fma_t<T>(-beta_j, mul_t<T>(prev[gi], s_prev), w1);
         if (MODE == HV_LANCZOS) {
           out[gi] = w1;
           dot = fma_t<T>(v, w1, dot);
