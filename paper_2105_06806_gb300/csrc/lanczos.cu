@@ -6,8 +6,10 @@
 // Per step j the host enqueues four kernels (captured in a CUDA graph and
 // replayed in chunks; every kernel exits at once when the device-side state
 // says the recurrence has stopped):
-//   k_hv<LANCZOS>   w1 = H v_j - beta_j v_{j-1}, block partials of <v_j, w1>
-//   k_alpha         alpha_j = sum of partials (fixed order)
+//   k_hv<LANCZOS>   H v_j, block partials of <v_j, H v_j>
+//   k_alpha         alpha_j = <v_j, H v_j> - beta_j <v_j, v_{j-1}> (Paige's
+//                   <v_j, H v_j - beta_j v_{j-1}> by linearity; partials
+//                   summed in a fixed order)
 //   k_axpy_norm     w = H v_j - beta_j v_{j-1} - alpha_j v_j, block partials of
 //                   ||w||^2 and <w, v_j>
 //   k_beta          beta_{j+1}, lazy scale of v_{j+1} = w / beta_{j+1},
