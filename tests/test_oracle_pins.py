@@ -239,6 +239,49 @@ def test_ground_vector_residual_and_dense_ns8():
     assert abs(abs(U[:, 0] @ r["psi"]) - 1.0) < 1e-12
 
 
+def test_alpha_by_linearity_matches_paige_form():
+    """The CUDA path forms alpha_j = <v_j, H v_j> - beta_j <v_j, v_{j-1}>
+    (with the computed <v_j, v_{j-1}>) and the vector update w = H v_j -
+    beta_j v_{j-1} - alpha_j v_j; the oracle uses alpha_j = <v_j, H v_j -
+    beta_j v_{j-1}>.  Both, written out here in FP64 on the Ns=8 sector,
+    give the same coefficients to rounding over 40 steps (well past the
+    loss of orthogonality of the plain recurrence), and the oracle's own
+    routine gives the same first coefficients."""
+    wl = workload_ns8()
+    s = fock.Sector(wl.model, 4, 4)
+    v0 = lanczos.start_vector(0x5EED, s.dim)
+    steps = 40
+
+    def run(linear):
+        v = v0 / np.linalg.norm(v0)
+        vp = np.zeros_like(v)
+        a_s, b_s, c = [], [0.0], 0.0
+        for j in range(steps):
+            hv = s.matvec(v)
+            if linear:
+                a = float(v @ hv) - b_s[j] * c
+                w = hv - b_s[j] * vp - a * v
+            else:
+                w = hv - b_s[j] * vp
+                a = float(v @ w)
+                w = w - a * v
+            b = float(np.linalg.norm(w))
+            c = float(w @ v) / b     # <v_{j+1}, v_j>
+            a_s.append(a)
+            b_s.append(b)
+            vp, v = v, w / b
+        return np.array(a_s), np.array(b_s[1:])
+
+    a_lin, b_lin = run(True)
+    a_pai, b_pai = run(False)
+    scale = max(np.abs(a_pai).max(), b_pai.max())
+    assert np.abs(a_lin - a_pai).max() <= 1e-12 * scale
+    assert np.abs(b_lin - b_pai).max() <= 1e-12 * scale
+    r = lanczos.lanczos_ground(s.matvec, v0, maxit=steps, tol=0.0)
+    k = min(10, len(r["alpha"]))
+    assert np.abs(r["alpha"][:k] - a_pai[:k]).max() <= 1e-12 * scale
+
+
 # ---------------------------------------------------------------- a7: c, c^+
 
 @pytest.mark.parametrize("spin", [0, 1])
