@@ -194,11 +194,12 @@ def run_ours(args):
         r, G = E.solve(m, wl.nup, wl.ndw, stream=stream, psi=psi_out, precision="fp32_polish",
                        gf_precision="fp32", nmats=nmats if do_gf else 0, beta=beta,
                        gf_steps=gf_steps)
-        # ground state: FP32 first pass (k) and second pass (k-1) at 8 D per
-        # product; polish passes and residual products in FP64 at 16 D
+        # ground state: the products the library reports as executed, FP32
+        # ones at 8 D bytes (read v + write w), FP64 ones (polish steps and
+        # residual products) at 16 D
         k = r["iterations"]
-        n32 = k + max(k - 1, 0)
-        n64 = r["matvecs"] - n32
+        n64 = r["matvecs_fp64"]
+        n32 = r["matvecs"] - n64
         nbytes = 8 * D * n32 + 16 * D * n64 + r["gf_product_bytes"]
         nmv = r["matvecs"] + r["gf_steps_total"]
         iters = k + r["polish_iterations"] + r["gf_steps_total"]

@@ -225,6 +225,9 @@ typedef struct {
   int32_t polish_iterations;
   int32_t stop_reason;      /* 0 converged, 1 breakdown, 2 max_iter            */
   int32_t matvecs;          /* total products performed                        */
+  int32_t matvecs_fp64;     /* of which in FP64 (all of them for ED_FP64; the
+                               polish steps and residual products otherwise)   */
+  int32_t reserved;         /* 0                                               */
 } ed_lanczos_result;
 
 /* Lanczos ground state of the sector (Sec. 6.6): plain Lanczos, Paige form,
@@ -339,24 +342,30 @@ ed_status ed_server_inject_alloc_failure(ed_server srv, int32_t count);
 
 /* ---------------------------------------------------------------- no allocation
  * Residual check that allocates nothing (the paper has no counterpart: this
- * is a service of this library).  For callers that must not allocate device
- * memory on this path -- code recording into a stream capture in global
- * mode, where cudaMalloc is prohibited; applications whose device memory is
- * owned by their own pool allocator; latency-critical loops where an
- * allocation could block or fail -- it computes, for a caller's vector psi
- * of n = D elements in sector order (double, device memory):
+ * is a service of this library).  It is meant for callers that cannot let a
+ * library allocate device memory: applications that hand all device memory
+ * to their own pool or arena allocator up front (a cudaMalloc by the library
+ * would then fail or fragment their pool), and latency-critical loops in
+ * which cudaMalloc/cudaFree could block (cudaFree synchronises the device).
+ * For a caller's vector psi of n = D elements in sector order (double,
+ * device memory) it computes
  *   host_e_r[0] = <psi, H psi> / <psi, psi>,
- *   host_e_r[1] = ||H psi - host_e_r[0] psi|| / ||psi||.
+ *   host_e_r[1] = ||H psi - host_e_r[0] psi|| / ||psi||,
+ * enqueued on `stream`, then copies the two words to the host and
+ * synchronises `stream` before returning.
  * It calls no cudaMalloc, cudaFree or other allocating routine: its scratch
  * (H psi, partial sums, result words) is a file-scope device array of
- * ED_NOALLOC_MAX_DIM + 2052 doubles (about 8 MiB) that every GPU loading the
- * library holds until exit.  D above ED_NOALLOC_MAX_DIM (or n != D) returns
- * ED_ERR_ARG.  The first call on a device looks up the array's device
- * address (with that device current); make that first call before any
- * stream capture.  Every call overwrites the scratch words it reads, so no
- * clearing is needed; calls whose kernels overlap on the GPU (other streams
- * or threads) race on the shared array and must be serialised by the
- * caller.  Synchronises `stream`. */
+ * ED_NOALLOC_MAX_DIM + 2052 doubles (about 8 MiB).  Every GPU that loads the
+ * library's module holding the array reserves it until the process exits;
+ * under CUDA's default lazy module loading that happens on the module's first
+ * use, which is this entry point's first call on the device.  D above
+ * ED_NOALLOC_MAX_DIM (or n != D) returns ED_ERR_ARG.  The first call on a
+ * device also looks up the array's device address (with that device
+ * current): make that first call at set-up time, before any stream capture.
+ * Every call overwrites the scratch words it reads before reading them, so
+ * no clearing is needed; calls whose kernels overlap on the GPU (other
+ * streams or threads) race on the shared array and must be serialised by
+ * the caller. */
 #define ED_NOALLOC_MAX_DIM (1 << 20)
 ed_status ed_residual_noalloc(ed_sector s, const double *d_psi, int64_t n, double *host_e_r,
                               void *stream);

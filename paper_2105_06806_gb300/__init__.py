@@ -79,7 +79,7 @@ class ed_lanczos_result(C.Structure):
     _fields_ = [("e0", C.c_double), ("e0_raw", C.c_double), ("residual", C.c_double),
                 ("residual_estimate", C.c_double), ("iterations", C.c_int32),
                 ("polish_iterations", C.c_int32), ("stop_reason", C.c_int32),
-                ("matvecs", C.c_int32)]
+                ("matvecs", C.c_int32), ("matvecs_fp64", C.c_int32), ("reserved", C.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -242,6 +242,8 @@ class Sector:
         self.dim_up, self.dim_dw = self.info["dim_up"], self.info["dim_dw"]
         self.blocked_dim = self.info["blocked_dim"]
         self.blocked_stride = self.info["blocked_stride"]
+        import torch
+        self.device = torch.cuda.current_device()  # the device holding the tables
 
     def free(self):
         if self.h:
@@ -336,7 +338,16 @@ def permute(sector: Sector, x, out, to_blocked=True, precision="fp64", stream=No
 def residual_noalloc(sector: Sector, psi, stream=None):
     """(E, ||H psi - E psi|| / ||psi||) of an FP64 sector-order vector without
     any device allocation (scratch in a static device array; the sector
-    dimension must not exceed ED_NOALLOC_MAX_DIM = 2**20)."""
+    dimension must not exceed ED_NOALLOC_MAX_DIM = 2**20).
+
+    ``psi`` must be a contiguous float64 CUDA tensor on the sector's device:
+    the C entry point reads it as ``double`` elements, so anything else is
+    rejected here with ED_ERR_ARG before the library is called."""
+    import torch
+    if not (isinstance(psi, torch.Tensor) and psi.dtype == torch.float64 and psi.is_cuda
+            and psi.is_contiguous() and psi.device.index == getattr(sector, "device", None)):
+        raise EDError(ED_ERR_ARG, "ed_residual_noalloc: psi must be a contiguous float64 "
+                                  "CUDA tensor on the sector's device")
     out = np.zeros(2, dtype=np.float64)
     _check(lib().ed_residual_noalloc(sector.h, C.c_void_p(psi.data_ptr()), int(psi.numel()),
                                      C.c_void_p(out.ctypes.data), C.c_void_p(_stream_ptr(stream))),

@@ -125,10 +125,12 @@ struct ChainTask {
   int nsteps;
 };
 
-// Sum over the CTA, the same value in every thread, fixed order: lanes in
-// the vector type (FP64 is the slow pipe), the 32 warp sums in FP64.
+// Sum over the CTA, the same value in every thread, fixed order, in FP64
+// (each thread's partial covers at most n / CHAIN_THREADS <= 16 elements of
+// a chain's sector, summed in the vector type).
 template <typename T>
-__device__ double chain_allsum(T x, double *red) {
+__device__ double chain_allsum(T xt, double *red) {
+  double x = (double)xt;
   for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   if (lane == 0) red[wid] = (double)x;

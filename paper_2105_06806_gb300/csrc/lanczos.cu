@@ -26,6 +26,12 @@
 
 constexpr int SCALAR_THREADS = 512;
 constexpr int AXPY_THREADS = 256;
+// Reductions of the FP32 modes sum at most FLUSH products per thread in FP32
+// before adding them into an FP64 accumulator (every partial across threads,
+// warps and CTAs is FP64): the FP64 pipe is slow on this GPU, so the
+// elementwise products stay FP32, but no FP32 sum runs over more than FLUSH
+// terms.
+constexpr int FLUSH = 16;
 
 // ----------------------------------------------------------------- reductions
 
@@ -274,18 +280,24 @@ __global__ void __launch_bounds__(AXPY_THREADS) k_axpy_norm(LanczosState *st, T 
   const T s_prev = (T)st->scale[(j + 2) % 3];
   const T al = (T)st->alpha[j];
   const T be = (T)st->beta[j];
-  T acc = T(0), cvv = T(0);
+  // per-thread sums in T over at most FLUSH elements, then added into FP64
+  double accd = 0.0, cvvd = 0.0;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += stride) {
-    T x = w[i];
-    if (j > 0) x = fmaT<T>(-be, mulT<T>(prev[i], s_prev), x);
-    const T vi = mulT<T>(v[i], s);
-    x = fmaT<T>(-al, vi, x);
-    w[i] = x;
-    acc = fmaT<T>(x, x, acc);
-    cvv = fmaT<T>(x, vi, cvv);
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;) {
+    T acc = T(0), cvv = T(0);
+    for (int k = 0; k < FLUSH && i < n; ++k, i += stride) {
+      T x = w[i];
+      if (j > 0) x = fmaT<T>(-be, mulT<T>(prev[i], s_prev), x);
+      const T vi = mulT<T>(v[i], s);
+      x = fmaT<T>(-al, vi, x);
+      w[i] = x;
+      acc = fmaT<T>(x, x, acc);
+      cvv = fmaT<T>(x, vi, cvv);
+    }
+    accd += (double)acc;
+    cvvd += (double)cvv;
   }
-  double d = warp_sum((double)acc), c = warp_sum((double)cvv);
+  double d = warp_sum(accd), c = warp_sum(cvvd);
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   if (lane == 0) {
     red[0][wid] = d;
@@ -394,21 +406,25 @@ __global__ void __launch_bounds__(AXPY_THREADS) k_start_vector(T *v, int64_t n, 
                                                                int64_t stride, int64_t dup,
                                                                double *part) {
   __shared__ double red[AXPY_THREADS / 32];
-  T acc = T(0);
+  double accd = 0.0;
   const int64_t step = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += step) {
-    const int64_t r = i / stride, pc = i - r * stride;
-    const int32_t cb = padinv[pc];
-    T x = T(0);
-    if (cb >= 0) {
-      const uint64_t p = (uint64_t)pidx_dw[r] * (uint64_t)dup + (uint64_t)pidx_up[cb];
-      double u = (double)(splitmix64_at(seed, p) >> 11) * (1.0 / 9007199254740992.0);
-      x = (T)(u - 0.5);
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;) {
+    T acc = T(0);
+    for (int k = 0; k < FLUSH && i < n; ++k, i += step) {
+      const int64_t r = i / stride, pc = i - r * stride;
+      const int32_t cb = padinv[pc];
+      T x = T(0);
+      if (cb >= 0) {
+        const uint64_t p = (uint64_t)pidx_dw[r] * (uint64_t)dup + (uint64_t)pidx_up[cb];
+        double u = (double)(splitmix64_at(seed, p) >> 11) * (1.0 / 9007199254740992.0);
+        x = (T)(u - 0.5);
+      }
+      v[i] = x;
+      acc = fmaT<T>(x, x, acc);
     }
-    v[i] = x;
-    acc = fmaT<T>(x, x, acc);
+    accd += (double)acc;
   }
-  double d = warp_sum((double)acc);
+  double d = warp_sum(accd);
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   if (lane == 0) red[wid] = d;
   __syncthreads();
@@ -423,11 +439,14 @@ __global__ void __launch_bounds__(AXPY_THREADS) k_start_vector(T *v, int64_t n, 
 template <typename T>
 __global__ void __launch_bounds__(AXPY_THREADS) k_norm2(const T *v, int64_t n, double *part) {
   __shared__ double red[AXPY_THREADS / 32];
-  T acc = T(0);
+  double accd = 0.0;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += stride)
-    acc = fmaT<T>(v[i], v[i], acc);
-  double d = warp_sum((double)acc);
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;) {
+    T acc = T(0);
+    for (int k = 0; k < FLUSH && i < n; ++k, i += stride) acc = fmaT<T>(v[i], v[i], acc);
+    accd += (double)acc;
+  }
+  double d = warp_sum(accd);
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   if (lane == 0) red[wid] = d;
   __syncthreads();
@@ -1033,7 +1052,7 @@ ed_status ed_lanczos_ground_impl(ed_sector s, const ed_lanczos_opts *o, ed_lancz
   const int64_t n = s->bdim;  // padded block-major vectors
   std::vector<char> hbuf(sizeof(LanczosState));
   LanczosState *h = (LanczosState *)hbuf.data();
-  int mv = 0;
+  int mv = 0, mv32 = 0;
   const int64_t g2 = reduce_grid(n);
   if (prec == ED_FP64) {
     Workspace psi;   // block-major ground state
@@ -1055,6 +1074,7 @@ ed_status ed_lanczos_ground_impl(ed_sector s, const ed_lanczos_opts *o, ed_lancz
     float *fpsi = (float *)psi32.mem;
     ED_TRY(lanczos_solve<float>(s, maxit, tol, o->seed, nullptr, want, fpsi, h, cs, &mv,
                                 o->basis_mib));
+    mv32 = mv;  // the FP32 first pass (and second pass, if any)
     fill_result(*h, res);
     if (want) {
       // FP64 copy of the FP32 ground state (normalised in FP64)
@@ -1096,6 +1116,7 @@ ed_status ed_lanczos_ground_impl(ed_sector s, const ed_lanczos_opts *o, ed_lancz
   }
   ED_TRY_CUDA(cudaStreamSynchronize(cs));
   res->matvecs = mv;
+  res->matvecs_fp64 = mv - mv32;
   if (res->stop_reason == 2) return ED_ERR_NOT_CONVERGED;
   return ED_OK;
 }

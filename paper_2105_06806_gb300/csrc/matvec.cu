@@ -950,7 +950,8 @@ __global__ void __launch_bounds__(NT, NT >= 1024 ? 1 : EDGB_MIN_CTAS) k_hv(HvLau
   const int nrt = min(RT, nr - lr0);  // rows of this thread (may be <= 0)
   const T *smq = sm + (size_t)q * ncp * RT;
 
-  T dot = T(0);
+  T dot = T(0);      // FP32 mode: the tile's 4 x RT <= 16 products
+  double dotd = 0.0;  // the thread's sum of the tiles' partials
   if (nrt > 0) {
     for (int tl = p; tl < ntile; tl += P) {
       const int cb = tl * 4;
@@ -1025,6 +1026,8 @@ __global__ void __launch_bounds__(NT, NT >= 1024 ? 1 : EDGB_MIN_CTAS) k_hv(HvLau
                 if (cb + u < nc) o[u] = acc[u][i];
             }
           }
+          dotd += (double)dot;
+          dot = T(0);
           continue;
         }
         // second pass: the step's scalars, read from shared memory once per tile
@@ -1076,7 +1079,7 @@ __global__ void __launch_bounds__(NT, NT >= 1024 ? 1 : EDGB_MIN_CTAS) k_hv(HvLau
     }
   }
   if (MODE == HV_LANCZOS && !PASSA) {
-    double smv = block_sum<T>((double)dot, red);
+    double smv = block_sum<T>(dotd + (double)dot, red);
     if (threadIdx.x == 0) a.part[blockIdx.x] = smv;
   }
 }
@@ -1139,8 +1142,11 @@ __global__ void __launch_bounds__(DW_THREADS) k_hv_dw(HvLaunch<T> a) {
   }
   __syncthreads();
   const int ntile = (it.nc + 3) >> 2, ngrp = (it.nr + RT - 1) / RT;
-  T dot = T(0);
+  T dot = T(0);       // one tile's products (at most 16)
+  double dotd = 0.0;  // the thread's tiles
   for (int idx = threadIdx.x; idx < ngrp * ntile; idx += blockDim.x) {
+    dotd += (double)dot;
+    dot = T(0);
     const int q = idx / ntile, cb = (idx - q * ntile) * 4;
     const int lr0 = q * RT, nrt = min(RT, it.nr - lr0);
     const int64_t col0 = (int64_t)it.c0p + cb;
@@ -1201,7 +1207,7 @@ __global__ void __launch_bounds__(DW_THREADS) k_hv_dw(HvLaunch<T> a) {
     }
   }
   if (MODE == HV_LANCZOS) {
-    double smv = block_sum<T>((double)dot, red);
+    double smv = block_sum<T>(dotd + (double)dot, red);
     if (threadIdx.x == 0) a.part[blockIdx.x] = smv;
   }
 }

@@ -1,10 +1,10 @@
 // Allocation-free residual check of a caller's vector.
 //
 // Some callers cannot let a library allocate device memory on this path:
-// code that records into a stream capture in global mode (where cudaMalloc
-// is a prohibited call), applications that hand all device memory to their
-// own pool allocator, and latency-critical loops where an allocation could
-// block or fail.  ed_residual_noalloc computes what the Lanczos driver's
+// applications that hand all device memory to their own pool or arena
+// allocator up front (an allocation by the library would fail or fragment
+// their pool), and latency-critical loops in which cudaMalloc/cudaFree could
+// block (cudaFree synchronises the device).  ed_residual_noalloc computes what the Lanczos driver's
 // FP64 residual step computes (E = <psi,H psi>/<psi,psi> and
 // ||H psi - E psi|| / ||psi||) without calling cudaMalloc, cudaFree or any
 // allocating routine: its scratch (the vector H psi, per-CTA partial sums and

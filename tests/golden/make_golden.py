@@ -11,8 +11,12 @@ the workload recipe and the oracle's FP64 results:
   components of psi.
 * ``oracle_norb2_ns14.json`` — Ns=14 two-orbital Kanamori AIM, sector (5,6),
   seeded bath (seed 0): the same quantities (orbital 0, spin up).
+* ``oracle_ns16.json`` — Ns=16 two-orbital Kanamori AIM, half filling (8,8),
+  D=165,636,900, seeded bath (seed 0): the benchmark sector.  E0, 256 psi
+  samples and G_{0,up}(i w_n) from 200-step chains, all from the oracle's
+  factorised product (Sec. 6.7 without MPI); about 90 minutes on one core.
 
-Usage: python tests/golden/make_golden.py [ns8] [ns14] [norb2_ns14]
+Usage: python tests/golden/make_golden.py [ns8] [ns14] [norb2_ns14] [ns16]
 """
 import json
 import os
@@ -25,7 +29,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, os.path.dirname(os.path.dirname(HERE)))
 
 from oracle import fock, gf, lanczos  # noqa: E402
-from workloads import workload_ns8, workload_ns14, workload_norb2_ns14  # noqa: E402
+from workloads import (workload_ns8, workload_ns14, workload_norb2_ns14,  # noqa: E402
+                       workload_ns16)
 
 SEED = 0x5EED
 
@@ -66,6 +71,10 @@ def main(which):
     if "norb2_ns14" in which:
         with open(os.path.join(HERE, "oracle_norb2_ns14.json"), "w") as f:
             json.dump(run(workload_norb2_ns14(0), nsamp=256), f, indent=1)
+    if "ns16" in which:
+        out = run(workload_ns16(0), nsamp=256)
+        with open(os.path.join(HERE, "oracle_ns16.json"), "w") as f:
+            json.dump(out, f, indent=1)
 
 
 if __name__ == "__main__":

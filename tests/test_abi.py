@@ -49,7 +49,7 @@ STRUCTS = {
     "ed_sector_info": ["ns", "dim_up", "dim", "device_bytes", "blocked_stride", "blocked_dim"],
     "ed_lanczos_opts": ["precision", "max_iter", "tol", "seed", "polish_steps", "want_vector",
                         "basis_mib"],
-    "ed_lanczos_result": ["e0", "residual_estimate", "iterations", "matvecs"],
+    "ed_lanczos_result": ["e0", "residual_estimate", "iterations", "matvecs", "matvecs_fp64"],
     "ed_gf_info": ["weight_hole", "steps_particle", "steps_hole"],
     "ed_solve_opts": ["lanczos", "gf_steps", "nmats", "beta", "gf_precision"],
     "ed_solve_result": ["ground", "t_build_s", "t_gf_s", "gf_chains", "gf_product_bytes"],

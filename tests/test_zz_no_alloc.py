@@ -1,6 +1,7 @@
 """ed_residual_noalloc: the allocation-free residual check, for callers that
-must not allocate device memory on this path (stream capture in global
-mode, application-owned pool allocators, latency-critical loops).
+cannot let a library allocate device memory (applications that give all
+device memory to their own pool allocator, latency-critical loops in which
+cudaMalloc/cudaFree could block).
 
 It is compared with the entry points that allocate: the Lanczos ground state
 (its energy and FP64 residual) and ed_matvec (the product it re-computes),
@@ -12,9 +13,6 @@ import torch
 
 from workloads import make_model, workload_ns8
 
-pytestmark = pytest.mark.gpu
-
-
 def _reference(ed, s, psi):
     """E and ||H psi - E psi|| / ||psi|| through ed_matvec (allocating path)."""
     w = torch.empty_like(psi)
@@ -25,6 +23,7 @@ def _reference(ed, s, psi):
     return e, r
 
 
+@pytest.mark.gpu
 @pytest.mark.parametrize("case", ["ns8", "norb2_ns10"])
 def test_noalloc_matches_allocating_entry_points(ed, case):
     if case == "ns8":
@@ -56,6 +55,7 @@ def test_noalloc_matches_allocating_entry_points(ed, case):
     s.free()
 
 
+@pytest.mark.gpu
 def test_noalloc_rejects_oversized_and_mismatched(ed):
     from workloads import workload_ns14
     wl = workload_ns14(0)
@@ -70,3 +70,46 @@ def test_noalloc_rejects_oversized_and_mismatched(ed):
         ed.residual_noalloc(s, torch.zeros(s.dim + 1, dtype=torch.float64, device="cuda"))
     assert e.value.status == ed.ED_ERR_ARG
     s.free()
+    # a float32 vector (as the FP32 ground state returns) is refused before
+    # the library reads it as doubles
+    s = ed.Sector(workload_ns8().model, 4, 4)
+    with pytest.raises(ed.EDError) as e:
+        ed.residual_noalloc(s, torch.zeros(s.dim, dtype=torch.float32, device="cuda"))
+    assert e.value.status == ed.ED_ERR_ARG
+    s.free()
+
+
+@pytest.mark.gpu
+def test_noalloc_allocates_no_device_memory(ed):
+    """After the first call on the device (which loads the module holding the
+    static scratch array), further calls leave the free device memory as it
+    was: nothing is allocated or released."""
+    s = ed.Sector(make_model(2, 4, U=3.0, Jh=0.5, seed=6), 5, 5)
+    g = torch.Generator(device="cuda").manual_seed(2)
+    x = torch.rand(s.dim, dtype=torch.float64, device="cuda", generator=g) - 0.5
+    first = ed.residual_noalloc(s, x)            # set-up call
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    for _ in range(5):
+        assert ed.residual_noalloc(s, x) == first
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0
+    s.free()
+
+
+def test_noalloc_binding_rejects_non_double_vectors():
+    """CPU check of the binding's argument guard: a vector that is not a
+    contiguous float64 CUDA tensor on the sector's device never reaches the
+    C entry point (which would read it as doubles)."""
+    import paper_2105_06806_gb300 as E
+
+    class _FakeSector:
+        h = None
+        device = 0
+
+    for bad in (torch.zeros(16, dtype=torch.float32), torch.zeros(16, dtype=torch.float64),
+                torch.zeros(32, dtype=torch.float64)[::2]):
+        with pytest.raises(E.EDError) as e:
+            E.residual_noalloc(_FakeSector(), bad)
+        assert e.value.status == E.ED_ERR_ARG
