@@ -280,20 +280,30 @@ __global__ void __launch_bounds__(AXPY_THREADS) k_axpy_norm(LanczosState *st, T 
   const T s_prev = (T)st->scale[(j + 2) % 3];
   const T al = (T)st->alpha[j];
   const T be = (T)st->beta[j];
-  // per-thread sums in T over at most FLUSH elements, then added into FP64
+  // per-thread sums in T over at most FLUSH elements, then added into FP64:
+  // whole groups of FLUSH elements without bounds checks, then the tail
   double accd = 0.0, cvvd = 0.0;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  auto step = [&](int64_t k, T &acc, T &cvv) {
+    T x = w[k];
+    if (j > 0) x = fmaT<T>(-be, mulT<T>(prev[k], s_prev), x);
+    const T vi = mulT<T>(v[k], s);
+    x = fmaT<T>(-al, vi, x);
+    w[k] = x;
+    acc = fmaT<T>(x, x, acc);
+    cvv = fmaT<T>(x, vi, cvv);
+  };
+  for (; i + (FLUSH - 1) * stride < n; i += FLUSH * stride) {
     T acc = T(0), cvv = T(0);
-    for (int k = 0; k < FLUSH && i < n; ++k, i += stride) {
-      T x = w[i];
-      if (j > 0) x = fmaT<T>(-be, mulT<T>(prev[i], s_prev), x);
-      const T vi = mulT<T>(v[i], s);
-      x = fmaT<T>(-al, vi, x);
-      w[i] = x;
-      acc = fmaT<T>(x, x, acc);
-      cvv = fmaT<T>(x, vi, cvv);
-    }
+#pragma unroll 4
+    for (int k = 0; k < FLUSH; ++k) step(i + k * stride, acc, cvv);
+    accd += (double)acc;
+    cvvd += (double)cvv;
+  }
+  {
+    T acc = T(0), cvv = T(0);
+    for (; i < n; i += stride) step(i, acc, cvv);
     accd += (double)acc;
     cvvd += (double)cvv;
   }

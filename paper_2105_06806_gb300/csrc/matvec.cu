@@ -518,6 +518,23 @@ std::mutex g_tune_mu;
 std::map<TuneKey, int> g_tune;
 }  // namespace
 
+// Autotuning input: v_i = u_i - 1/2 at every real element (u_i a uniform
+// from a hash of the index, the distribution of the Lanczos start vector),
+// zero at padding columns; timings on a zero vector run faster than on the
+// vectors the solves see.
+template <typename T>
+__global__ void k_tune_fill(T *v, int64_t n, int64_t stride, const int32_t *padinv) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t pc = i % stride;
+    uint64_t z = (uint64_t)i * 0x9E3779B97F4A7C15ull + 0x5EEDull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    v[i] = padinv[pc] < 0 ? T(0) : (T)((double)(z >> 11) * (1.0 / 9007199254740992.0) - 0.5);
+  }
+}
+
 template <typename T>
 static ed_status time_hv_kernels(ed_sector s, int e, cudaStream_t cs, double ms[2]) {
   const int64_t n = s->bdim;
@@ -526,9 +543,15 @@ static ed_status time_hv_kernels(ed_sector s, int e, cudaStream_t cs, double ms[
   T *v = (T *)mem, *w = v + n;
   cudaEvent_t ev[2] = {nullptr, nullptr};
   ed_status rs = ED_OK;
-  if (cudaMemsetAsync(mem, 0, 2 * n * sizeof(T), cs) != cudaSuccess ||
+  if (cudaMemsetAsync(w, 0, n * sizeof(T), cs) != cudaSuccess ||
       cudaEventCreate(&ev[0]) != cudaSuccess || cudaEventCreate(&ev[1]) != cudaSuccess)
     rs = ED_ERR_CUDA;
+  if (rs == ED_OK) {
+    k_tune_fill<T><<<(unsigned)std::min<int64_t>((n + 255) / 256, 152 * 32), 256, 0, cs>>>(
+        v, n, s->bstride, s->padinv);
+    ed_count_launches(1);
+    if (cudaGetLastError() != cudaSuccess) rs = ED_ERR_CUDA;
+  }
   // one warm-up launch of each kernel, then three rounds that alternate the
   // two, so that a clock that is still ramping up favours neither
   ms[0] = ms[1] = 0.0;
@@ -950,8 +973,12 @@ __global__ void __launch_bounds__(NT, NT >= 1024 ? 1 : EDGB_MIN_CTAS) k_hv(HvLau
   const int nrt = min(RT, nr - lr0);  // rows of this thread (may be <= 0)
   const T *smq = sm + (size_t)q * ncp * RT;
 
-  T dot = T(0);      // FP32 mode: the tile's 4 x RT <= 16 products
-  double dotd = 0.0;  // the thread's sum of the tiles' partials
+  // Lanczos mode: <v_j, w1> summed in T over this thread's tiles of the item
+  // (at most ceil(1225 / 512) = 3 tiles of 16 products at Ns=16), then in
+  // FP64 across threads and CTAs.  An FP64 accumulator per thread (or a
+  // shared-memory FP64 slot per tile) doubled the register spills of this
+  // kernel at its 64-register cap and slowed the FP32 Lanczos step.
+  T dot = T(0);
   if (nrt > 0) {
     for (int tl = p; tl < ntile; tl += P) {
       const int cb = tl * 4;
@@ -1026,8 +1053,6 @@ __global__ void __launch_bounds__(NT, NT >= 1024 ? 1 : EDGB_MIN_CTAS) k_hv(HvLau
                 if (cb + u < nc) o[u] = acc[u][i];
             }
           }
-          dotd += (double)dot;
-          dot = T(0);
           continue;
         }
         // second pass: the step's scalars, read from shared memory once per tile
@@ -1079,7 +1104,7 @@ __global__ void __launch_bounds__(NT, NT >= 1024 ? 1 : EDGB_MIN_CTAS) k_hv(HvLau
     }
   }
   if (MODE == HV_LANCZOS && !PASSA) {
-    double smv = block_sum<T>(dotd + (double)dot, red);
+    double smv = block_sum<T>((double)dot, red);
     if (threadIdx.x == 0) a.part[blockIdx.x] = smv;
   }
 }

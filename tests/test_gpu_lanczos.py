@@ -12,7 +12,7 @@ import pytest
 import torch
 
 from oracle import fock
-from workloads import make_model, workload_ns8, workload_ns14, workload_ns16
+from workloads import workload_ns18, make_model, workload_ns8, workload_ns14, workload_ns16
 
 pytestmark = pytest.mark.gpu
 GOLD = os.path.join(os.path.dirname(__file__), "golden")
@@ -121,6 +121,28 @@ def test_ns16_fp32_polish_against_fp64_gpu(ed):
     assert abs(rp["e0_raw"] - e) <= 1e-6 * abs(e)
     assert abs(rp["e0"] - e) <= 1e-10 * abs(e)
     assert r64["residual"] < 1e-6 and rp["residual"] < 1e-4
+    s.free()
+
+
+def test_ns18_ground_state(ed):
+    """Ns=18 (D = 2,363,904,400), the largest single-GPU workload, ground
+    state only: FP32 + FP64 polish against the plain FP64 GPU path (within
+    1e-10), the FP64 residual of both (the Rayleigh-quotient residual bound
+    |E - lambda| <= ||H psi - E psi|| for some eigenvalue lambda), and a
+    second FP32 + polish run from another seeded start vector that reaches
+    the same energy: two independent random start vectors converging to one
+    eigenvalue leave no room for a converged excited state (Lanczos finds the
+    extreme eigenvalue of the start vector's Krylov space first)."""
+    wl = workload_ns18(0)
+    s = ed.Sector(wl.model, 9, 9)
+    r64 = ed.lanczos_ground(s, "fp64", want_vector=True)
+    rp = ed.lanczos_ground(s, "fp32_polish")
+    rq = ed.lanczos_ground(s, "fp32_polish", seed=0x1234567)
+    e = r64["e0"]
+    assert r64["residual"] < 1e-6 and rp["residual"] < 1e-4 and rq["residual"] < 1e-4
+    assert abs(rp["e0_raw"] - e) <= 1e-6 * abs(e)
+    assert abs(rp["e0"] - e) <= 1e-10 * abs(e)
+    assert abs(rq["e0"] - e) <= 1e-10 * abs(e)
     s.free()
 
 

@@ -246,16 +246,18 @@ def test_autotuner_picks_the_faster_kernel_per_shape(ed):
 
 
 @pytest.mark.parametrize("maker,prec,kernel", [
+    (workload_ns16, "fp32", "tiled"),
     (workload_ns16, "fp64", "two_pass"), (workload_ns16, "fp64", "elementwise"),
     (workload_ns18, "fp32", "two_pass"), (workload_ns18, "fp32", "elementwise")])
 def test_full_size_sampled(ed, maker, prec, kernel):
     """The full-size products of the Lanczos runs, checked on sampled outputs
     against the oracle (input a closed-form function of the sector index):
-    the two-pass block-major product (H_up pass, then H_dw pass over column
-    chunks; taken where the block pairs exceed L2) and the element-parallel
-    product with several chunks of 256 elements per CTA (10 at Ns=16, 141
-    at Ns=18), the two kernels the autotuner chooses between at these
-    sizes."""
+    the one-pass tiled block-major product at Ns=16 in FP32 (the kernel the
+    benchmark times and the FP32 Lanczos runs use there), the two-pass
+    block-major product (H_up pass, then H_dw pass over column chunks; taken
+    where the block pairs exceed L2) and the element-parallel product with
+    several chunks of 256 elements per CTA (10 at Ns=16, 141 at Ns=18), the
+    kernels the autotuner chooses between at these sizes."""
     wl = maker(0)
     m = wl.model
     s = ed.Sector(m, wl.nup, wl.ndw)
