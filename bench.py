@@ -377,8 +377,9 @@ def run_ours(args):
     print(json.dumps(line))
 
 
-def time_products(E, wl, stream, dev, reps=20, which=("blocked_fp32",)):
-    """Median CUDA-event time of single H.v launches on the full sector."""
+def time_products(E, wl, stream, dev, reps=20, which=("blocked_fp32",), kernel=None):
+    """Median CUDA-event time of single H.v launches on the full sector
+    (`kernel`: pin the block-major product kernel, else the autotuned one)."""
     import torch
     m = wl.model
     s = E.Sector(m, wl.nup, wl.ndw, stream=stream)
@@ -386,6 +387,9 @@ def time_products(E, wl, stream, dev, reps=20, which=("blocked_fp32",)):
     out = {}
     for name in which:
         lay, prec = name.split("_")
+        if kernel and lay == "blocked":
+            s.set_kernel(kernel, prec)
+            out[name + "_kernel"] = s.blocked_kernel(prec)
         dt = torch.float32 if prec == "fp32" else torch.float64
         n = s.blocked_dim if lay == "blocked" else D    # block-major vectors are padded
         v = torch.randn(n, dtype=dt, device=dev)
@@ -418,7 +422,7 @@ def run_matvec_only(args):
     wl = _workload(args.workload)
     which = tuple(args.matvec_only.split(","))
     r = time_products(E, wl, torch.cuda.current_stream(), torch.device("cuda", 0),
-                      reps=args.steps, which=which)
+                      reps=args.steps, which=which, kernel=args.kernel or None)
     hbm, src = _peaks()
     for k, v in list(r.items()):
         if not k.endswith("_ms"):
@@ -656,6 +660,9 @@ def main():
     ap.add_argument("--serving-max-ns", type=int, default=12)
     ap.add_argument("--matvec-only", default="",
                     help="comma list of {blocked,sector}_{fp32,fp64}: time products only")
+    ap.add_argument("--kernel", default="",
+                    help="with --matvec-only: pin the block-major kernel "
+                         "(tiled, two_pass, elementwise)")
     args = ap.parse_args()
     if args.matvec_only:
         run_matvec_only(args)

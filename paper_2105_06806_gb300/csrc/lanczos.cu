@@ -265,6 +265,24 @@ __global__ void k_alpha(LanczosState *st, const double *part, const int64_t npar
 // (part[g, 2g), g = gridDim.x) for the next step's <v_{j+1}, v_j>.  The
 // operations per element are those of the second pass's product epilogue,
 // so both passes form the same vectors bit for bit.
+// 16-byte vector of the element type: 4 floats or 2 doubles.
+template <typename T>
+struct Vec16;
+template <>
+struct Vec16<float> {
+  using V = float4;
+  static constexpr int N = 4;
+  __device__ static void get(const V &v, float *x) { x[0] = v.x; x[1] = v.y; x[2] = v.z; x[3] = v.w; }
+  __device__ static V make(const float *x) { return make_float4(x[0], x[1], x[2], x[3]); }
+};
+template <>
+struct Vec16<double> {
+  using V = double2;
+  static constexpr int N = 2;
+  __device__ static void get(const V &v, double *x) { x[0] = v.x; x[1] = v.y; }
+  __device__ static V make(const double *x) { return make_double2(x[0], x[1]); }
+};
+
 template <typename T>
 __global__ void __launch_bounds__(AXPY_THREADS) k_axpy_norm(LanczosState *st, T *b0, T *b1, T *b2,
                                                             T *const *basis, int64_t n,
@@ -280,30 +298,38 @@ __global__ void __launch_bounds__(AXPY_THREADS) k_axpy_norm(LanczosState *st, T 
   const T s_prev = (T)st->scale[(j + 2) % 3];
   const T al = (T)st->alpha[j];
   const T be = (T)st->beta[j];
-  // per-thread sums in T over at most FLUSH elements, then added into FP64:
-  // whole groups of FLUSH elements without bounds checks, then the tail
+  // Block-major vectors are 16-byte aligned and their length is a multiple
+  // of 4 elements: 16-byte accesses, one vector per thread and iteration.
+  // Per-thread sums in T over at most FLUSH elements, then into FP64.
+  using VT = Vec16<T>;
+  constexpr int NV = VT::N;
+  constexpr int GROUP = FLUSH / NV;  // vectors per FP64 flush
+  const typename VT::V *vv = reinterpret_cast<const typename VT::V *>(v);
+  const typename VT::V *pv = reinterpret_cast<const typename VT::V *>(prev);
+  typename VT::V *wv = reinterpret_cast<typename VT::V *>(w);
+  const int64_t nv = n / NV;
   double accd = 0.0, cvvd = 0.0;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  auto step = [&](int64_t k, T &acc, T &cvv) {
-    T x = w[k];
-    if (j > 0) x = fmaT<T>(-be, mulT<T>(prev[k], s_prev), x);
-    const T vi = mulT<T>(v[k], s);
-    x = fmaT<T>(-al, vi, x);
-    w[k] = x;
-    acc = fmaT<T>(x, x, acc);
-    cvv = fmaT<T>(x, vi, cvv);
-  };
-  for (; i + (FLUSH - 1) * stride < n; i += FLUSH * stride) {
+  while (i < nv) {
     T acc = T(0), cvv = T(0);
-#pragma unroll 4
-    for (int k = 0; k < FLUSH; ++k) step(i + k * stride, acc, cvv);
-    accd += (double)acc;
-    cvvd += (double)cvv;
-  }
-  {
-    T acc = T(0), cvv = T(0);
-    for (; i < n; i += stride) step(i, acc, cvv);
+#pragma unroll
+    for (int g = 0; g < GROUP; ++g, i += stride) {
+      if (i >= nv) break;
+      T x[NV], pr[NV], vi[NV];
+      VT::get(wv[i], x);
+      VT::get(vv[i], vi);
+      if (j > 0) VT::get(pv[i], pr);
+#pragma unroll
+      for (int q = 0; q < NV; ++q) {
+        if (j > 0) x[q] = fmaT<T>(-be, mulT<T>(pr[q], s_prev), x[q]);
+        vi[q] = mulT<T>(vi[q], s);
+        x[q] = fmaT<T>(-al, vi[q], x[q]);
+        acc = fmaT<T>(x[q], x[q], acc);
+        cvv = fmaT<T>(x[q], vi[q], cvv);
+      }
+      wv[i] = VT::make(x);
+    }
     accd += (double)acc;
     cvvd += (double)cvv;
   }

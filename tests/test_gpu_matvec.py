@@ -318,3 +318,32 @@ def test_vector_length_checked(ed):
         ed.matvec_blocked(s, big[1:], torch.zeros_like(vb))
     assert e.value.status == ed.ED_ERR_ARG
     s.free()
+
+
+def test_tiled_family_bit_identical_to_elementwise_ns18(ed):
+    """Ns=18 (D = 2,363,904,400), FP32: the product the Lanczos runs use here
+    (the tiled family: one pass on the block pairs that fit L2, two passes
+    on the larger ones) gives the same w bit for bit as the element-parallel
+    product (the same order of operations per element), which
+    test_full_size_sampled pins against the oracle at this size."""
+    wl = workload_ns18(0)
+    s = ed.Sector(wl.model, wl.nup, wl.ndw)
+    g = torch.Generator(device="cuda").manual_seed(18)
+    vs = torch.empty(s.dim, dtype=torch.float32, device="cuda")
+    step = 1 << 28
+    for o in range(0, s.dim, step):
+        n = min(step, s.dim - o)
+        vs[o:o + n] = torch.rand(n, dtype=torch.float32, device="cuda", generator=g) - 0.5
+    v = torch.empty(s.blocked_dim, dtype=torch.float32, device="cuda")
+    ed.permute(s, vs, v, True, "fp32")       # padding columns written as zero
+    del vs
+    out = {}
+    for kernel in ("two_pass", "elementwise"):
+        s.set_kernel(kernel, "fp32")
+        w = torch.zeros_like(v)              # padding is not written: stays zero
+        ed.matvec_blocked(s, v, w, "fp32")
+        out[kernel] = w
+    torch.cuda.synchronize()
+    assert torch.equal(out["two_pass"], out["elementwise"])
+    assert bool(torch.isfinite(out["two_pass"]).all())
+    s.free()
