@@ -570,6 +570,7 @@ def run_serving(E, n_requests, max_ns, rate=0.0, precision="fp32_polish"):
                                     max_ns=max_ns)
     srv = E.Server(slots=8)
     gprec = "fp64" if precision == "fp64" else "fp32"
+    b0 = E.batch_stats()
     t0 = time.perf_counter()
     tickets = []
     for q in reqs:
@@ -590,11 +591,14 @@ def run_serving(E, n_requests, max_ns, rate=0.0, precision="fp32_polish"):
         lat.append(res["t_done_s"] - res["t_submit_s"])
     wall = time.perf_counter() - t0
     srv.close()
+    b1 = E.batch_stats()
     lat = np.array(lat)
     return {"requests": n_requests, "completed_ok": int(ok), "solves_per_s": round(ok / wall, 3),
             "p50_s": round(float(np.percentile(lat, 50)), 4),
             "p99_s": round(float(np.percentile(lat, 99)), 4), "max_ns": max_ns,
             "precision": precision,
+            "batched_chain_launches": b1["launches"] - b0["launches"],
+            "batched_chains": b1["chains"] - b0["chains"],
             "arrival_rate_per_s": rate if rate > 0 else "all at once (saturation)",
             "work": ("FP32 ground state + FP64 polish + G(512 Matsubara, 200-step FP32 chains)"
                      if precision != "fp64" else

@@ -336,6 +336,17 @@ ed_status ed_poll(ed_server srv, uint64_t ticket, ed_result *out, double *host_G
 /* Blocks up to timeout_s seconds for the request; ED_ERR_TIMEOUT otherwise. */
 ed_status ed_wait(ed_server srv, uint64_t ticket, double timeout_s);
 ed_status ed_server_destroy(ed_server srv);
+/* Batched Green's-function launches of this process (no counterpart in the
+ * paper; the task parallelism over independent impurity problems of Sec. 6.9
+ * on one GPU).  The chains of solves whose N+-1 sectors are small (at most
+ * 2^14 states) run in one persistent launch, one CTA per chain; solves that
+ * reach that phase at about the same time -- concurrent server requests,
+ * or several host threads calling ed_solve -- share one launch (the first
+ * one leads and waits at most 1 ms for the others).  A chain's result does
+ * not depend on the chains it shares a launch with.  Returns the number of
+ * such launches, of chains run in them, and the largest number of solves
+ * merged into one launch. */
+ed_status ed_batch_stats(int64_t *launches, int64_t *chains, int64_t *max_solves);
 /* Test hook: the next `count` admissions fail as if the device allocation
  * had failed (the request completes with ED_ERR_OOM). */
 ed_status ed_server_inject_alloc_failure(ed_server srv, int32_t count);

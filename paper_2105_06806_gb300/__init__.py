@@ -30,7 +30,8 @@ EXPORTED = [
     "ed_sector_tune_info", "ed_sector_set_kernel",
     "ed_sector_permute", "ed_lanczos_ground", "ed_gf_lanczos", "ed_solve",
     "ed_server_create", "ed_submit", "ed_poll", "ed_wait", "ed_server_destroy",
-    "ed_server_inject_alloc_failure", "ed_residual_noalloc", "ed_status_string", "ed_last_error",
+    "ed_server_inject_alloc_failure", "ed_batch_stats", "ed_residual_noalloc", "ed_status_string",
+    "ed_last_error",
     "ed_kernel_launches",
 ]
 
@@ -162,6 +163,7 @@ def lib():
             "ed_server_destroy": [vp],
             "ed_server_inject_alloc_failure": [vp, i32],
             "ed_residual_noalloc": [vp, vp, i64, vp, vp],
+            "ed_batch_stats": [C.POINTER(i64), C.POINTER(i64), C.POINTER(i64)],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -333,6 +335,15 @@ def permute(sector: Sector, x, out, to_blocked=True, precision="fp64", stream=No
                                    C.c_void_p(x.data_ptr()), int(x.numel()),
                                    C.c_void_p(out.data_ptr()), int(out.numel()),
                                    C.c_void_p(_stream_ptr(stream))), "ed_sector_permute")
+
+
+def batch_stats():
+    """Counters of the batched Green's-function launches of this process
+    (ed_batch_stats): launches, chains run in them, most solves merged into
+    one launch."""
+    a, b, c = C.c_int64(), C.c_int64(), C.c_int64()
+    _check(lib().ed_batch_stats(C.byref(a), C.byref(b), C.byref(c)), "ed_batch_stats")
+    return {"launches": a.value, "chains": b.value, "max_solves": c.value}
 
 
 def residual_noalloc(sector: Sector, psi, stream=None):

@@ -9,6 +9,8 @@
 #include <thread>
 #include <vector>
 
+#include <algorithm>
+
 #include "internal.cuh"
 
 static thread_local std::string g_last_error;
@@ -58,10 +60,40 @@ ed_status ed_gf_chain_batch(ed_sector s, ed_precision prec, const void *d_psi, d
                             const int *spin, const int *create, double *host_G, double *weight,
                             int *steps, int64_t *dim, cudaStream_t cs);
 
+void ed_gf_batch_announce(int delta);
+
 static double now_s() {
   using namespace std::chrono;
   return duration<double>(steady_clock::now().time_since_epoch()).count();
 }
+
+static uint64_t binom_u(int n, int k) {
+  if (k < 0 || k > n) return 0;
+  uint64_t r = 1;
+  for (int i = 1; i <= k; ++i) r = r * (uint64_t)(n - k + i) / (uint64_t)i;
+  return r;
+}
+
+// Marks a solve whose chains will be small enough for the batched launch
+// (every N+-1 sector at most 2^14 states, before padding) as under way, so
+// that a batch leader knows other members may still join.
+struct BatchAnnounce {
+  bool on = false;
+  BatchAnnounce(const ed_model *m, int nup, int ndw, int nmats) {
+    if (nmats <= 0) return;
+    const int ns = m->norb * (m->nbath + 1);
+    uint64_t d = 0;
+    for (int ds = -1; ds <= 1; ds += 2) {
+      d = std::max(d, binom_u(ns, nup + ds) * binom_u(ns, ndw));
+      d = std::max(d, binom_u(ns, nup) * binom_u(ns, ndw + ds));
+    }
+    on = d <= (1u << 14);
+    if (on) ed_gf_batch_announce(1);
+  }
+  ~BatchAnnounce() {
+    if (on) ed_gf_batch_announce(-1);
+  }
+};
 
 ed_status ed_solve_impl(const ed_model *model, int nup, int ndw, const ed_solve_opts *o,
                         ed_solve_result *res, double *host_G, void *d_psi_out, cudaStream_t cs) {
@@ -76,6 +108,7 @@ ed_status ed_solve_impl(const ed_model *model, int nup, int ndw, const ed_solve_
   if (nmats > 0 && !psi_double && !chain32) return ED_ERR_ARG;
   const ed_precision gfp = psi_double ? (chain32 ? ED_FP32_POLISH : ED_FP64) : ED_FP32;
 
+  const BatchAnnounce announce(model, nup, ndw, nmats);
   double t0 = now_s();
   ed_sector s = nullptr;
   ED_TRY(ed_sector_build(model, nup, ndw, cs, &s));

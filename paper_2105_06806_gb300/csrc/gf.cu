@@ -5,6 +5,12 @@
 #include <string.h>
 
 #include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <map>
+#include <mutex>
+#include <tuple>
+#include <type_traits>
 #include <vector>
 
 #include "internal.cuh"
@@ -277,12 +283,14 @@ __global__ void __launch_bounds__(CHAIN_THREADS) k_chain_batch(const ChainTask<T
 }
 
 // Continued fractions of a batch of chains (grid.y = chain): the arithmetic
-// of k_cfrac, with the weight ||phi||^2 read from the chain's state.
-__global__ void k_cfrac_batch(const LanczosState *const *sts, const int *sgns, double e0,
+// of k_cfrac, with the weight ||phi||^2 read from the chain's state and the
+// ground energy of the chain's solve.
+__global__ void k_cfrac_batch(const LanczosState *const *sts, const int *sgns, const double *e0s,
                               double beta, int nmats, double2 *G) {
   const int n = blockIdx.x * blockDim.x + threadIdx.x;
   const int c = blockIdx.y;
   if (n >= nmats) return;
+  const double e0 = e0s[c];
   const LanczosState *st = sts[c];
   const int k = st->j;
   const double weight = st->acc[0];
@@ -487,6 +495,228 @@ bool ed_gf_batchable(ed_sector s, int spin, int create) {
   return nb->bdim <= CHAIN_MAX_DIM && nb->small_cols != nullptr;
 }
 
+// ----------------------------------------------------------------- cross-request batches
+//
+// Solves that reach their small-sector chains at about the same time (the
+// requests a server runs concurrently, or several host threads calling
+// ed_solve) share one launch of k_chain_batch / k_cfrac_batch: the first
+// caller of a (device, precision, grid) group leads it, waits a short window
+// for the others while other small solves are under way, then launches every
+// member's chains at once on its own stream after the members' streams.  A
+// chain runs on one CTA from its own task and workspace, so its coefficients
+// and G do not depend on which other chains share the launch: a solve gives
+// the same result alone and in any mix.
+namespace {
+
+constexpr double kBatchWindowS = 1e-3;  // the leader's wait for more members
+constexpr double kMemberWaitS = 300.0;    // a member's bound on the leader's launch
+
+struct BatchMember {
+  int key = 0;
+  int nmats = 0;
+  double beta = 0;
+  size_t task_bytes = 0;              // bytes of one ChainTask of this precision
+  std::vector<unsigned char> tasks;   // nt tasks, device pointers inside
+  int nt = 0;
+  std::vector<LanczosState *> sts;
+  std::vector<int> sgn;
+  std::vector<double> e0;
+  cudaStream_t stream = nullptr;
+  cudaEvent_t ready = nullptr;        // recorded on the member's stream: workspace written
+  // filled by the leader
+  std::vector<double> G;
+  std::vector<int32_t> steps;
+  std::vector<double> weight;
+  ed_status st = ED_OK;
+  bool done = false;
+};
+
+struct BatchGroup {
+  std::vector<BatchMember *> members;
+};
+
+struct Batcher {
+  std::mutex mu;
+  std::condition_variable cv;
+  std::map<std::tuple<int, int, int, double>, BatchGroup *> open;  // (device, key, nmats, beta)
+  int active = 0;  // small solves under way (ed_gf_batch_announce)
+  int64_t launches = 0, chains = 0, max_members = 0;
+};
+Batcher &batcher() {
+  static Batcher b;
+  return b;
+}
+
+// Launches the chains of every member of a closed group on the leader's stream.
+template <typename Ti, typename To>
+ed_status run_group(const std::vector<BatchMember *> &ms, cudaStream_t cs) {
+  int nt = 0;
+  for (const BatchMember *m : ms) nt += m->nt;
+  const int nmats = ms[0]->nmats;
+  const double beta = ms[0]->beta;
+  std::vector<ChainTask<Ti, To>> tasks(nt);
+  std::vector<LanczosState *> sts(nt);
+  std::vector<int> sgn(nt);
+  std::vector<double> e0(nt);
+  int64_t nmax = 1;
+  {
+    int i = 0;
+    for (const BatchMember *m : ms)
+      for (int q = 0; q < m->nt; ++q, ++i) {
+        memcpy(&tasks[i], m->tasks.data() + (size_t)q * sizeof(ChainTask<Ti, To>),
+               sizeof(ChainTask<Ti, To>));
+        sts[i] = m->sts[q];
+        sgn[i] = m->sgn[q];
+        e0[i] = m->e0[q];
+        nmax = std::max<int64_t>(nmax, tasks[i].a.dst_dim);
+      }
+  }
+  const size_t o_tasks = 0, o_sts = al256(nt * sizeof(ChainTask<Ti, To>));
+  const size_t o_sgn = o_sts + al256(nt * sizeof(LanczosState *));
+  const size_t o_e0 = o_sgn + al256(nt * sizeof(int));
+  const size_t o_G = o_e0 + al256(nt * sizeof(double));
+  const size_t o_next = o_G + al256((size_t)nt * std::max(nmats, 1) * sizeof(double2));
+  void *mem = nullptr;
+  ED_TRY(ed_dmalloc(&mem, o_next + 256, cs, "batched chains"));
+  char *base = (char *)mem;
+  ed_status rs = ED_OK;
+  for (const BatchMember *m : ms)
+    if (rs == ED_OK && m->stream != cs && cudaStreamWaitEvent(cs, m->ready, 0) != cudaSuccess)
+      rs = ED_ERR_CUDA;
+  auto h2d = [&](size_t o, const void *src, size_t n) {
+    if (rs == ED_OK && cudaMemcpyAsync(base + o, src, n, cudaMemcpyHostToDevice, cs) != cudaSuccess)
+      rs = ED_ERR_CUDA;
+  };
+  h2d(o_tasks, tasks.data(), nt * sizeof(ChainTask<Ti, To>));
+  h2d(o_sts, sts.data(), nt * sizeof(LanczosState *));
+  h2d(o_sgn, sgn.data(), nt * sizeof(int));
+  h2d(o_e0, e0.data(), nt * sizeof(double));
+  if (rs == ED_OK && cudaMemsetAsync(base + o_next, 0, sizeof(int), cs) != cudaSuccess) rs = ED_ERR_CUDA;
+  if (rs == ED_OK && cudaFuncSetAttribute(k_chain_batch<Ti, To>,
+                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)(CHAIN_MAX_DIM * sizeof(To))) != cudaSuccess)
+    rs = ED_ERR_CUDA;
+  if (rs == ED_OK) {
+    k_chain_batch<Ti, To><<<(unsigned)std::min(nt, 2 * 152), CHAIN_THREADS,
+                            (size_t)nmax * sizeof(To), cs>>>(
+        (const ChainTask<Ti, To> *)(base + o_tasks), nt, (int *)(base + o_next));
+    ed_count_launches(1);
+    if (nmats > 0) {
+      k_cfrac_batch<<<dim3((nmats + 31) / 32, nt), 32, 0, cs>>>(
+          (const LanczosState *const *)(base + o_sts), (const int *)(base + o_sgn),
+          (const double *)(base + o_e0), beta, nmats, (double2 *)(base + o_G));
+      ed_count_launches(1);
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+      ed_set_cuda_error(e, "batched chains launch", __FILE__, __LINE__);
+      rs = ED_ERR_CUDA;
+    }
+  }
+  std::vector<double> G((size_t)nt * 2 * std::max(nmats, 0));
+  std::vector<int32_t> hj(nt, 0);
+  std::vector<double> hw(nt, 0.0);
+  if (rs == ED_OK && nmats > 0 &&
+      cudaMemcpyAsync(G.data(), base + o_G, G.size() * sizeof(double), cudaMemcpyDeviceToHost,
+                      cs) != cudaSuccess)
+    rs = ED_ERR_CUDA;
+  for (int i = 0; i < nt && rs == ED_OK; ++i) {
+    if (cudaMemcpyAsync(&hj[i], &sts[i]->j, sizeof(int32_t), cudaMemcpyDeviceToHost, cs) !=
+            cudaSuccess ||
+        cudaMemcpyAsync(&hw[i], &sts[i]->acc[0], sizeof(double), cudaMemcpyDeviceToHost, cs) !=
+            cudaSuccess)
+      rs = ED_ERR_CUDA;
+  }
+  cudaError_t e = cudaStreamSynchronize(cs);
+  if (rs == ED_OK && e != cudaSuccess) {
+    ed_set_cuda_error(e, "batched chains", __FILE__, __LINE__);
+    rs = ED_ERR_CUDA;
+  }
+  ed_dfree(mem, cs);
+  int i = 0;
+  for (BatchMember *m : ms) {
+    m->st = rs;
+    m->G.assign(G.begin() + (size_t)i * 2 * std::max(nmats, 0),
+                G.begin() + (size_t)(i + m->nt) * 2 * std::max(nmats, 0));
+    m->steps.assign(hj.begin() + i, hj.begin() + i + m->nt);
+    m->weight.assign(hw.begin() + i, hw.begin() + i + m->nt);
+    i += m->nt;
+  }
+  return rs;
+}
+
+// Joins (or leads) the group of m's kind; returns when m's chains have run.
+template <typename Ti, typename To>
+ed_status join_group(BatchMember &m) {
+  Batcher &B = batcher();
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return ED_ERR_CUDA;
+  const auto key = std::make_tuple(dev, m.key, m.nmats, m.beta);
+  std::unique_lock<std::mutex> lk(B.mu);
+  auto it = B.open.find(key);
+  if (it != B.open.end()) {
+    it->second->members.push_back(&m);
+    B.cv.notify_all();
+    // bounded: the leader's launch ends with a synchronisation of its stream
+    const auto deadline = std::chrono::steady_clock::now() +
+                          std::chrono::microseconds((int64_t)(kMemberWaitS * 1e6));
+    while (!m.done)
+      if (B.cv.wait_until(lk, deadline) == std::cv_status::timeout && !m.done) {
+        ed_set_error_msg("batched chains: the leading solve did not finish in time");
+        return ED_ERR_TIMEOUT;
+      }
+    return m.st;
+  }
+  BatchGroup *g = new BatchGroup();
+  g->members.push_back(&m);
+  B.open[key] = g;
+  // wait a short window for the other small solves under way to join
+  const auto deadline = std::chrono::steady_clock::now() +
+                        std::chrono::microseconds((int64_t)(kBatchWindowS * 1e6));
+  while ((int)g->members.size() < B.active &&
+         B.cv.wait_until(lk, deadline) != std::cv_status::timeout) {
+  }
+  B.open.erase(key);
+  lk.unlock();
+  const ed_status rs = run_group<Ti, To>(g->members, m.stream);
+  lk.lock();
+  B.launches += 1;
+  int64_t nt = 0;
+  for (BatchMember *x : g->members) {
+    nt += x->nt;
+    x->done = true;
+  }
+  B.chains += nt;
+  B.max_members = std::max<int64_t>(B.max_members, (int64_t)g->members.size());
+  delete g;
+  lk.unlock();
+  B.cv.notify_all();
+  return rs;
+}
+
+}  // namespace
+
+// Small solves under way: a leader only waits for more members while more
+// than one is (see join_group).
+void ed_gf_batch_announce(int delta) {
+  Batcher &B = batcher();
+  {
+    std::lock_guard<std::mutex> lk(B.mu);
+    B.active = std::max(0, B.active + delta);
+  }
+  B.cv.notify_all();
+}
+
+extern "C" ed_status ed_batch_stats(int64_t *launches, int64_t *chains, int64_t *max_solves) {
+  if (!launches || !chains || !max_solves) return ED_ERR_ARG;
+  Batcher &B = batcher();
+  std::lock_guard<std::mutex> lk(B.mu);
+  *launches = B.launches;
+  *chains = B.chains;
+  *max_solves = B.max_members;
+  return ED_OK;
+}
+
 template <typename Ti, typename To>
 static ed_status chain_batch(ed_sector s, const Ti *psi, double e0, int nsteps, double beta,
                              int nmats, int njobs, const int *orb, const int *spin,
@@ -528,81 +758,44 @@ static ed_status chain_batch(ed_sector s, const Ti *psi, double e0, int nsteps, 
   }
   const int nt = (int)tasks.size();
   if (nt == 0) return ED_OK;
-  const size_t o_tasks = bytes, o_sts = o_tasks + al256(nt * sizeof(ChainTask<Ti, To>));
-  const size_t o_sgn = o_sts + al256(nt * sizeof(LanczosState *));
-  const size_t o_G = o_sgn + al256(nt * sizeof(int));
-  const size_t o_next = o_G + al256((size_t)nt * std::max(nmats, 1) * sizeof(double2));
+  // the chains' vectors and states, on this solve's stream
   void *mem = nullptr;
-  ED_TRY(ed_dmalloc(&mem, o_next + 256, cs, "batched chains"));
+  ED_TRY(ed_dmalloc(&mem, bytes + 256, cs, "batched chain workspace"));
   char *base = (char *)mem;
-  std::vector<LanczosState *> sts(nt);
-  int64_t nmax = 0;
+  BatchMember m;
+  m.key = std::is_same<Ti, double>::value * 2 + std::is_same<To, double>::value;
+  m.nmats = nmats;
+  m.beta = beta;
+  m.nt = nt;
+  m.stream = cs;
   for (int i = 0; i < nt; ++i) {
     char *p = base + off[i];
     const size_t vb = al256(tasks[i].a.dst_dim * sizeof(To));
     tasks[i].b0 = (To *)p;
     tasks[i].b1 = (To *)(p + vb);
     tasks[i].b2 = (To *)(p + 2 * vb);
-    tasks[i].st = sts[i] = (LanczosState *)(p + 3 * vb);
-    nmax = std::max<int64_t>(nmax, tasks[i].a.dst_dim);
+    tasks[i].st = (LanczosState *)(p + 3 * vb);
+    m.sts.push_back(tasks[i].st);
+    m.sgn.push_back(sgn[i]);
+    m.e0.push_back(e0);
   }
+  m.tasks.resize((size_t)nt * sizeof(ChainTask<Ti, To>));
+  memcpy(m.tasks.data(), tasks.data(), m.tasks.size());
   ed_status rs = ED_OK;
-  auto h2d = [&](size_t o, const void *src, size_t n) {
-    if (rs == ED_OK && cudaMemcpyAsync(base + o, src, n, cudaMemcpyHostToDevice, cs) != cudaSuccess)
-      rs = ED_ERR_CUDA;
-  };
-  h2d(o_tasks, tasks.data(), nt * sizeof(ChainTask<Ti, To>));
-  h2d(o_sts, sts.data(), nt * sizeof(LanczosState *));
-  h2d(o_sgn, sgn.data(), nt * sizeof(int));
-  if (rs == ED_OK && cudaMemsetAsync(base + o_next, 0, sizeof(int), cs) != cudaSuccess) rs = ED_ERR_CUDA;
-  if (rs == ED_OK && cudaFuncSetAttribute(k_chain_batch<Ti, To>,
-                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          (int)(CHAIN_MAX_DIM * sizeof(To))) != cudaSuccess)
+  if (cudaEventCreateWithFlags(&m.ready, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventRecord(m.ready, cs) != cudaSuccess)
     rs = ED_ERR_CUDA;
-  if (rs == ED_OK) {
-    k_chain_batch<Ti, To><<<(unsigned)std::min(nt, 2 * 152), CHAIN_THREADS,
-                            (size_t)nmax * sizeof(To), cs>>>(
-        (const ChainTask<Ti, To> *)(base + o_tasks), nt, (int *)(base + o_next));
-    ed_count_launches(1);
-    if (nmats > 0) {
-      k_cfrac_batch<<<dim3((nmats + 31) / 32, nt), 32, 0, cs>>>(
-          (const LanczosState *const *)(base + o_sts), (const int *)(base + o_sgn), e0, beta, nmats,
-          (double2 *)(base + o_G));
-      ed_count_launches(1);
-    }
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) {
-      ed_set_cuda_error(e, "batched chains launch", __FILE__, __LINE__);
-      rs = ED_ERR_CUDA;
-    }
-  }
-  std::vector<double> G((size_t)nt * 2 * std::max(nmats, 0));
-  std::vector<int32_t> hj(nt, 0);
-  std::vector<double> hw(nt, 0.0);
-  if (rs == ED_OK && nmats > 0 &&
-      cudaMemcpyAsync(G.data(), base + o_G, G.size() * sizeof(double), cudaMemcpyDeviceToHost,
-                      cs) != cudaSuccess)
-    rs = ED_ERR_CUDA;
-  for (int i = 0; i < nt && rs == ED_OK; ++i) {
-    if (cudaMemcpyAsync(&hj[i], &sts[i]->j, sizeof(int32_t), cudaMemcpyDeviceToHost, cs) !=
-            cudaSuccess ||
-        cudaMemcpyAsync(&hw[i], &sts[i]->acc[0], sizeof(double), cudaMemcpyDeviceToHost, cs) !=
-            cudaSuccess)
-      rs = ED_ERR_CUDA;
-  }
-  cudaError_t e = cudaStreamSynchronize(cs);
-  if (rs == ED_OK && e != cudaSuccess) {
-    ed_set_cuda_error(e, "batched chains", __FILE__, __LINE__);
-    rs = ED_ERR_CUDA;
-  }
+  if (rs == ED_OK) rs = join_group<Ti, To>(m);
+  if (m.ready) cudaEventDestroy(m.ready);
+  if (rs == ED_ERR_TIMEOUT) return rs;  // the leader may still use the workspace: keep it
   ed_dfree(mem, cs);
   if (rs != ED_OK) return rs;
   for (int i = 0; i < nt; ++i) {
     const int q = job_of[i];
-    weight[q] = hw[i];
-    steps[q] = hj[i];
+    weight[q] = m.weight[i];
+    steps[q] = m.steps[i];
     if (nmats > 0)
-      memcpy(host_G + 2 * (size_t)nmats * q, G.data() + 2 * (size_t)nmats * i,
+      memcpy(host_G + 2 * (size_t)nmats * q, m.G.data() + 2 * (size_t)nmats * i,
              2 * sizeof(double) * nmats);
   }
   return ED_OK;

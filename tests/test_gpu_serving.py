@@ -113,3 +113,37 @@ def test_injected_allocation_failure_and_polling(ed):
         t = srv.submit(big, 7, 7, **OPTS)
         assert srv.wait(t, 0.001) == ed.ED_ERR_TIMEOUT      # bounded wait
         assert srv.wait(t, 300.0) == 0
+
+
+def test_small_requests_share_chain_launches(ed):
+    """Requests whose Green's-function chains live in small sectors (every
+    N+-1 sector at most 2^14 states: Ns=8 and Norb=2 Ns=8 sectors here) and
+    that reach that phase together share one persistent launch of their
+    chains (ed_batch_stats counts launches that merged several solves); every
+    request's E0 and G are the same, bit for bit, as the same request solved
+    alone in a launch of its own."""
+    rng = np.random.default_rng(8)
+    reqs = []
+    for i in range(24):
+        if i % 2:
+            m = make_model(1, 7, U=float(rng.uniform(1, 4)), seed=100 + i)
+            nup, ndw = 4 + (i % 3 == 0), 4
+        else:
+            m = make_model(2, 3, U=float(rng.uniform(1, 4)), Jh=0.3, seed=200 + i)
+            nup, ndw = 4, 4 - (i % 4 == 0)
+        reqs.append((m, nup, ndw))
+    alone = [ed.solve(m, nup, ndw, **OPTS) for (m, nup, ndw) in reqs]
+    before = ed.batch_stats()
+    with ed.Server(slots=8) as srv:
+        tickets = [srv.submit(m, nup, ndw, **OPTS) for (m, nup, ndw) in reqs]
+        res = _wait_all(srv, tickets)
+    after = ed.batch_stats()
+    # every request's chains ran batched, and some launches merged solves:
+    # fewer launches than requests
+    assert 0 < after["launches"] - before["launches"] < len(reqs)
+    assert after["max_solves"] >= 2
+    for (r_alone, G_alone), t in zip(alone, tickets):
+        r_mix, G_mix = res[t]
+        assert r_mix["status"] == 0
+        assert r_mix["e0"] == r_alone["e0"]
+        assert np.array_equal(G_mix, G_alone)
