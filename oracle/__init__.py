@@ -20,8 +20,13 @@ Modules
               inverse iteration, the second pass for the ground-state vector
               and an FP64 Rayleigh-quotient polish.
 ``gf``        Impurity Green's function from c^+|gs> and c|gs> Lanczos chains
-              and continued fractions (Sec. 6.8, Eq. KLgf), plus the exact
+              and continued fractions (Sec. 6.8, Eq. KLgf) at Matsubara or
+              arbitrary complex frequencies (the real axis), plus the exact
               Lehmann sum from dense eigenvectors for small sectors.
+``observables`` The non-interacting impurity function of the normal bath, the
+              self-energy by the Dyson equation, the Hartree limit of the
+              self-energy, and local densities, density-density correlators
+              and the interaction energy of a ground state (Sec. 6.8, App. B).
 
 Every function cites the passage of the paper it follows.  Pins (tests under
 ``tests/test_oracle_*.py``) tie each function to something other than itself:

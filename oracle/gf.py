@@ -80,8 +80,17 @@ def continued_fraction(a, b, z):
 def impurity_gf(model, nup, ndw, psi, e0, orb, spin, nsteps=200, beta=100.0,
                 nmats=512, return_parts=False):
     """G_{orb,spin}(i w_n) from two Lanczos chains of ``nsteps`` steps."""
-    wn = matsubara(beta, nmats)
-    G = np.zeros(nmats, dtype=np.complex128)
+    return impurity_gf_z(model, nup, ndw, psi, e0, orb, spin, 1j * matsubara(beta, nmats),
+                         nsteps=nsteps, return_parts=return_parts)
+
+
+def impurity_gf_z(model, nup, ndw, psi, e0, orb, spin, z, nsteps=200, return_parts=False):
+    """G_{orb,spin}(z) at arbitrary complex frequencies z (Eq. KLgf at T = 0):
+    n+ [(E0 + z - T+)^-1]_00 - n- [(E0 - z - T-)^-1]_00 from the chains
+    started at c^+|gs> and c|gs> (z = i w_n: the Matsubara axis; z = w + i eta:
+    the real axis, retarded)."""
+    z = np.asarray(z, dtype=np.complex128)
+    G = np.zeros(z.shape, dtype=np.complex128)
     parts = {}
     for create in (+1, -1):
         phi, (n2u, n2d) = _apply(model, psi, nup, ndw, orb, spin, create)
@@ -96,9 +105,9 @@ def impurity_gf(model, nup, ndw, psi, e0, orb, spin, nsteps=200, beta=100.0,
         a, b = lanczos_chain(sec.matvec, phi, nsteps)
         parts[create] = (nrm2, a, b)
         if create > 0:
-            G += nrm2 * continued_fraction(a, b, e0 + 1j * wn)
+            G += nrm2 * continued_fraction(a, b, e0 + z)
         else:
-            G -= nrm2 * continued_fraction(a, b, e0 - 1j * wn)
+            G -= nrm2 * continued_fraction(a, b, e0 - z)
     if return_parts:
         return G, parts
     return G
@@ -107,11 +116,17 @@ def impurity_gf(model, nup, ndw, psi, e0, orb, spin, nsteps=200, beta=100.0,
 def lehmann_gf_dense(model, nup, ndw, orb, spin, beta=100.0, nmats=512):
     """Exact T = 0 Lehmann sum of Eq. KLgf from dense eigenvectors of the
     sector and its two neighbours (small sectors only)."""
-    wn = matsubara(beta, nmats)
+    return lehmann_gf_dense_z(model, nup, ndw, orb, spin, 1j * matsubara(beta, nmats))
+
+
+def lehmann_gf_dense_z(model, nup, ndw, orb, spin, z):
+    """The exact Lehmann sum at arbitrary complex frequencies z: returns
+    (G(z), E0)."""
+    z = np.asarray(z, dtype=np.complex128)
     s0 = fock.get_sector(model, nup, ndw)
     E, U = np.linalg.eigh(s0.hamiltonian().toarray())
     e0, gs = E[0], U[:, 0]
-    G = np.zeros(nmats, dtype=np.complex128)
+    G = np.zeros(z.shape, dtype=np.complex128)
     for create in (+1, -1):
         phi, (n2u, n2d) = _apply(model, gs, nup, ndw, orb, spin, create)
         if phi is None or not np.any(phi):
@@ -120,7 +135,7 @@ def lehmann_gf_dense(model, nup, ndw, orb, spin, beta=100.0, nmats=512):
         E1, U1 = np.linalg.eigh(s1.hamiltonian().toarray())
         w = (U1.T @ phi) ** 2
         if create > 0:
-            G += (w[None, :] / (1j * wn[:, None] - (E1 - e0)[None, :])).sum(1)
+            G += (w[None, :] / (z[:, None] - (E1 - e0)[None, :])).sum(1)
         else:
-            G += (w[None, :] / (1j * wn[:, None] + (E1 - e0)[None, :])).sum(1)
+            G += (w[None, :] / (z[:, None] + (E1 - e0)[None, :])).sum(1)
     return G, e0

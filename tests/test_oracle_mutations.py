@@ -65,3 +65,82 @@ def test_wrong_hole_sign_in_gf_is_caught(monkeypatch):
     monkeypatch.setattr(gf, "continued_fraction", bad)
     G2 = gf.impurity_gf(m, 3, 3, r["psi"], r["e0"], 0, 0, nmats=16)
     assert np.abs(G2 - ref).max() > 1e-3
+
+
+def _two_orbital_case():
+    from workloads import ImpurityModel
+    r = np.random.default_rng(64)
+    base = make_model(2, 3, U=2.6, Jh=0.4, seed=64)
+    m = ImpurityModel(norb=2, nbath=3, U=base.U, Ust=base.Ust, Jh=base.Jh,
+                      e_imp=base.e_imp + r.normal(0, .2, (2, 2)),
+                      e_bath=base.e_bath + r.normal(0, .2, base.e_bath.shape),
+                      v_bath=base.v_bath * r.uniform(.5, 1.5, base.v_bath.shape))
+    fock._SECTOR_CACHE.clear()
+    s = fock.Sector(m, 4, 3)
+    return m, s, lanczos.ground_state(s.matvec, s.dim)
+
+
+def _e_int_mismatch(m, s, r):
+    from oracle import observables
+    from workloads import ImpurityModel
+    m0 = ImpurityModel(norb=m.norb, nbath=m.nbath, U=0.0, Ust=0.0, Jh=0.0, e_imp=m.e_imp,
+                       e_bath=m.e_bath, v_bath=m.v_bath)
+    e_free = float(r["psi"] @ fock.Sector(m0, 4, 3).matvec(r["psi"]))
+    _, _, e_int = observables.local_observables(m, 4, 3, r["psi"])
+    return abs(r["e0"] - e_free - e_int)
+
+
+def test_dropped_same_spin_term_in_interaction_energy_is_caught(monkeypatch):
+    from oracle import observables
+    m, s, r = _two_orbital_case()
+    assert _e_int_mismatch(m, s, r) < 1e-10
+    orig = observables.local_observables
+
+    def bad(model, nup, ndw, psi):
+        dens, nn, e_int = orig(model, nup, ndw, psi)
+        return dens, nn, e_int - (model.Ust - model.Jh) * (nn[0, 0, 0, 1] + nn[1, 1, 0, 1])
+    monkeypatch.setattr(observables, "local_observables", bad)
+    assert _e_int_mismatch(m, s, r) > 1e-3
+
+
+def test_wrong_spin_in_hartree_term_is_caught(monkeypatch):
+    from oracle import observables
+    m, s, r = _two_orbital_case()
+    dens, _, _ = observables.local_observables(m, 4, 3, r["psi"])
+    z = np.array([1e4j])
+
+    def tail_err():
+        G = gf.impurity_gf_z(m, 4, 3, r["psi"], r["e0"], 0, 0, z)
+        S = observables.self_energy(m, 0, 0, z, G)
+        return abs(S[0] - observables.hartree(m, dens, 0, 0))
+    assert tail_err() < 2e-3
+
+    def bad(model, d, orb, spin):   # the same-spin density where the other spin's belongs
+        h = model.U * d[spin, orb]
+        for b in range(model.norb):
+            if b != orb:
+                h += model.Ust * d[1 - spin, b] + (model.Ust - model.Jh) * d[spin, b]
+        return h
+    monkeypatch.setattr(observables, "hartree", bad)
+    assert tail_err() > 1e-2
+
+
+def test_wrong_sign_in_hybridisation_is_caught(monkeypatch):
+    from oracle import observables
+    m, s, r = _two_orbital_case()
+    z = 1j * gf.matsubara(50.0, 32)
+
+    def sigma_max():
+        G = gf.impurity_gf_z(m, 4, 3, r["psi"], r["e0"], 0, 0, z)
+        return np.abs(observables.self_energy(m, 0, 0, z, G)).max()
+    from workloads import ImpurityModel
+    m0 = ImpurityModel(norb=2, nbath=3, U=0.0, Ust=0.0, Jh=0.0, e_imp=m.e_imp, e_bath=m.e_bath,
+                       v_bath=m.v_bath)
+    fock._SECTOR_CACHE.clear()
+    s0 = fock.Sector(m0, 4, 3)
+    r0 = lanczos.ground_state(s0.matvec, s0.dim)
+    G0 = gf.impurity_gf_z(m0, 4, 3, r0["psi"], r0["e0"], 0, 0, z)
+    assert np.abs(observables.self_energy(m0, 0, 0, z, G0)).max() < 1e-7
+    orig = observables.hybridisation
+    monkeypatch.setattr(observables, "hybridisation", lambda mm, o, sp, zz: -orig(mm, o, sp, zz))
+    assert np.abs(observables.self_energy(m0, 0, 0, z, G0)).max() > 1e-2

@@ -12,7 +12,7 @@ import numpy as np
 import pytest
 import scipy.linalg as sla
 
-from oracle import fock, fullfock, gf, lanczos
+from oracle import fock, fullfock, gf, lanczos, observables
 from workloads import (SplitMix64, make_model, splitmix64_uniform_array,
                        workload_ns8, ImpurityModel)
 
@@ -337,3 +337,149 @@ def test_gf_lehmann_symmetry_and_sum_rule_ns8():
     assert np.abs(1j * wn * Gt - 1.0).max() < 1e-3
     Gd = gf.impurity_gf(m, 4, 4, r["psi"], r["e0"], 0, 1)
     assert np.abs(G - Gd).max() < 1e-10          # spin symmetry at N_up = N_dw
+
+
+# ---------------------------------------------------------------- f1: Sigma, real axis, observables
+
+def _u0(m):
+    """The same model with every interaction switched off."""
+    return ImpurityModel(norb=m.norb, nbath=m.nbath, U=0.0, Ust=0.0, Jh=0.0, e_imp=m.e_imp,
+                         e_bath=m.e_bath, v_bath=m.v_bath)
+
+
+def test_g0_inverse_is_schur_complement_of_one_body_matrix():
+    """1 / G0^-1(z) of the normal bath equals [(z - h)^-1]_{dd} of the
+    one-body matrix h (an independent route: a dense inverse)."""
+    m = _spin_asym(make_model(2, 3, U=2.0, Jh=0.3, seed=61), 61)
+    z = np.array([0.3j, 1.7j, 0.4 + 0.05j, -1.1 + 0.2j])
+    for spin in (0, 1):
+        h = _one_body(m, spin)
+        for orb in range(m.norb):
+            d = fock.level_of_impurity(m, orb)
+            ref = np.array([np.linalg.inv(x * np.eye(m.ns) - h)[d, d] for x in z])
+            got = 1.0 / observables.g0_inverse(m, orb, spin, z)
+            assert np.abs(got - ref).max() < 1e-12
+
+
+def test_sigma_vanishes_without_interaction():
+    """U = U' = J = 0: the chains span their Krylov spaces exactly, so G = G0
+    and the Dyson self-energy is zero."""
+    m = _spin_asym(make_model(2, 3, U=0.0, Jh=0.0, Ust=0.0, seed=62), 62)
+    s = fock.Sector(m, 4, 3)
+    r = lanczos.ground_state(s.matvec, s.dim)
+    z = 1j * gf.matsubara(50.0, 64)
+    for spin in (0, 1):
+        for orb in range(m.norb):
+            G = gf.impurity_gf_z(m, 4, 3, r["psi"], r["e0"], orb, spin, z)
+            S = observables.self_energy(m, orb, spin, z, G)
+            assert np.abs(S).max() < 1e-7, (orb, spin)
+
+
+def test_sigma_particle_hole_symmetry_ns8():
+    """Particle-hole symmetric single-orbital model at half filling
+    (e_d = -U/2, symmetric bath): Re Sigma(i w_n) = U / 2 at every n."""
+    wl = workload_ns8()
+    m = wl.model
+    s = fock.Sector(m, 4, 4)
+    r = lanczos.ground_state(s.matvec, s.dim)
+    z = 1j * gf.matsubara(100.0, 128)
+    G = gf.impurity_gf_z(m, 4, 4, r["psi"], r["e0"], 0, 0, z)
+    S = observables.self_energy(m, 0, 0, z, G)
+    assert np.abs(S.real - m.U / 2).max() < 1e-9
+    assert np.all(S.imag <= 1e-12)              # causal: Im Sigma(i w) <= 0
+
+
+@pytest.mark.parametrize("case", ["ns8", "norb2_asym"])
+def test_sigma_hartree_tail(case):
+    """At large |z| the self-energy tends to its first moment, the Hartree
+    term U<n_{a,-s}> + U' sum <n_{b,-s}> + (U'-J) sum <n_{b,s}>; the next
+    term falls as 1/|z|."""
+    if case == "ns8":
+        m, nup, ndw = workload_ns8().model, 4, 4
+    else:
+        m, nup, ndw = _spin_asym(make_model(2, 3, U=2.6, Jh=0.4, seed=63), 63), 4, 3
+    s = fock.Sector(m, nup, ndw)
+    r = lanczos.ground_state(s.matvec, s.dim)
+    dens, _, _ = observables.local_observables(m, nup, ndw, r["psi"])
+    z = np.array([1e4j, 2e4j])
+    for spin in (0, 1):
+        for orb in range(m.norb):
+            G = gf.impurity_gf_z(m, nup, ndw, r["psi"], r["e0"], orb, spin, z)
+            S = observables.self_energy(m, orb, spin, z, G)
+            h = observables.hartree(m, dens, orb, spin)
+            err = np.abs(S - h)
+            assert err[0] < 2e-3 and err[1] < 0.6 * err[0] + 1e-9, (orb, spin, err)
+
+
+def test_real_axis_gf_lehmann_causality_and_sum_rule():
+    """The real-axis G(w + i eta) of the 200-step chains against the exact
+    Lehmann sum (dense eigenvectors) on the Ns=8 sector: equal to rounding
+    for eta = 0.3 (the continued fraction of a 200-step chain converges
+    quickly a distance eta from the real axis; at eta = 0.05 the two differ
+    by 6e-4 near the poles, as a 200-step chain does not span the 3920-state
+    Krylov space: reading 15), Im G <= 0 everywhere, and the spectral sum rule
+    -1/pi int Im G(w + i eta) dw = n+ + n- = 1 (the Lorentzian tails beyond
+    |w| = 40 cut 2 eta / (pi 40) at most)."""
+    wl = workload_ns8()
+    m = wl.model
+    s = fock.Sector(m, 4, 4)
+    r = lanczos.ground_state(s.matvec, s.dim)
+    w = np.linspace(-10.0, 10.0, 2001)
+    G3 = gf.impurity_gf_z(m, 4, 4, r["psi"], r["e0"], 0, 0, w + 0.3j)
+    Gx, _ = gf.lehmann_gf_dense_z(m, 4, 4, 0, 0, w + 0.3j)
+    assert np.abs(G3 - Gx).max() < 1e-11
+    eta = 0.05
+    w = np.linspace(-40.0, 40.0, 16001)
+    G = gf.impurity_gf_z(m, 4, 4, r["psi"], r["e0"], 0, 0, w + 1j * eta)
+    assert np.all(G.imag <= 0.0)
+    weight = -np.trapezoid(G.imag, w) / np.pi
+    assert abs(weight - 1.0) < 2 * eta / (np.pi * 40.0) + 1e-3
+
+
+def test_local_observables_pins():
+    """Densities equal the hole weights ||c_{a s} psi||^2 of the chains (the
+    operators of Sec. 2.3, an independent route); particle-hole symmetry
+    gives n = 1/2; without interaction the two spins are uncorrelated,
+    <n_up n_dw> = <n_up><n_dw>; the interaction energy equals E0 minus the
+    energy of the same state under the model with every interaction
+    switched off; in the atomic limit (V = 0) the double occupancy is 0 or
+    1."""
+    # densities vs chain weights, and E_int, on an asymmetric two-orbital sector
+    m = _spin_asym(make_model(2, 3, U=2.6, Jh=0.4, seed=64), 64)
+    nup, ndw = 4, 3
+    s = fock.Sector(m, nup, ndw)
+    r = lanczos.ground_state(s.matvec, s.dim)
+    psi = r["psi"]
+    dens, nn, e_int = observables.local_observables(m, nup, ndw, psi)
+    for spin in (0, 1):
+        for orb in range(m.norb):
+            phi, _ = gf._apply(m, psi, nup, ndw, orb, spin, -1)
+            assert abs(dens[spin, orb] - float(phi @ phi)) < 1e-12
+            assert abs(nn[spin, spin, orb, orb] - dens[spin, orb]) < 1e-12   # n^2 = n
+    s0 = fock.Sector(_u0(m), nup, ndw)
+    e_free = float(psi @ s0.matvec(psi))
+    assert abs(r["e0"] - e_free - e_int) < 1e-10 * max(1.0, abs(r["e0"]))
+    # particle-hole symmetric single orbital at half filling
+    wl = workload_ns8()
+    s8 = fock.Sector(wl.model, 4, 4)
+    r8 = lanczos.ground_state(s8.matvec, s8.dim)
+    d8, nn8, _ = observables.local_observables(wl.model, 4, 4, r8["psi"])
+    assert np.abs(d8 - 0.5).max() < 1e-10
+    assert 0.0 < nn8[0, 1, 0, 0] < 0.25          # U > 0 suppresses double occupancy
+    # no interaction: spins uncorrelated
+    mu = _u0(m)
+    su = fock.Sector(mu, nup, ndw)
+    ru = lanczos.ground_state(su.matvec, su.dim)
+    du, nnu, eu = observables.local_observables(mu, nup, ndw, ru["psi"])
+    assert eu == 0.0
+    for a in range(m.norb):
+        for b in range(m.norb):
+            assert abs(nnu[0, 1, a, b] - du[0, a] * du[1, b]) < 1e-9
+    # atomic limit: integer double occupancy
+    ma = ImpurityModel(norb=1, nbath=3, U=1.5, Ust=1.5, Jh=0.0, e_imp=np.array([-0.4]),
+                       e_bath=np.array([[-0.9, 0.2, 0.8]]), v_bath=np.zeros((1, 3)))
+    sa = fock.Sector(ma, 2, 1)
+    E, U = np.linalg.eigh(sa.hamiltonian().toarray())
+    assert E[1] - E[0] > 1e-6                    # a non-degenerate ground state
+    _, nna, _ = observables.local_observables(ma, 2, 1, U[:, 0])
+    assert min(abs(nna[0, 1, 0, 0]), abs(nna[0, 1, 0, 0] - 1.0)) < 1e-12
