@@ -267,6 +267,42 @@ ed_status ed_gf_lanczos(ed_sector s, ed_precision prec, const void *d_psi, doubl
                         int32_t nmats, double *host_G, ed_gf_info *info,
                         void *stream);
 
+/* The same Green's function at arbitrary complex frequencies z_n (Sec. 6.8,
+ * Eq. KLgf; App. B for the real axis): host_z holds nz complex values (re, im
+ * interleaved) and host_G receives 2*nz doubles,
+ *   G(z) = n+ [(e0 + z - T+)^-1]_00 - n- [(e0 - z - T-)^-1]_00,
+ * so z = i w_n gives the Matsubara function of ed_gf_lanczos and z = w + i eta
+ * (eta > 0) the retarded function on the real axis.  Arguments otherwise as
+ * ed_gf_lanczos.  Synchronises `stream`. */
+ed_status ed_gf_lanczos_z(ed_sector s, ed_precision prec, const void *d_psi, double e0,
+                          int32_t orb, int32_t spin, int32_t nsteps, const double *host_z,
+                          int32_t nz, double *host_G, ed_gf_info *info, void *stream);
+
+/* Impurity self-energy by the Dyson equation (Sec. 6.8, App. B):
+ *   Sigma(z) = G0(z)^-1 - G(z)^-1,
+ *   G0_{orb,spin}(z)^-1 = z - e_imp[spin][orb]
+ *                         - sum_nu v_bath[spin][orb][nu]^2 / (z - e_bath[spin][orb][nu])
+ * (the non-interacting impurity function of the normal bath of `model`).
+ * host_z and host_G: nz complex values each (re, im interleaved), host_sigma
+ * receives 2*nz doubles; all host arrays owned by the caller.  ED_ERR_ARG for
+ * a null pointer, nz < 0 or orb / spin out of range.  Synchronises `stream`. */
+ed_status ed_sigma(const ed_model *model, int32_t orb, int32_t spin, const double *host_z,
+                   int32_t nz, const double *host_G, double *host_sigma, void *stream);
+
+/* Local observables of a sector-order state psi of n = D elements (device;
+ * double for ED_FP64 / ED_FP32_POLISH, float for ED_FP32), normalised by the
+ * call (App. B: densities and double occupancies of the impurity).
+ * host_out receives 2*norb + 4*norb*norb + 2 doubles:
+ *   dens[s][a]        <n_{a s}>                          (2*norb)
+ *   nn[s][t][a][b]    <n_{a s} n_{b t}>                  (4*norb*norb; the
+ *                     double occupancy of orbital a is nn[0][1][a][a])
+ *   e_int             <H_int> = U sum_a nn[0][1][a][a] + U' sum_{a!=b} nn[0][1][a][b]
+ *                     + (U' - J) sum_{a<b} (nn[0][0][a][b] + nn[1][1][a][b])
+ *   norm              <psi, psi> before normalisation.
+ * ED_ERR_ARG when n != D.  Synchronises `stream`. */
+ed_status ed_observables(ed_sector s, ed_precision prec, const void *d_psi, int64_t n,
+                         double *host_out, void *stream);
+
 /* One impurity solve: sector build, ground state, and G for every orbital and
  * both spins (the down spin is copied from the up spin when N_up = N_dw and
  * the model is spin symmetric, Sec. 6.6 twin symmetry).  The particle and

@@ -28,7 +28,8 @@ EXPORTED = [
     "ed_sector_build", "ed_sector_get_info", "ed_sector_copy_tables", "ed_sector_copy_w",
     "ed_sector_free", "ed_matvec", "ed_matvec_blocked", "ed_sector_blocked_kernel",
     "ed_sector_tune_info", "ed_sector_set_kernel",
-    "ed_sector_permute", "ed_lanczos_ground", "ed_gf_lanczos", "ed_solve",
+    "ed_sector_permute", "ed_lanczos_ground", "ed_gf_lanczos", "ed_gf_lanczos_z", "ed_sigma",
+    "ed_observables", "ed_solve",
     "ed_server_create", "ed_submit", "ed_poll", "ed_wait", "ed_server_destroy",
     "ed_server_inject_alloc_failure", "ed_batch_stats", "ed_residual_noalloc", "ed_status_string",
     "ed_last_error",
@@ -164,6 +165,10 @@ def lib():
             "ed_server_inject_alloc_failure": [vp, i32],
             "ed_residual_noalloc": [vp, vp, i64, vp, vp],
             "ed_batch_stats": [C.POINTER(i64), C.POINTER(i64), C.POINTER(i64)],
+            "ed_gf_lanczos_z": [vp, C.c_int, vp, C.c_double, i32, i32, i32, vp, i32, vp,
+                                C.POINTER(ed_gf_info), vp],
+            "ed_sigma": [C.POINTER(ed_model), i32, i32, vp, i32, vp, vp, vp],
+            "ed_observables": [vp, C.c_int, vp, i64, vp, vp],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -391,6 +396,49 @@ def gf_lanczos(sector: Sector, psi, e0, orb, spin, precision="fp64", nsteps=200,
                                int(nmats), G.ctypes.data, C.byref(info),
                                C.c_void_p(_stream_ptr(stream))), "ed_gf_lanczos")
     return G.view(np.complex128), {k: getattr(info, k) for k, _ in info._fields_}
+
+
+def gf_lanczos_z(sector: Sector, psi, e0, orb, spin, z, precision="fp64", nsteps=200,
+                 stream=None):
+    """G_{orb,spin}(z) at arbitrary complex frequencies z (ed_gf_lanczos_z):
+    z = 1j * w_n gives the Matsubara axis, z = w + 1j * eta the real axis."""
+    zz = np.ascontiguousarray(np.asarray(z, dtype=np.complex128).reshape(-1))
+    G = np.zeros(zz.size, dtype=np.complex128)
+    info = ed_gf_info()
+    _check(lib().ed_gf_lanczos_z(sector.h, _prec(precision), C.c_void_p(psi.data_ptr()),
+                                 float(e0), int(orb), int(spin), int(nsteps),
+                                 C.c_void_p(zz.ctypes.data), int(zz.size),
+                                 C.c_void_p(G.ctypes.data), C.byref(info),
+                                 C.c_void_p(_stream_ptr(stream))), "ed_gf_lanczos_z")
+    return G, {k: getattr(info, k) for k, _ in info._fields_}
+
+
+def sigma(model, orb, spin, z, G, stream=None):
+    """Sigma(z) = G0(z)^-1 - G(z)^-1 of the model's normal bath (ed_sigma)."""
+    m = as_model(model)
+    zz = np.ascontiguousarray(np.asarray(z, dtype=np.complex128).reshape(-1))
+    gg = np.ascontiguousarray(np.asarray(G, dtype=np.complex128).reshape(-1))
+    if gg.size != zz.size:
+        raise EDError(ED_ERR_ARG, "sigma: G and z differ in length")
+    out = np.zeros(zz.size, dtype=np.complex128)
+    _check(lib().ed_sigma(C.byref(m.c), int(orb), int(spin), C.c_void_p(zz.ctypes.data),
+                          int(zz.size), C.c_void_p(gg.ctypes.data), C.c_void_p(out.ctypes.data),
+                          C.c_void_p(_stream_ptr(stream))), "ed_sigma")
+    return out
+
+
+def observables(sector: Sector, psi, precision="fp64", stream=None):
+    """Impurity densities, density-density correlators and interaction energy
+    of a sector-order state (ed_observables): dict with dens[2][norb],
+    nn[2][2][norb][norb], e_int, norm."""
+    no = sector.info["norb"]
+    out = np.zeros(2 * no + 4 * no * no + 2, dtype=np.float64)
+    _check(lib().ed_observables(sector.h, _prec(precision), C.c_void_p(psi.data_ptr()),
+                                int(psi.numel()), C.c_void_p(out.ctypes.data),
+                                C.c_void_p(_stream_ptr(stream))), "ed_observables")
+    return {"dens": out[:2 * no].reshape(2, no).copy(),
+            "nn": out[2 * no:2 * no + 4 * no * no].reshape(2, 2, no, no).copy(),
+            "e_int": float(out[-2]), "norm": float(out[-1])}
 
 
 def solve_opts(precision="fp32_polish", gf_precision=None, nmats=512, beta=100.0,

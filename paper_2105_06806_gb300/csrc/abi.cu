@@ -48,7 +48,7 @@ extern "C" const char *ed_status_string(ed_status st) {
 
 ed_status ed_gf_impl(ed_sector s, ed_precision prec, const void *d_psi, double e0, int orb,
                      int spin, int nsteps, double beta, int nmats, double *host_G,
-                     ed_gf_info *info, cudaStream_t cs);
+                     ed_gf_info *info, cudaStream_t cs, const double *host_z = nullptr);
 ed_status ed_gf_chain_job(ed_sector s, ed_precision prec, const void *d_psi, double e0, int orb,
                           int spin, int create, int nsteps, double beta, int nmats,
                           double *host_G, double *weight, int *steps, int64_t *dim,

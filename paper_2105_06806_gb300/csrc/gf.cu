@@ -105,6 +105,31 @@ __global__ void k_cfrac(const LanczosState *st, double weight, double e0, double
   G[n].y += sgn * gi;
 }
 
+// The same continued fraction at arbitrary complex frequencies z_n (the real
+// axis: z = w + i eta): G[n] += sgn * weight * [(E0 + sgn z_n - T)^-1]_00,
+// the particle term (sgn = +1) and the hole term (sgn = -1) of Eq. KLgf.
+// For z_n = i w_n this is k_cfrac's arithmetic.
+__global__ void k_cfrac_z(const LanczosState *st, double weight, double e0, const double2 *z,
+                          int nz, int sgn, double2 *G) {
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= nz) return;
+  const int k = st->j;
+  if (k <= 0 || weight == 0.0) return;
+  const double zr = e0 + sgn * z[n].x, zi = sgn * z[n].y;
+  double fr = zr - st->alpha[k - 1], fi = zi;
+  for (int m = k - 2; m >= 0; --m) {
+    const double b2 = st->beta[m + 1] * st->beta[m + 1];
+    const double inv = 1.0 / (fr * fr + fi * fi);
+    const double qr = b2 * fr * inv, qi = -b2 * fi * inv;
+    fr = zr - st->alpha[m] - qr;
+    fi = zi - qi;
+  }
+  const double inv = 1.0 / (fr * fr + fi * fi);
+  const double gr = weight * fr * inv, gi = -weight * fi * inv;
+  G[n].x += sgn * gr;
+  G[n].y += sgn * gi;
+}
+
 static size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 // ----------------------------------------------------------------- batched chains
@@ -317,7 +342,7 @@ __global__ void k_cfrac_batch(const LanczosState *const *sts, const int *sgns, c
 template <typename Ti, typename To>
 static ed_status one_chain(ed_sector s, const Ti *psi, int orb, int spin, int create, int nsteps,
                            double e0, double beta, int nmats, double2 *dG, double *weight,
-                           int *steps, cudaStream_t cs) {
+                           int *steps, cudaStream_t cs, const double2 *dz = nullptr) {
   *weight = 0.0;
   *steps = 0;
   ed_sector nb = nullptr;
@@ -380,7 +405,10 @@ static ed_status one_chain(ed_sector s, const Ti *psi, int orb, int spin, int cr
   }
   if (rs == ED_OK && hw[0] > 0.0 && nmats > 0) {
     // 32 frequencies per CTA: the FP64 recurrences spread over many SMs
-    k_cfrac<<<(nmats + 31) / 32, 32, 0, cs>>>(st, hw[0], e0, beta, nmats, create, dG);
+    if (dz)  // nmats arbitrary complex frequencies
+      k_cfrac_z<<<(nmats + 31) / 32, 32, 0, cs>>>(st, hw[0], e0, dz, nmats, create, dG);
+    else
+      k_cfrac<<<(nmats + 31) / 32, 32, 0, cs>>>(st, hw[0], e0, beta, nmats, create, dG);
     ed_count_launches(1);
     if (cudaGetLastError() != cudaSuccess) rs = ED_ERR_CUDA;
   }
@@ -392,14 +420,23 @@ static ed_status one_chain(ed_sector s, const Ti *psi, int orb, int spin, int cr
 
 ed_status ed_gf_impl(ed_sector s, ed_precision prec, const void *d_psi, double e0, int orb,
                      int spin, int nsteps, double beta, int nmats, double *host_G,
-                     ed_gf_info *info, cudaStream_t cs) {
+                     ed_gf_info *info, cudaStream_t cs, const double *host_z = nullptr) {
   if (!s || !d_psi || orb < 0 || orb >= s->mp.norb || spin < 0 || spin > 1 || nsteps <= 0 ||
-      nsteps > ED_MAX_LANCZOS || nmats < 0 || (nmats > 0 && (!host_G || !(beta > 0))))
+      nsteps > ED_MAX_LANCZOS || nmats < 0 ||
+      (nmats > 0 && (!host_G || (!host_z && !(beta > 0)))))
     return ED_ERR_ARG;
   double2 *dG = nullptr;
-  ED_TRY(ed_dmalloc((void **)&dG, std::max(1, nmats) * sizeof(double2), cs, "gf accumulator"));
+  // [0, nmats): G; with host_z, then the nmats frequencies
+  const size_t nz = host_z ? (size_t)nmats : 0;
+  ED_TRY(ed_dmalloc((void **)&dG, (std::max(1, nmats) + nz) * sizeof(double2), cs,
+                    "gf accumulator"));
   ed_status rs = ED_OK;
   if (cudaMemsetAsync(dG, 0, std::max(1, nmats) * sizeof(double2), cs) != cudaSuccess) rs = ED_ERR_CUDA;
+  const double2 *dz = nz ? dG + std::max(1, nmats) : nullptr;
+  if (rs == ED_OK && nz &&
+      cudaMemcpyAsync((void *)dz, host_z, nz * sizeof(double2), cudaMemcpyHostToDevice, cs) !=
+          cudaSuccess)
+    rs = ED_ERR_CUDA;
   double wp = 0, wh = 0;
   int sp = 0, sh = 0;
   for (int create = 1; create >= -1 && rs == ED_OK; create -= 2) {
@@ -407,13 +444,13 @@ ed_status ed_gf_impl(ed_sector s, ed_precision prec, const void *d_psi, double e
     int *k = create > 0 ? &sp : &sh;
     if (prec == ED_FP64)
       rs = one_chain<double, double>(s, (const double *)d_psi, orb, spin, create, nsteps, e0, beta,
-                                     nmats, dG, w, k, cs);
+                                     nmats, dG, w, k, cs, dz);
     else if (prec == ED_FP32)
       rs = one_chain<float, float>(s, (const float *)d_psi, orb, spin, create, nsteps, e0, beta,
-                                   nmats, dG, w, k, cs);
+                                   nmats, dG, w, k, cs, dz);
     else
       rs = one_chain<double, float>(s, (const double *)d_psi, orb, spin, create, nsteps, e0, beta,
-                                    nmats, dG, w, k, cs);
+                                    nmats, dG, w, k, cs, dz);
   }
   if (rs == ED_OK && nmats > 0) {
     cudaError_t e = cudaMemcpyAsync(host_G, dG, nmats * sizeof(double2), cudaMemcpyDeviceToHost, cs);
@@ -825,4 +862,15 @@ extern "C" ed_status ed_gf_lanczos(ed_sector s, ed_precision prec, const void *d
   if (prec != ED_FP64 && prec != ED_FP32 && prec != ED_FP32_POLISH) return ED_ERR_ARG;
   return ed_gf_impl(s, prec, d_psi, e0, orb, spin, nsteps, beta, nmats, host_G, info,
                     (cudaStream_t)stream);
+}
+
+extern "C" ed_status ed_gf_lanczos_z(ed_sector s, ed_precision prec, const void *d_psi, double e0,
+                                     int32_t orb, int32_t spin, int32_t nsteps,
+                                     const double *host_z, int32_t nz, double *host_G,
+                                     ed_gf_info *info, void *stream) {
+  if (prec != ED_FP64 && prec != ED_FP32 && prec != ED_FP32_POLISH) return ED_ERR_ARG;
+  if (nz < 0 || (nz > 0 && (!host_z || !host_G))) return ED_ERR_ARG;
+  static const double none[2] = {0.0, 0.0};
+  return ed_gf_impl(s, prec, d_psi, e0, orb, spin, nsteps, 0.0, nz, host_G, info,
+                    (cudaStream_t)stream, host_z ? host_z : none);
 }
