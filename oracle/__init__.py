@@ -10,7 +10,9 @@ Modules
 ``fock``      Fock basis of a sector (Sec. 2.3, Sec. 6.3), fermionic signs
               (Sec. 2.3), per-spin hopping matrices, the diagonal and the
               sector Hamiltonian split of Eq. Hdecomp / Eq. Hbuild (Sec. 2.4),
-              the factorised product of Sec. 3.2 without MPI.
+              the factorised product of Sec. 3.2 without MPI, and the
+              non-factorisable part H_nd of Eq. Ham1 (spin exchange J_X,
+              pair hopping J_P) applied term by term to every basis state.
 ``fullfock``  Independent checkers: the whole Fock space built from
               Jordan-Wigner operator matrices (Eq. Ham1, Ns <= 6) and a
               sector Hamiltonian built state by state with the full mode

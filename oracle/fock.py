@@ -163,12 +163,94 @@ def interaction_table(model) -> np.ndarray:
     return W
 
 
+def nondiagonal_terms(model):
+    """H_nd of Eq. Ham1 as (coefficient, operator string) pairs, the string
+    a list of (level, spin, create) read left to right as written:
+    spin exchange  -J_X d^+_{a up} d_{a dw} d^+_{b dw} d_{b up} and
+    pair hopping   +J_P d^+_{a up} d^+_{a dw} d_{b dw} d_{b up},
+    for every ordered pair of impurity orbitals a != b (Sec. 3.2: the part of
+    H that keeps N_up and N_dw but not the per-spin factorisation)."""
+    terms = []
+    for a in range(model.norb):
+        for b in range(model.norb):
+            if a == b:
+                continue
+            A, B = level_of_impurity(model, a), level_of_impurity(model, b)
+            if model.Jx != 0.0:
+                terms.append((-model.Jx, [(A, 0, 1), (A, 1, 0), (B, 1, 1), (B, 0, 0)]))
+            if model.Jp != 0.0:
+                terms.append((model.Jp, [(A, 0, 1), (A, 1, 1), (B, 1, 0), (B, 0, 0)]))
+    return terms
+
+
+def apply_operator_string(ns: int, I, ops):
+    """Apply an operator string (rightmost operator first) to full Fock
+    integers I = I_up + 2**Ns I_dw (an int64 array): mode of (level, spin) is
+    level + spin Ns, and each c or c^+ contributes (-1)**(occupied modes below
+    it) before it acts (Sec. 2.3).  Returns (sign, J): sign 0 where the
+    string annihilates the state."""
+    I = np.array(I, dtype=np.int64, copy=True)
+    sign = np.ones(I.shape, dtype=np.int64)
+    for (lev, spin, create) in reversed(ops):
+        m = lev + spin * ns
+        occ = (I >> m) & 1
+        sign[occ == create] = 0
+        below = np.zeros(I.shape, dtype=np.int64)
+        for k in range(m):
+            below += (I >> k) & 1
+        sign = np.where(below & 1, -sign, sign)
+        I = I ^ (np.int64(1) << m)
+    return sign, I
+
+
+def nondiagonal_matrix(model, map_up, map_dw) -> sp.csr_matrix:
+    """H_nd on the sector of the two maps, built by applying every term of
+    nondiagonal_terms to every basis state (column j = the image of state j)
+    and locating the image by binary search in the maps (Sec. 6.3)."""
+    ns = model.ns
+    du, dd = len(map_up), len(map_dw)
+    src = np.arange(du * dd, dtype=np.int64)
+    I = map_up[src % du].astype(np.int64) + (map_dw[src // du].astype(np.int64) << ns)
+    rows, cols, vals = [], [], []
+    for coef, ops in nondiagonal_terms(model):
+        sgn, J = apply_operator_string(ns, I, ops)
+        k = sgn != 0
+        Ju, Jd = J[k] & ((1 << ns) - 1), J[k] >> ns
+        iu, idw = np.searchsorted(map_up, Ju), np.searchsorted(map_dw, Jd)
+        assert np.all(map_up[iu] == Ju) and np.all(map_dw[idw] == Jd)
+        rows.append(idw * du + iu)
+        cols.append(src[k])
+        vals.append(coef * sgn[k])
+    n = du * dd
+    if not rows:
+        return sp.csr_matrix((n, n))
+    H = sp.csr_matrix((np.concatenate(vals).astype(np.float64),
+                       (np.concatenate(rows), np.concatenate(cols))), shape=(n, n))
+    H.sum_duplicates()
+    return H
+
+
+def nondiagonal_row(model, I_up: int, I_dw: int):
+    """The terms of H_nd applied to one basis state: [(element, J_up, J_dw)].
+    H_nd is real and symmetric (the adjoint of the (a, b) term of either kind
+    is the (b, a) term), so these are also the entries of the state's row:
+    (H_nd v)_i = sum of element * v_j over this list."""
+    ns = model.ns
+    out = []
+    I = np.array([int(I_up) + (int(I_dw) << ns)], dtype=np.int64)
+    for coef, ops in nondiagonal_terms(model):
+        sgn, J = apply_operator_string(ns, I, ops)
+        if sgn[0] != 0:
+            out.append((coef * int(sgn[0]), int(J[0]) & ((1 << ns) - 1), int(J[0]) >> ns))
+    return out
+
+
 class Sector:
-    """Per-spin pieces of the sector S[N_up, N_dw] (Sec. 2.2-2.4)."""
+    """Per-spin pieces of the sector S[N_up, N_dw] (Sec. 2.2-2.4), and the
+    non-factorisable part H_nd of Eq. Ham1 as an explicit sparse matrix when
+    J_X or J_P is non-zero."""
 
     def __init__(self, model, nup: int, ndw: int):
-        if model.Jx != 0.0 or model.Jp != 0.0:
-            raise ValueError("oracle covers the density-density interaction only")
         self.model = model
         self.nup, self.ndw = nup, ndw
         ns = model.ns
@@ -181,6 +263,9 @@ class Sector:
         self.E_up, self.m_up = spin_diagonal(model, 0, nup, self.map_up)
         self.E_dw, self.m_dw = spin_diagonal(model, 1, ndw, self.map_dw)
         self.W = interaction_table(model)
+        self.H_nd = None
+        if model.Jx != 0.0 or model.Jp != 0.0:
+            self.H_nd = nondiagonal_matrix(model, self.map_up, self.map_dw)
 
     def diagonal(self) -> np.ndarray:
         """H_d of Eq. Hdecomp as a [D_dw][D_up] array."""
@@ -188,14 +273,18 @@ class Sector:
                 + self.W[self.m_up[None, :], self.m_dw[:, None]])
 
     def matvec(self, v: np.ndarray) -> np.ndarray:
-        """w = H_d v + (H_up x 1) v + (1 x H_dw) v, the serial product of
-        Sec. 6.7 without MPI: the up part runs along each dw row (contiguous),
-        the dw part along the strided axis (Sec. 3.2)."""
+        """w = H_d v + (H_up x 1) v + (1 x H_dw) v + H_nd v, the serial
+        product of Sec. 6.7 without MPI: the up part runs along each dw row
+        (contiguous), the dw part along the strided axis, H_nd over the whole
+        sector (Sec. 3.2)."""
         V = v.reshape(self.dim_dw, self.dim_up)
         Wm = self.diagonal() * V
         Wm += (self.H_up @ V.T).T
         Wm += self.H_dw @ V
-        return Wm.reshape(-1)
+        w = Wm.reshape(-1)
+        if self.H_nd is not None:
+            w = w + self.H_nd @ v
+        return w
 
     def hamiltonian(self) -> sp.csr_matrix:
         """Explicit sparse sector matrix of Eq. Hbuild (small sectors)."""
@@ -203,6 +292,8 @@ class Sector:
         Id = sp.identity(self.dim_dw, format="csr")
         H = (sp.kron(Id, self.H_up) + sp.kron(self.H_dw, Iu)
              + sp.diags(self.diagonal().reshape(-1)))
+        if self.H_nd is not None:
+            H = H + self.H_nd
         return sp.csr_matrix(H)
 
 

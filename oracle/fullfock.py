@@ -3,10 +3,11 @@
 Neither function uses the per-spin factorisation or the helpers of
 ``oracle.fock``:
 
-* ``fock_space_hamiltonian`` builds Eq. Ham1 (J_X = J_P = 0) on the whole
-  Fock space from Jordan-Wigner matrices of the 2 Ns annihilation operators,
-  mode m = a for (a, up) and m = Ns + a for (a, down) (the order of Sec. 2.3);
-  only for Ns <= 6 (4**6 = 4096 states).
+* ``fock_space_hamiltonian`` builds Eq. Ham1 on the whole Fock space from
+  Jordan-Wigner matrices of the 2 Ns annihilation operators, mode m = a for
+  (a, up) and m = Ns + a for (a, down) (the order of Sec. 2.3), the spin
+  exchange and pair hopping as products of those matrices in the order
+  written; only for Ns <= 6 (4**6 = 4096 states).
 * ``sector_hamiltonian_statewise`` walks the sector states one by one,
   applies every term of Eq. Ham1 with the sign counted over all 2 Ns modes,
   and looks the result up in a dictionary (Ns <= 8).
@@ -74,6 +75,15 @@ def fock_space_hamiltonian(model):
         for a in range(model.norb):
             for b in range(a + 1, model.norb):
                 H = H + (model.Ust - model.Jh) * (n(mode(a, s)) @ n(mode(b, s)))
+    # -J_X d+_{a up} d_{a dw} d+_{b dw} d_{b up} + J_P d+_{a up} d+_{a dw} d_{b dw} d_{b up}
+    for a in range(model.norb):
+        for b in range(model.norb):
+            if a == b:
+                continue
+            au, ad = c[mode(_imp_level(model, a), 0)], c[mode(_imp_level(model, a), 1)]
+            bu, bd = c[mode(_imp_level(model, b), 0)], c[mode(_imp_level(model, b), 1)]
+            H = H - model.Jx * (au.T @ ad @ bd.T @ bu)
+            H = H + model.Jp * (au.T @ ad.T @ bd @ bu)
     return sp.csr_matrix(H)
 
 
@@ -129,6 +139,27 @@ def sector_hamiltonian_statewise(model, nup: int, ndw: int) -> sp.csr_matrix:
                             rows.append(where[I])
                             cols.append(j)
                             vals.append(sg * model.v_bath[s, a, nu])
+        # spin exchange and pair hopping: one operator at a time, right to left
+        for a in range(model.norb):
+            for b in range(model.norb):
+                if a == b:
+                    continue
+                for coef, ops in ((-model.Jx, ((a, 1), (a + ns, 0), (b + ns, 1), (b, 0))),
+                                  (model.Jp, ((a, 1), (a + ns, 1), (b + ns, 0), (b, 0)))):
+                    if coef == 0.0:
+                        continue
+                    I, sg = J, 1
+                    for (m, create) in reversed(ops):
+                        if occ(I, m) == create:
+                            sg = 0
+                            break
+                        if bin(I & ((1 << m) - 1)).count("1") % 2:
+                            sg = -sg
+                        I ^= 1 << m
+                    if sg:
+                        rows.append(where[I])
+                        cols.append(j)
+                        vals.append(sg * coef)
         for a in range(model.norb):
             diag += model.U * occ(J, a) * occ(J, a + ns)
             for b in range(model.norb):

@@ -12,13 +12,16 @@ Green's functions on the real axis, the impurity observables):
 * from the ground state psi of a sector (sector order, Eq. Vmatrix):
   densities <n_{alpha sigma}>, the density-density correlators
   <n_{alpha sigma} n_{beta sigma'}> (double occupancy d_alpha =
-  <n_{alpha up} n_{alpha dw}>) and the interaction energy <H_int> of Eq. Ham1
-  with J_X = J_P = 0:
+  <n_{alpha up} n_{alpha dw}>) and the interaction energy <H_int> of Eq. Ham1:
   U sum_alpha n_{a up} n_{a dw} + U' sum_{a != b} n_{a up} n_{b dw}
-  + (U' - J) sum_{a < b, sigma} n_{a sigma} n_{b sigma};
-* the Hartree (first-moment) limit of Sigma at large |z| for this
-  interaction: U <n_{a, -s}> + U' sum_{b != a} <n_{b, -s}>
-  + (U' - J) sum_{b != a} <n_{b, s}>.
+  + (U' - J) sum_{a < b, sigma} n_{a sigma} n_{b sigma}, plus <psi|H_nd|psi>
+  for the spin exchange and pair hopping (J_X, J_P);
+* the Hartree (first-moment) limit of Sigma at large |z|:
+  U <n_{a, -s}> + U' sum_{b != a} <n_{b, -s}> + (U' - J) sum_{b != a} <n_{b, s}>.
+  Reading: the spin exchange and pair hopping add nothing to the diagonal
+  first moment <{[c_{a s}, H], c^+_{a s}}>: a term that holds c^+_{a s}
+  leaves an odd operator without that mode, which anticommutes with
+  c^+_{a s}; a term that holds c_{a s} commutes to zero.
 """
 from __future__ import annotations
 
@@ -74,6 +77,9 @@ def local_observables(model, nup, ndw, psi):
                 e_int += model.Ust * nn[0, 1, a, b]
             if a < b:
                 e_int += (model.Ust - model.Jh) * (nn[0, 0, a, b] + nn[1, 1, a, b])
+    if s.H_nd is not None:
+        p = np.asarray(psi, dtype=np.float64)
+        e_int += float(p @ (s.H_nd @ p)) / float(p @ p)
     return dens, nn, float(e_int)
 
 

@@ -144,3 +144,85 @@ def test_wrong_sign_in_hybridisation_is_caught(monkeypatch):
     orig = observables.hybridisation
     monkeypatch.setattr(observables, "hybridisation", lambda mm, o, sp, zz: -orig(mm, o, sp, zz))
     assert np.abs(observables.self_energy(m0, 0, 0, z, G0)).max() > 1e-2
+
+
+# ------------------------------------------------ spin exchange and pair hopping
+
+def _atom_multiplet_error():
+    """Largest distance of the oracle's two- and three-electron spectra of a
+    three-orbital atom from the Kanamori multiplets U - 3J (9), U - J (5),
+    U + 2J (1) and 3U - 9J (4), 3U - 6J (10), 3U - 4J (6).  (The sign of
+    J_X shows only with three electrons: with two, U' + J_X and U' - J_X
+    merely trade eigenvectors.)"""
+    from workloads import ImpurityModel
+    U, J = 3.0, 0.55
+    m = ImpurityModel(norb=3, nbath=0, U=U, Ust=U - 2 * J, Jh=J, e_imp=np.zeros(3),
+                      e_bath=np.zeros((3, 0)), v_bath=np.zeros((3, 0)), Jx=J, Jp=J)
+    wants = {2: [(U - 3 * J, 9), (U - J, 5), (U + 2 * J, 1)],
+             3: [(3 * U - 9 * J, 4), (3 * U - 6 * J, 10), (3 * U - 4 * J, 6)]}
+    err = 0.0
+    for n, levels in wants.items():
+        ev = []
+        for nup in range(n + 1):
+            fock._SECTOR_CACHE.clear()
+            ev.extend(np.linalg.eigvalsh(fock.Sector(m, nup, n - nup).hamiltonian().toarray()))
+        want = np.sort(np.concatenate([np.full(c, e) for e, c in levels]))
+        err = max(err, np.abs(np.sort(ev) - want).max())
+    return err
+
+
+def _mutate_terms(monkeypatch, edit):
+    orig = fock.nondiagonal_terms
+    monkeypatch.setattr(fock, "nondiagonal_terms", lambda m: edit(m, orig(m)))
+
+
+def test_wrong_sign_of_spin_exchange_is_caught(monkeypatch):
+    assert _atom_multiplet_error() < 1e-12
+    _mutate_terms(monkeypatch, lambda m, ts: [(-c if o[1] == (o[0][0], 1, 0) else c, o)
+                                              for c, o in ts])
+    assert _atom_multiplet_error() > 1e-3
+
+
+def test_dropped_pair_hopping_is_caught(monkeypatch):
+    _mutate_terms(monkeypatch, lambda m, ts: [(c, o) for c, o in ts if o[1] != (o[0][0], 1, 1)])
+    assert _atom_multiplet_error() > 1e-3
+
+
+def test_swapped_pair_annihilators_are_caught(monkeypatch):
+    """d_{b up} d_{b dw} in place of d_{b dw} d_{b up}: the pair hopping
+    changes sign; the Jordan-Wigner blocks and the multiplets see it."""
+    from workloads import ImpurityModel
+    _mutate_terms(monkeypatch, lambda m, ts: [(c, o[:2] + [o[3], o[2]]) if o[1][2] == 1 else (c, o)
+                                              for c, o in ts])
+    assert _atom_multiplet_error() > 1e-3
+    b = make_model(2, 1, U=2.9, Jh=0.45, seed=72)
+    m = ImpurityModel(norb=2, nbath=1, U=b.U, Ust=b.Ust, Jh=b.Jh, e_imp=b.e_imp,
+                      e_bath=b.e_bath, v_bath=b.v_bath, Jx=0.35, Jp=0.27)
+    assert _jw_mismatch(m, 2, 2) > 1e-3
+
+
+def test_interaction_energy_without_nondiagonal_terms_is_caught(monkeypatch):
+    from oracle import observables
+    from workloads import ImpurityModel
+    b = make_model(2, 3, U=2.6, Jh=0.4, seed=64)
+    m = ImpurityModel(norb=2, nbath=3, U=b.U, Ust=b.Ust, Jh=b.Jh, e_imp=b.e_imp,
+                      e_bath=b.e_bath, v_bath=b.v_bath, Jx=0.45, Jp=0.35)
+    m0 = ImpurityModel(norb=2, nbath=3, U=0.0, Ust=0.0, Jh=0.0, e_imp=b.e_imp,
+                       e_bath=b.e_bath, v_bath=b.v_bath)
+    fock._SECTOR_CACHE.clear()
+    s = fock.Sector(m, 4, 3)
+    r = lanczos.ground_state(s.matvec, s.dim)
+    e_free = float(r["psi"] @ fock.Sector(m0, 4, 3).matvec(r["psi"]))
+
+    def gap():
+        return abs(r["e0"] - e_free - observables.local_observables(m, 4, 3, r["psi"])[2])
+    assert gap() < 1e-10
+    orig = observables.local_observables
+
+    def bad(model, nup, ndw, psi):
+        d, nn, e = orig(model, nup, ndw, psi)
+        sec = fock.get_sector(model, nup, ndw)
+        p = np.asarray(psi) / np.linalg.norm(psi)
+        return d, nn, e - float(p @ (sec.H_nd @ p))
+    monkeypatch.setattr(observables, "local_observables", bad)
+    assert gap() > 1e-3
