@@ -2,19 +2,22 @@
  * edgb.h — C ABI of the GB300 exact-diagonalisation hot path.
  *
  * The library computes, on one GPU, the Lanczos ground state and the impurity
- * Green's function of a density-density Anderson impurity model in one
+ * Green's function of a multi-orbital Anderson impurity model in one
  * (N_up, N_dw) Fock sector, following A. Amaricci et al., "EDIpack: a parallel
  * exact diagonalization package for quantum impurity problems":
  *
- *   - the model is Eq. Ham1 with J_X = J_P = 0, diagonal H^loc and bath h, and
- *     a "normal" bath (each impurity orbital has its own Nbath levels,
- *     Ns = Norb (Nbath + 1), Sec. 2.1 and Sec. 6.4);
+ *   - the model is Eq. Ham1 with diagonal H^loc and bath h and a "normal"
+ *     bath (each impurity orbital has its own Nbath levels,
+ *     Ns = Norb (Nbath + 1), Sec. 2.1 and Sec. 6.4); the interaction is the
+ *     density-density part (U, U', U' - J) plus, when J_X or J_P != 0, the
+ *     spin exchange and pair hopping H_nd;
  *   - the sector basis is the product of two ascending lists of Ns-bit strings
  *     with N_up and N_dw set bits (Sec. 2.3, Sec. 6.3);
  *   - the sector Hamiltonian has the split H = H_d + H_up x 1 + 1 x H_dw of
  *     Eq. Hdecomp with the matrix elements of Eq. Hbuild (Sec. 2.4);
  *   - the product w = H v is the serial form of Sec. 6.7 (diagonal, up part
- *     along contiguous rows, down part along the strided axis, Sec. 3.2);
+ *     along contiguous rows, down part along the strided axis, Sec. 3.2),
+ *     plus H_nd v over the whole sector when J_X or J_P != 0 (Sec. 3.2);
  *   - the ground state comes from plain Lanczos without re-orthogonalisation
  *     (Sec. 6.6); G(i w_n) from Lanczos chains and continued fractions
  *     (Sec. 6.8, Eq. KLgf).
@@ -62,7 +65,7 @@ typedef enum {
   ED_OK = 0,
   ED_PENDING = 1,            /* ed_poll: request not finished yet            */
   ED_ERR_ARG = -1,           /* invalid argument (NULL, out of range, size)  */
-  ED_ERR_UNSUPPORTED = -2,   /* J_X or J_P != 0, Ns or Norb above the limits */
+  ED_ERR_UNSUPPORTED = -2,   /* Ns or Norb above the limits                  */
   ED_ERR_OOM = -3,           /* device allocation failed                     */
   ED_ERR_CUDA = -4,          /* a CUDA runtime call failed                   */
   ED_ERR_TIMEOUT = -5,       /* a bounded wait ran out                       */
@@ -78,14 +81,17 @@ typedef enum {
                          ground state (energy and vector reported in FP64)       */
 } ed_precision;
 
-/* Model parameters, Eq. Ham1 with J_X = J_P = 0 (host arrays, copied). */
+/* Model parameters of Eq. Ham1 (host arrays, copied). */
 typedef struct {
   int32_t norb;            /* impurity orbitals, 1..ED_MAX_NORB              */
   int32_t nbath;           /* bath levels per orbital, >= 0                  */
   double U;                /* intra-orbital U                                */
   double Ust;              /* inter-orbital opposite-spin U'                 */
   double Jh;               /* Hund J: same-spin inter-orbital term is U'-J   */
-  double Jx, Jp;           /* spin exchange / pair hopping: must be 0        */
+  double Jx, Jp;           /* spin exchange J_X, pair hopping J_P: the terms
+                              -J_X d+_{a up} d_{a dw} d+_{b dw} d_{b up} and
+                              +J_P d+_{a up} d+_{a dw} d_{b dw} d_{b up},
+                              a != b impurity orbitals (0: term absent)      */
   const double *e_imp;     /* [2][norb]        impurity levels (H^loc diag)  */
   const double *e_bath;    /* [2][norb][nbath] bath energies                 */
   const double *v_bath;    /* [2][norb][nbath] hybridisations V^nu_{alpha s} */
@@ -108,9 +114,14 @@ typedef struct {
  * order as the paper's scan + binary search), and builds the per-spin CSR
  * hopping matrices (columns sorted, FP64 and FP32 values) and the diagonal
  * tables: E_sigma[i] (one-body energies + (U'-J) same-spin pairs) and
- * W[m_up][m_dw] (U and U' terms over impurity occupation masks).
+ * W[m_up][m_dw] (U and U' terms over impurity occupation masks).  With
+ * J_X or J_P != 0 it also tabulates, per spin and vector layout, the string
+ * reached by moving one electron between two impurity orbitals (its index
+ * and the sign of the move), Norb^2 int32 entries per string: the product
+ * then adds H_nd v with one gather kernel (every entry point that applies H,
+ * the GF chains and the interaction energy of ed_observables included).
  * Returns ED_ERR_ARG for nup/ndw outside 0..Ns, ED_ERR_UNSUPPORTED for
- * Jx/Jp != 0 or Ns > ED_MAX_NS.  Synchronises `stream`. */
+ * Norb > ED_MAX_NORB or Ns > ED_MAX_NS.  Synchronises `stream`. */
 ed_status ed_sector_build(const ed_model *model, int32_t nup, int32_t ndw,
                           void *stream, ed_sector *out);
 ed_status ed_sector_get_info(ed_sector s, ed_sector_info *out);
@@ -298,6 +309,8 @@ ed_status ed_sigma(const ed_model *model, int32_t orb, int32_t spin, const doubl
  *                     double occupancy of orbital a is nn[0][1][a][a])
  *   e_int             <H_int> = U sum_a nn[0][1][a][a] + U' sum_{a!=b} nn[0][1][a][b]
  *                     + (U' - J) sum_{a<b} (nn[0][0][a][b] + nn[1][1][a][b])
+ *                     + <psi|H_nd|psi> / <psi, psi> (spin exchange and pair
+ *                     hopping; summed in FP32 for ED_FP32 vectors)
  *   norm              <psi, psi> before normalisation.
  * ED_ERR_ARG when n != D.  Synchronises `stream`. */
 ed_status ed_observables(ed_sector s, ed_precision prec, const void *d_psi, int64_t n,

@@ -266,6 +266,8 @@ __global__ void __launch_bounds__(CHAIN_THREADS) k_chain_batch(const ChainTask<T
         const int32_t d0 = __ldg(tb.rp_dw + r), d1 = __ldg(tb.rp_dw + r + 1);
         for (int32_t k = d0; k < d1; ++k)
           acc = ch_fma<To>(__ldg(tb.val_dw + k), S[(int64_t)__ldg(tb.col_dw + k) * stride + pc], acc);
+        if (tb.nd_up)  // spin exchange and pair hopping
+          acc += ed_nd_terms<To>(tb, S, stride, r, pc, (int)tb.m_up[ci.x], (int)tb.m_dw[r]);
         const To v = x * s_cur;
         To w1 = acc * s_cur;
         if (j > 0) w1 = ch_fma<To>(-bj, prev[i] * s_prev, w1);

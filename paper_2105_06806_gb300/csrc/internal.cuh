@@ -70,6 +70,7 @@ struct ModelParams {
   double V[2][ED_MAX_NS];     // V of the bath level (0 for impurity levels)
   int orb_of_level[ED_MAX_NS];  // orbital alpha owning the level
   double U, Ust, Jh;
+  double Jx, Jp;              // spin exchange, pair hopping (H_nd of Eq. Ham1)
 };
 
 // Per-spin basis and hopping tables of a sector (device pointers).
@@ -137,6 +138,22 @@ struct ItemList {
   int64_t nditems = 0;
 };
 
+struct LanczosState;
+
+// Move tables of the spin-exchange and pair-hopping terms (H_nd of Eq. Ham1)
+// in one vector layout.  Both terms move one electron of each spin between
+// two impurity orbitals, and each factorises into a move on the up string
+// times a move on the dw string (the two N_up-dependent signs of the dw
+// operators cancel): entry k = from * Norb + to of index i is the layout
+// index of the string with the electron moved, shifted left by one, with
+// bit 0 the sign (-1)^(occupied impurity levels strictly between), or -1
+// where the move does not apply (and on padding columns).
+struct NdTables {
+  int32_t *up = nullptr;   // [Norb^2][ncols]
+  int32_t *dw = nullptr;   // [Norb^2][D_dw]
+  int64_t ncols = 0;       // columns of the layout (padded in block-major)
+};
+
 struct ed_sector_s {
   ModelParams mp;
   std::vector<double> e_imp, e_bath, v_bath;  // host copies (for neighbours)
@@ -169,6 +186,7 @@ struct ed_sector_s {
   int8_t hv_kernel[2] = {-1, -1};
   bool hv_pinned[2] = {false, false};
   double tune_ms[2][2] = {{-1.0, -1.0}, {-1.0, -1.0}};  // [precision][tiled, element-parallel]
+  NdTables nd[2];          // [layout]; empty when J_X = J_P = 0
   double *W = nullptr;     // [2^norb][2^norb]
   float *W32 = nullptr;
   ed_sector nb[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};  // [spin][0:c,1:c+]
@@ -287,7 +305,61 @@ struct HvTables {
   int64_t small_grid;      // its CTAs (= block partials of the Lanczos mode)
   int32_t small_chunk;     // its elements per thread
   bool passa_wide;         // two-pass product: the wide shape of the H_up pass
+  // H_nd (spin exchange, pair hopping): move tables of this layout, or null
+  const int32_t *nd_up = nullptr, *nd_dw = nullptr;
+  int64_t nd_ncols = 0;
+  int nd_norb = 0;
+  T nd_jx = T(0), nd_jp = T(0);
 };
+
+// Sum of the H_nd terms of Eq. Ham1 for the basis state of row r (impurity
+// mask md) and column c (mask mu) of a layout: every up move b -> a (b
+// occupied, a empty in mu) pairs with the dw move a -> b (spin exchange,
+// +J_X: -J_X d+_{a up} d_{a dw} d+_{b dw} d_{b up} = +J_X (d+_{a up} d_{b up})
+// (d+_{b dw} d_{a dw})) or b -> a (pair hopping, +J_P), whichever md allows.
+// H_nd is real symmetric, so the terms applied to the output state give its
+// row.  v is read at [row * stride + column] of the moved strings.
+template <typename T>
+__device__ __forceinline__ T ed_nd_terms(const HvTables<T> &tb, const T *v, int64_t stride,
+                                         int64_t r, int64_t c, int mu, int md) {
+  T acc = T(0);
+  const int no = tb.nd_norb;
+  for (int b = 0; b < no; ++b) {
+    if (!((mu >> b) & 1)) continue;
+    for (int a = 0; a < no; ++a) {
+      if ((mu >> a) & 1) continue;
+      int kd;
+      T cf;
+      if (((md >> a) & 1) && !((md >> b) & 1)) {
+        kd = a * no + b;
+        cf = tb.nd_jx;
+      } else if (((md >> b) & 1) && !((md >> a) & 1)) {
+        kd = b * no + a;
+        cf = tb.nd_jp;
+      } else {
+        continue;
+      }
+      if (cf == T(0)) continue;
+      const int32_t eu = __ldg(tb.nd_up + (int64_t)(b * no + a) * tb.nd_ncols + c);
+      const int32_t ed = __ldg(tb.nd_dw + (int64_t)kd * tb.ddw + r);
+      const T x = v[(int64_t)(ed >> 1) * stride + (eu >> 1)];
+      acc += ((eu ^ ed) & 1) ? -cf * x : cf * x;
+    }
+  }
+  return acc;
+}
+
+ed_status ed_build_nd_tables(ed_sector s, cudaStream_t st);
+void ed_free_nd_tables(ed_sector s, cudaStream_t st);
+// CTAs (= partial sums of the Lanczos and dot modes) of the H_nd kernel
+int64_t ed_nd_grid(int64_t ddw);
+// Adds the H_nd terms after the factorised product (modes of k_hv; ND_DOT:
+// part[cta] = sum_i v_i (H_nd v)_i, nothing written).
+enum { ND_DOT = 3 };
+template <typename T>
+ed_status ed_launch_nd(const HvTables<T> &tb, int mode, const T *v, T *w, T *const *bufs,
+                       T *const *basis, const struct LanczosState *state, double *part,
+                       cudaStream_t st);
 // layout 0: sector (paper) order; 1: block-major order
 template <typename T>
 HvTables<T> ed_hv_tables(ed_sector s, int layout);

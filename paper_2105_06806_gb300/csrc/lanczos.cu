@@ -841,8 +841,9 @@ static ed_status run_steps(ed_sector s, const HvTables<T> &tb, T *const *bufs, L
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   ED_TRY(ed_hv_prepare<T>());
-  // product kernels per step: two for the two-pass product, else one
-  const int64_t hv_per_step = (tb.ditems && !tb.small_cols) ? 2 : 1;
+  // product kernels per step: two for the two-pass product, else one; plus
+  // the H_nd kernel with spin exchange or pair hopping
+  const int64_t hv_per_step = ((tb.ditems && !tb.small_cols) ? 2 : 1) + (tb.nd_up ? 1 : 0);
   ED_TRY_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
   ed_status rs = ED_OK;
   for (int it = 0; it < chunk && rs == ED_OK; ++it) {

@@ -195,6 +195,17 @@ static void fill_tables(HvTables<T> &t, const SpinTables &u, const SpinTables &d
   t.nmask = 1 << norb;
 }
 
+template <typename T>
+static void set_nd(HvTables<T> &t, ed_sector s, int layout) {
+  const NdTables &nd = s->nd[layout];
+  t.nd_up = nd.up;
+  t.nd_dw = nd.dw;
+  t.nd_ncols = nd.ncols;
+  t.nd_norb = s->mp.norb;
+  t.nd_jx = (T)s->mp.Jx;
+  t.nd_jp = (T)s->mp.Jp;
+}
+
 template <>
 HvTables<double> ed_hv_tables<double>(ed_sector s, int layout) {
   HvTables<double> t;
@@ -214,6 +225,7 @@ HvTables<double> ed_hv_tables<double>(ed_sector s, int layout) {
   t.small_grid = t.small_cols ? small_grid_of(s->bdim) : 0;
   t.small_chunk = (int32_t)small_chunk_of(s->bdim);
   t.passa_wide = layout == 1 && passa_is_wide(s);
+  set_nd<double>(t, s, layout);
   return t;
 }
 template <>
@@ -235,6 +247,7 @@ HvTables<float> ed_hv_tables<float>(ed_sector s, int layout) {
   t.small_grid = t.small_cols ? small_grid_of(s->bdim) : 0;
   t.small_chunk = (int32_t)small_chunk_of(s->bdim);
   t.passa_wide = layout == 1 && passa_is_wide(s);
+  set_nd<float>(t, s, layout);
   return t;
 }
 
@@ -1330,9 +1343,11 @@ __global__ void __launch_bounds__(HVS_THREADS) k_hv_small(HvLaunch<T> a) {
 
 int64_t ed_hv_num_parts(ed_sector s, int layout, int elem_size) {
   if (ed_build_items(s, layout, elem_size) != ED_OK) return 0;
-  if (layout == 1 && s->hv_kernel[elem_size == 8 ? 1 : 0] == 1) return small_grid_of(s->bdim);
+  // the H_nd kernel's partials follow the product's
+  const int64_t nd = s->nd[layout].up ? ed_nd_grid(s->sp[1].dim) : 0;
+  if (layout == 1 && s->hv_kernel[elem_size == 8 ? 1 : 0] == 1) return small_grid_of(s->bdim) + nd;
   const ItemList &il = s->items[layout][elem_size == 8 ? 1 : 0];
-  return il.d_ditems ? il.nditems : il.nitems;
+  return (il.d_ditems ? il.nditems : il.nitems) + nd;
 }
 
 // Opt the product kernels into large dynamic shared memory, once per device
@@ -1424,9 +1439,14 @@ ed_status ed_launch_hv(ed_sector s, const HvTables<T> &tb, int mode, const T *v,
   a.psi = psi;
   a.st = state;
   a.part = part;
-  if (mode == HV_PLAIN) return launch_mode<T, HV_PLAIN>(a, st);
-  if (mode == HV_LANCZOS) return launch_mode<T, HV_LANCZOS>(a, st);
-  return launch_mode<T, HV_SECOND>(a, st);
+  if (mode == HV_PLAIN) ED_TRY((launch_mode<T, HV_PLAIN>(a, st)));
+  else if (mode == HV_LANCZOS) ED_TRY((launch_mode<T, HV_LANCZOS>(a, st)));
+  else ED_TRY((launch_mode<T, HV_SECOND>(a, st)));
+  if (!tb.nd_up) return ED_OK;
+  // spin exchange and pair hopping, added to the product (partials after the product's)
+  const int64_t np = tb.small_cols ? tb.small_grid : (tb.ditems ? tb.nditems : tb.nitems);
+  if (nparts) *nparts = np + ed_nd_grid(tb.ddw);
+  return ed_launch_nd<T>(tb, mode, v, w, bufs, basis, state, part ? part + np : nullptr, st);
 }
 
 template ed_status ed_launch_hv<float>(ed_sector, const HvTables<float> &, int, const float *,

@@ -175,10 +175,19 @@ extern "C" ed_status ed_residual_noalloc(ed_sector s, const double *d_psi, int64
   tb.m_dw = s->sp[1].imask;
   tb.W = s->W;
   tb.nmask = 1 << s->mp.norb;
+  // spin exchange and pair hopping (sector order), added after the product
+  tb.stride = s->sp[0].dim;
+  tb.nd_up = s->nd[0].up;
+  tb.nd_dw = s->nd[0].dw;
+  tb.nd_ncols = s->nd[0].ncols;
+  tb.nd_norb = s->mp.norb;
+  tb.nd_jx = s->mp.Jx;
+  tb.nd_jp = s->mp.Jp;
 
   const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(NA_PARTS, (n + NA_THREADS - 1) / NA_THREADS));
   k_na_product<<<grid, NA_THREADS, 0, cs>>>(tb, d_psi, w, n);
   ED_LAUNCHED(1);
+  ED_TRY(ed_launch_nd<double>(tb, HV_PLAIN, d_psi, w, nullptr, nullptr, nullptr, nullptr, cs));
   k_na_rq_parts<<<grid, NA_THREADS, 0, cs>>>(d_psi, w, n, parts);
   ED_LAUNCHED(1);
   k_na_rq_final<<<1, 32, 0, cs>>>(parts, grid, res);

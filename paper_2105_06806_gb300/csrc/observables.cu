@@ -10,7 +10,8 @@
 // ed_observables: every density-density observable of the impurity depends
 // on a basis state only through its impurity occupation masks (m_up, m_dw),
 // so they all follow from the table P[m_up][m_dw] = sum of |psi_i|^2 over
-// the states with those masks.  The table is formed in a fixed order (no
+// the states with those masks.  The spin exchange and pair hopping add
+// <psi|H_nd|psi> to the interaction energy (the H_nd kernel's dot mode).  The table is formed in a fixed order (no
 // atomics): one warp per dw row sums |psi|^2 over the row's columns per up
 // mask (lanes in a fixed stride, a fixed shuffle tree), then one thread per
 // mask pair sums the rows in row order.  One thread then forms the
@@ -80,9 +81,10 @@ __global__ void k_mask_pairs(const double *S, const uint8_t *m_dw, int64_t ddw, 
   P[t] = acc;
 }
 
-// out: dens[2][norb], nn[2][2][norb][norb], e_int, norm (normalised by norm)
+// out: dens[2][norb], nn[2][2][norb][norb], e_int, norm (normalised by norm);
+// nd: nnd partial sums of <psi|H_nd|psi> (spin exchange, pair hopping)
 __global__ void k_observables(const double *P, int norb, double U, double Ust, double Jh,
-                              double *out) {
+                              const double *nd, int nnd, double *out) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   const int nm = 1 << norb;
   double norm = 0.0;
@@ -114,6 +116,9 @@ __global__ void k_observables(const double *P, int norb, double U, double Ust, d
                                nn[((1 * 2 + 1) * norb + a) * norb + b]);
     }
   }
+  double e_nd = 0.0;
+  for (int k = 0; k < nnd; ++k) e_nd += nd[k];
+  e_int += e_nd * inv;
   out[2 * norb + 4 * norb * norb] = e_int;
   out[2 * norb + 4 * norb * norb + 1] = norm;
 }
@@ -176,12 +181,23 @@ extern "C" ed_status ed_observables(ed_sector s, ed_precision prec, const void *
   const int nout = 2 * norb + 4 * norb * norb + 2;
   const size_t sb = ((size_t)ddw * nm * sizeof(double) + 255) & ~(size_t)255;
   const size_t pb = ((size_t)nm * nm * sizeof(double) + 255) & ~(size_t)255;
+  const int nnd = (s->nd[0].up && ddw > 0 && dup > 0) ? (int)ed_nd_grid(ddw) : 0;
+  const size_t ndb = ((size_t)std::max(nnd, 1) * sizeof(double) + 255) & ~(size_t)255;
   void *mem = nullptr;
-  ED_TRY(ed_dmalloc(&mem, sb + pb + nout * sizeof(double), cs, "observables"));
-  double *S = (double *)mem, *P = (double *)((char *)mem + sb), *dout = (double *)((char *)mem + sb + pb);
+  ED_TRY(ed_dmalloc(&mem, sb + pb + ndb + nout * sizeof(double), cs, "observables"));
+  double *S = (double *)mem, *P = (double *)((char *)mem + sb);
+  double *ndp = (double *)((char *)mem + sb + pb), *dout = (double *)((char *)mem + sb + pb + ndb);
   ed_status rs = ED_OK;
+  if (nnd > 0) {  // <psi|H_nd|psi>, one partial per CTA
+    rs = prec == ED_FP32
+             ? ed_launch_nd<float>(ed_hv_tables<float>(s, 0), ND_DOT, (const float *)d_psi,
+                                   nullptr, nullptr, nullptr, nullptr, ndp, cs)
+             : ed_launch_nd<double>(ed_hv_tables<double>(s, 0), ND_DOT, (const double *)d_psi,
+                                    nullptr, nullptr, nullptr, nullptr, ndp, cs);
+  }
   const unsigned rows_grid = (unsigned)((ddw + OB_WARPS - 1) / OB_WARPS);
-  if (ddw > 0 && dup > 0) {
+  if (rs != ED_OK) {
+  } else if (ddw > 0 && dup > 0) {
     if (prec == ED_FP32)
       k_mask_rows<float><<<rows_grid, 32 * OB_WARPS, 0, cs>>>((const float *)d_psi, dup, ddw,
                                                               s->sp[0].imask, nm, S);
@@ -195,7 +211,7 @@ extern "C" ed_status ed_observables(ed_sector s, ed_precision prec, const void *
     rs = ED_ERR_CUDA;
   }
   if (rs == ED_OK) {
-    k_observables<<<1, 32, 0, cs>>>(P, norb, s->U, s->Ust, s->Jh, dout);
+    k_observables<<<1, 32, 0, cs>>>(P, norb, s->U, s->Ust, s->Jh, ndp, nnd, dout);
     ed_count_launches(1);
     if (cudaGetLastError() != cudaSuccess) rs = ED_ERR_CUDA;
   }

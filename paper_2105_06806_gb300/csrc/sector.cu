@@ -26,16 +26,14 @@ ModelParams ed_model_params(const ed_model *m, ed_status *st) {
     *st = ED_ERR_UNSUPPORTED;
     return mp;
   }
-  if (m->Jx != 0.0 || m->Jp != 0.0) {
-    *st = ED_ERR_UNSUPPORTED;
-    return mp;
-  }
   mp.norb = m->norb;
   mp.nbath = m->nbath;
   mp.ns = m->norb * (m->nbath + 1);
   mp.U = m->U;
   mp.Ust = m->Ust;
   mp.Jh = m->Jh;
+  mp.Jx = m->Jx;
+  mp.Jp = m->Jp;
   for (int s = 0; s < 2; ++s) {
     for (int a = 0; a < m->norb; ++a) {
       mp.eps[s][a] = m->e_imp[s * m->norb + a];
@@ -355,6 +353,8 @@ ed_status ed_build_sector_impl(const ModelParams &mp, double U, double Ust, doub
     ED_TRY_CUDA(cudaMemcpyAsync(s->colpos, colpos.data(), colpos.size() * 4, cudaMemcpyHostToDevice, st));
     ED_TRY_CUDA(cudaMemcpyAsync(s->padinv, padinv.data(), padinv.size() * 4, cudaMemcpyHostToDevice, st));
   }
+  // spin exchange and pair hopping (J_X, J_P != 0): move tables of both layouts
+  ED_TRY(ed_build_nd_tables(s, st));
   int nm = 1 << mp.norb;
   ED_TRY(dalloc(s, st, &s->W, nm * nm));
   ED_TRY(dalloc(s, st, &s->W32, nm * nm));
@@ -408,6 +408,7 @@ static void sector_destroy(ed_sector s, cudaStream_t st) {
   ed_dfree(s->small_cols, st);
   ed_dfree(s->W, st);
   ed_dfree(s->W32, st);
+  ed_free_nd_tables(s, st);
   delete s;
 }
 

@@ -94,7 +94,9 @@ def test_invalid_arguments(ed):
         ed.Sector(m, 5, 1)
     assert e.value.status == ed.ED_ERR_ARG
     m2 = make_model(1, 3, U=1.0, seed=1)
-    m2.Jx = 0.1
+    m2.Jx = 0.1   # one orbital: no spin exchange term, the sector builds
+    ed.Sector(m2, 2, 2).free()
+    m3 = make_model(6, 1, U=1.0, seed=1)   # Norb above ED_MAX_NORB
     with pytest.raises(ed.EDError) as e:
-        ed.Sector(m2, 2, 2)
+        ed.Sector(m3, 2, 2)
     assert e.value.status == ed.ED_ERR_UNSUPPORTED

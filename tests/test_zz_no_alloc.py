@@ -11,7 +11,7 @@ import numpy as np
 import pytest
 import torch
 
-from workloads import make_model, workload_ns8
+from workloads import make_model, with_exchange, workload_ns8
 
 def _reference(ed, s, psi):
     """E and ||H psi - E psi|| / ||psi|| through ed_matvec (allocating path)."""
@@ -24,12 +24,14 @@ def _reference(ed, s, psi):
 
 
 @pytest.mark.gpu
-@pytest.mark.parametrize("case", ["ns8", "norb2_ns10"])
+@pytest.mark.parametrize("case", ["ns8", "norb2_ns10", "kanamori_norb3_ns9"])
 def test_noalloc_matches_allocating_entry_points(ed, case):
     if case == "ns8":
         m, nup, ndw = workload_ns8().model, 4, 4
-    else:
+    elif case == "norb2_ns10":
         m, nup, ndw = make_model(2, 4, U=3.0, Jh=0.5, seed=6), 5, 5
+    else:   # spin exchange and pair hopping
+        m, nup, ndw = with_exchange(make_model(3, 2, U=2.6, Jh=0.4, seed=31), 0.35, 0.3), 4, 5
     s = ed.Sector(m, nup, ndw)
     assert s.dim <= 1 << 20
     psi = torch.empty(s.dim, dtype=torch.float64, device="cuda")

@@ -203,6 +203,45 @@ def workload_ns18(seed: int = 0) -> Workload:
                     description=f"Norb=3 Nbath=5 Ns=18 sector (9,9) D=2363904400 U=2.5 J=0.4 seed={seed}")
 
 
+def with_exchange(model: ImpurityModel, Jx=None, Jp=None, name=None) -> ImpurityModel:
+    """The same model with the spin-exchange and pair-hopping couplings of
+    Eq. Ham1 switched on (default J_X = J_P = J: with U' = U - 2J the fully
+    rotation-invariant Kanamori interaction)."""
+    return ImpurityModel(norb=model.norb, nbath=model.nbath, U=model.U, Ust=model.Ust,
+                         Jh=model.Jh, e_imp=model.e_imp, e_bath=model.e_bath,
+                         v_bath=model.v_bath, Jx=model.Jh if Jx is None else Jx,
+                         Jp=model.Jh if Jp is None else Jp,
+                         name=(model.name + "_full") if name is None else name)
+
+
+def workload_full_norb3_ns15(seed: int = 0) -> Workload:
+    """Full Kanamori AIM (spin exchange and pair hopping, J_X = J_P = J,
+    U' = U - 2J), three orbitals, Nbath=4 per orbital (Ns=15), sector (8,7),
+    D=41,409,225; U=3, J=0.5.  The three-orbital system of the paper's
+    density-density vs full Kanamori comparison (Ns = 15)."""
+    e, v = random_bath(3, 4, seed)
+    m = make_model(3, 4, U=3.0, Jh=0.5, e_bath=e, v_bath=v, name="kanamori3_ns15")
+    return Workload("full_kanamori_norb3_ns15_n8_7", with_exchange(m), 8, 7,
+                    description=f"Norb=3 Nbath=4 Ns=15 sector (8,7) D=41409225 U=3 J=JX=JP=0.5 seed={seed}")
+
+
+def workload_full_norb5_ns15(seed: int = 0) -> Workload:
+    """Full Kanamori AIM, five orbitals, Nbath=2 per orbital (Ns=15), sector
+    (8,7), D=41,409,225; U=3, J=0.5, J_X = J_P = J, U' = U - 2J."""
+    e, v = random_bath(5, 2, seed)
+    m = make_model(5, 2, U=3.0, Jh=0.5, e_bath=e, v_bath=v, name="kanamori5_ns15")
+    return Workload("full_kanamori_norb5_ns15_n8_7", with_exchange(m), 8, 7,
+                    description=f"Norb=5 Nbath=2 Ns=15 sector (8,7) D=41409225 U=3 J=JX=JP=0.5 seed={seed}")
+
+
+def workload_full_ns18(seed: int = 0) -> Workload:
+    """The three-orbital Ns=18 half-filled workload with the spin exchange and
+    pair hopping switched on (J_X = J_P = J = 0.4)."""
+    w = workload_ns18(seed)
+    return Workload("full_kanamori_norb3_ns18_n9_9", with_exchange(w.model), 9, 9, gf_steps=0,
+                    description=w.description.replace("J=0.4", "J=JX=JP=0.4"))
+
+
 # Valid (norb, ns) pairs for the serving stream: ns must be a multiple of
 # norb (Ns = Norb (Nbath+1)), ns in {8,...,16}, norb in {1,2,3}.
 SERVING_PAIRS = [(no, ns) for no in (1, 2, 3) for ns in (8, 10, 12, 14, 16)
@@ -248,4 +287,7 @@ WORKLOADS = {
     "ns14": workload_ns14,
     "ns16": workload_ns16,
     "ns18": workload_ns18,
+    "full3_ns15": workload_full_norb3_ns15,
+    "full5_ns15": workload_full_norb5_ns15,
+    "full_ns18": workload_full_ns18,
 }
