@@ -299,6 +299,9 @@ def run_ours(args):
             "product": {**mv16, "frac": round(8.0 * w16.dim / (mv16["blocked_fp32_ms"] / 1e3)
                                               / 1e9 / hbm, 4)}}
 
+    if rank == 0 and args.full_kanamori:
+        subs["full_kanamori"] = run_full_kanamori(E, stream, dev, hbm)
+
     # plain FP64 GPU Lanczos against FP32 + FP64 polish, ground state only,
     # time to solution at the same 1e-10 accuracy target
     cmp = None
@@ -342,7 +345,8 @@ def run_ours(args):
             serving["full_ns16"] = run_serving(E, 96, 16, 0.0, "fp32_polish")
 
     cpu = None
-    if rank == 0 and args.cpu_baseline:
+    if rank == 0 and args.cpu_baseline and not (m.Jx or m.Jp):
+        # (the parallel oracle product covers the factorised part only)
         cpu = cpu_baseline(wl, args.cpu_steps)
 
     value, iters_s, t_max = combine_ranks(dist, tot["bytes"], tot["it"], t_s)
@@ -409,6 +413,71 @@ def time_products(E, wl, stream, dev, reps=20, which=("blocked_fp32",), kernel=N
         del v, w
     out["kernel_choice"] = s.blocked_kernel("fp32")
     s.free()
+    return out
+
+
+def _nd_alg_bytes(m, nup, ndw, elem):
+    """Algorithmic bytes of one H_nd launch: every element with at least one
+    spin-exchange or pair-hopping term is read and written once, and every
+    term reads one element of v (counted from the impurity masks)."""
+    no, ns = m.norb, m.ns
+
+    def per_mask(n):
+        return [math.comb(ns - no, n - bin(mu).count("1"))
+                if 0 <= n - bin(mu).count("1") <= ns - no else 0 for mu in range(1 << no)]
+    cu, cd = per_mask(nup), per_mask(ndw)
+    touched = terms = 0
+    for mu in range(1 << no):
+        for md in range(1 << no):
+            t = 0
+            for b in range(no):
+                for a in range(no):
+                    if a == b or not (mu >> b) & 1 or (mu >> a) & 1:
+                        continue
+                    t += bool(m.Jx) and bool((md >> a) & 1) and not (md >> b) & 1
+                    t += bool(m.Jp) and bool((md >> b) & 1) and not (md >> a) & 1
+            terms += t * cu[mu] * cd[md]
+            touched += (t > 0) * cu[mu] * cd[md]
+    return elem * (2 * touched + terms)
+
+
+def run_full_kanamori(E, stream, dev, hbm):
+    """Spin exchange and pair hopping (H_nd of Eq. Ham1): the FP32 product and
+    the FP32 + polish ground state of the Ns = 15 three- and five-orbital
+    full-Kanamori sectors against the same models without H_nd; the H_nd
+    kernel's time is the difference of the two products."""
+    import torch
+    import workloads
+    out = {}
+    for name in ("full3_ns15", "full5_ns15"):
+        wl = _workload(name)
+        m = wl.model
+        dd = workloads.Workload(wl.name + "_dd", workloads.ImpurityModel(
+            norb=m.norb, nbath=m.nbath, U=m.U, Ust=m.Ust, Jh=m.Jh, e_imp=m.e_imp,
+            e_bath=m.e_bath, v_bath=m.v_bath), wl.nup, wl.ndw)
+        rec = {"dim": wl.dim, "Jx": m.Jx, "Jp": m.Jp}
+        for tag, w in (("full", wl), ("dd", dd)):
+            rec[f"product_fp32_ms_{tag}"] = time_products(E, w, stream, dev, reps=20)["blocked_fp32_ms"]
+            s = E.Sector(w.model, w.nup, w.ndw, stream=stream)
+            best = None
+            for _ in range(2):
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                r = E.lanczos_ground(s, "fp32_polish", want_vector=False, stream=stream)
+                torch.cuda.synchronize()
+                dt = time.perf_counter() - t0
+                best = dt if best is None else min(best, dt)
+            s.free()
+            rec[f"ground_fp32_polish_s_{tag}"] = round(best, 4)
+            rec[f"e0_{tag}"] = r["e0"]
+            rec[f"iterations_{tag}"] = r["iterations"] + r["polish_iterations"]
+        nd_ms = rec["product_fp32_ms_full"] - rec["product_fp32_ms_dd"]
+        alg = _nd_alg_bytes(m, wl.nup, wl.ndw, 4)
+        rec["nd_kernel_ms"] = round(nd_ms, 4)
+        rec["nd_algorithmic_bytes"] = int(alg)
+        rec["nd_gbs"] = round(alg / (nd_ms / 1e3) / 1e9, 1) if nd_ms > 0 else None
+        rec["nd_frac"] = round(alg / (nd_ms / 1e3) / 1e9 / hbm, 4) if nd_ms > 0 else None
+        out[wl.name] = rec
     return out
 
 
@@ -652,11 +721,13 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="ns18", choices=["ns14", "ns16", "ns18"])
+    import workloads
+    ap.add_argument("--workload", default="ns18", choices=sorted(workloads.WORKLOADS))
     ap.add_argument("--no-gf", dest="gf", action="store_false")
     ap.add_argument("--no-e2e", dest="e2e", action="store_false")
     ap.add_argument("--no-compare", dest="compare", action="store_false")
     ap.add_argument("--no-sub-ns16", dest="sub_ns16", action="store_false")
+    ap.add_argument("--no-full-kanamori", dest="full_kanamori", action="store_false")
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--cpu-steps", type=int, default=3)
     ap.add_argument("--serving", type=int, default=1000,

@@ -352,7 +352,7 @@ __device__ __forceinline__ T ed_nd_terms(const HvTables<T> &tb, const T *v, int6
 ed_status ed_build_nd_tables(ed_sector s, cudaStream_t st);
 void ed_free_nd_tables(ed_sector s, cudaStream_t st);
 // CTAs (= partial sums of the Lanczos and dot modes) of the H_nd kernel
-int64_t ed_nd_grid(int64_t ddw);
+int64_t ed_nd_grid(int64_t ddw, int64_t ncols);
 // Adds the H_nd terms after the factorised product (modes of k_hv; ND_DOT:
 // part[cta] = sum_i v_i (H_nd v)_i, nothing written).
 enum { ND_DOT = 3 };

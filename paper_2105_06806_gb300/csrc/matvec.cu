@@ -1344,7 +1344,7 @@ __global__ void __launch_bounds__(HVS_THREADS) k_hv_small(HvLaunch<T> a) {
 int64_t ed_hv_num_parts(ed_sector s, int layout, int elem_size) {
   if (ed_build_items(s, layout, elem_size) != ED_OK) return 0;
   // the H_nd kernel's partials follow the product's
-  const int64_t nd = s->nd[layout].up ? ed_nd_grid(s->sp[1].dim) : 0;
+  const int64_t nd = s->nd[layout].up ? ed_nd_grid(s->sp[1].dim, s->nd[layout].ncols) : 0;
   if (layout == 1 && s->hv_kernel[elem_size == 8 ? 1 : 0] == 1) return small_grid_of(s->bdim) + nd;
   const ItemList &il = s->items[layout][elem_size == 8 ? 1 : 0];
   return (il.d_ditems ? il.nditems : il.nitems) + nd;
@@ -1445,7 +1445,7 @@ ed_status ed_launch_hv(ed_sector s, const HvTables<T> &tb, int mode, const T *v,
   if (!tb.nd_up) return ED_OK;
   // spin exchange and pair hopping, added to the product (partials after the product's)
   const int64_t np = tb.small_cols ? tb.small_grid : (tb.ditems ? tb.nditems : tb.nitems);
-  if (nparts) *nparts = np + ed_nd_grid(tb.ddw);
+  if (nparts) *nparts = np + ed_nd_grid(tb.ddw, tb.nd_ncols);
   return ed_launch_nd<T>(tb, mode, v, w, bufs, basis, state, part ? part + np : nullptr, st);
 }
 

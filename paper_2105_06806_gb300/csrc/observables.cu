@@ -181,7 +181,7 @@ extern "C" ed_status ed_observables(ed_sector s, ed_precision prec, const void *
   const int nout = 2 * norb + 4 * norb * norb + 2;
   const size_t sb = ((size_t)ddw * nm * sizeof(double) + 255) & ~(size_t)255;
   const size_t pb = ((size_t)nm * nm * sizeof(double) + 255) & ~(size_t)255;
-  const int nnd = (s->nd[0].up && ddw > 0 && dup > 0) ? (int)ed_nd_grid(ddw) : 0;
+  const int nnd = (s->nd[0].up && ddw > 0 && dup > 0) ? (int)ed_nd_grid(ddw, s->nd[0].ncols) : 0;
   const size_t ndb = ((size_t)std::max(nnd, 1) * sizeof(double) + 255) & ~(size_t)255;
   void *mem = nullptr;
   ED_TRY(ed_dmalloc(&mem, sb + pb + ndb + nout * sizeof(double), cs, "observables"));

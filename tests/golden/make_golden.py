@@ -14,7 +14,7 @@ the workload recipe and the oracle's FP64 results:
 * ``oracle_ns16.json`` — Ns=16 two-orbital Kanamori AIM, half filling (8,8),
   D=165,636,900, seeded bath (seed 0): the benchmark sector.  E0, 256 psi
   samples and G_{0,up}(i w_n) from 200-step chains, all from the oracle's
-  factorised product (Sec. 6.7 without MPI); about 90 minutes on one core.
+  factorised product (Sec. 6.7 without MPI); about two hours on one core.
 
 Usage: python tests/golden/make_golden.py [ns8] [ns14] [norb2_ns14] [ns16]
 """

@@ -10,7 +10,7 @@ import pytest
 import torch
 
 from oracle import fock, gf, lanczos
-from workloads import make_model, workload_ns8, workload_ns14, workload_norb2_ns14
+from workloads import make_model, workload_ns8, workload_ns14, workload_norb2_ns14, workload_ns16
 
 pytestmark = pytest.mark.gpu
 GOLD = os.path.join(os.path.dirname(__file__), "golden")
@@ -91,6 +91,37 @@ def test_norb2_ns14_ground_and_gf(ed):
     G2, _ = ed.gf_lanczos(s, psip, rp["e0"], 0, 0, "fp32_polish", nsteps=200, beta=100.0,
                           nmats=512)
     assert np.abs(G2 - Gref).max() <= 1e-5
+    s.free()
+
+
+def test_ns16_benchmark_sector_against_golden(ed):
+    """The Ns=16 two-orbital half-filled sector (D = 165,636,900) against the
+    oracle's stored FP64 run (tests/golden/make_golden.py ns16): E0 of the
+    FP64 path, of the raw FP32 Lanczos (1e-6) and of FP32 + polish (1e-10);
+    256 samples of psi; G_{0,up}(i w_n) and the chain weights from FP64
+    chains (1e-8) and from FP32 chains on the polished state (3e-5)."""
+    g, Gref = _gold("oracle_ns16.json")
+    wl = workload_ns16(0)
+    s = ed.Sector(wl.model, wl.nup, wl.ndw)
+    e = g["e0"]
+    r, psi = _ground(ed, s, "fp64")
+    assert abs(r["e0"] - e) <= 1e-10 * abs(e)
+    sgn = float(torch.sign(psi[torch.argmax(psi.abs())]))
+    idx = torch.tensor(g["psi_index"], device="cuda")
+    assert np.abs(sgn * psi[idx].cpu().numpy() - np.array(g["psi_value"])).max() < 1e-8
+    G, info = ed.gf_lanczos(s, psi, r["e0"], 0, 0, "fp64", nsteps=200, beta=100.0, nmats=512)
+    assert np.abs(G - Gref).max() <= 1e-8
+    assert abs(info["weight_particle"] - g["weight_particle"]) < 1e-10
+    assert abs(info["weight_hole"] - g["weight_hole"]) < 1e-10
+    del psi
+    rp, psip = _ground(ed, s, "fp32_polish")
+    assert abs(rp["e0_raw"] - e) <= 1e-6 * abs(e)
+    assert abs(rp["e0"] - e) <= 1e-10 * abs(e)
+    G2, _ = ed.gf_lanczos(s, psip, rp["e0"], 0, 0, "fp32_polish", nsteps=200, beta=100.0,
+                          nmats=512)
+    # FP32 chains: the error grows with the sector dimension (about 5e-7 at
+    # D = 4.9e3, 3e-6 at 1.2e7, 1.3e-5 at 1.7e8), set by the FP32 vectors
+    assert np.abs(G2 - Gref).max() <= 3e-5
     s.free()
 
 
