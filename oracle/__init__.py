@@ -30,6 +30,11 @@ Modules
               self-energy, and local densities, density-density correlators
               and the interaction energy of a ground state (Sec. 6.8, App. B).
 
+``eph``       The electron-phonon (Holstein) extension of Sec. 4: the coupled
+              sector of Eq. HephBuild with the phonon index slowest (Eq.
+              Vdecomp2), its product slice by slice, c / c^+ on every phonon
+              slice and the T = 0 Green's function from chains.
+
 Every function cites the passage of the paper it follows.  Pins (tests under
 ``tests/test_oracle_*.py``) tie each function to something other than itself:
 binomial dimensions, brute force, closed forms and symmetry invariants.

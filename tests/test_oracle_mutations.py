@@ -226,3 +226,39 @@ def test_interaction_energy_without_nondiagonal_terms_is_caught(monkeypatch):
         return d, nn, e - float(p @ (sec.H_nd @ p))
     monkeypatch.setattr(observables, "local_observables", bad)
     assert gap() > 1e-3
+
+
+# ------------------------------------------------------------ electron-phonon
+
+def _polaron_error():
+    """Distance of the coupled atom's lowest level (two electrons) from the
+    displaced-oscillator value e n + U - g^2 n^2 / w0."""
+    from oracle import eph
+    from workloads import ImpurityModel
+    U, e, w0, g = 1.7, -0.4, 0.8, 0.5
+    m = ImpurityModel(norb=1, nbath=0, U=U, Ust=U, Jh=0.0, e_imp=np.array([e]),
+                      e_bath=np.zeros((1, 0)), v_bath=np.zeros((1, 0)))
+    ph = eph.Phonon(w0=w0, g=np.array([g]), nph=40)
+    fock._SECTOR_CACHE.clear()
+    ev = np.linalg.eigvalsh(eph.hamiltonian(m, ph, 1, 1).toarray())
+    return abs(ev[0] - (2 * e + U - 4 * g * g / w0))
+
+
+def test_wrong_displacement_matrix_is_caught(monkeypatch):
+    import scipy.sparse as sp
+    from oracle import eph
+    assert _polaron_error() < 1e-10
+
+    def bad(nph):   # sqrt(p) in place of sqrt(p + 1)
+        off = np.sqrt(np.arange(0, nph, dtype=np.float64))
+        return sp.csr_matrix(sp.diags([off, off], [-1, 1], shape=(nph + 1, nph + 1)))
+    monkeypatch.setattr(eph, "displacement", bad)
+    assert _polaron_error() > 1e-3
+
+
+def test_coupling_to_n_minus_one_is_caught(monkeypatch):
+    from oracle import eph
+    orig = eph.coupling_diagonal
+    monkeypatch.setattr(eph, "coupling_diagonal",
+                        lambda m, ph, nu, nd: orig(m, ph, nu, nd) - float(np.sum(ph.g)))
+    assert _polaron_error() > 1e-3
