@@ -316,6 +316,51 @@ ed_status ed_sigma(const ed_model *model, int32_t orb, int32_t spin, const doubl
 ed_status ed_observables(ed_sector s, ed_precision prec, const void *d_psi, int64_t n,
                          double *host_out, void *stream);
 
+/* ---------------------------------------------------------------- electron-phonon
+ * One local phonon mode coupled to the impurity densities (Sec. 4):
+ *   H = H_e + w0 b^+ b + sum_{alpha sigma} g_alpha d^+_{alpha sigma} d_{alpha sigma} (b + b^+),
+ * phonon number cut off at nph (states |0>..|nph>, D_ph = nph + 1).  A
+ * coupled sector is an electronic sector times the phonon space, phonon
+ * index slowest (Eq. Vdecomp2): element i_e + p * D of a vector of
+ * D * D_ph elements, i_e the electronic sector index; its matrix is
+ * Eq. HephBuild, 1 (x) H_e + H_ph (x) 1 + (b + b^+) (x) N_g with
+ * N_g = sum_alpha g_alpha (n_{alpha up} + n_{alpha dw}). */
+typedef struct {
+  double w0;               /* phonon frequency                               */
+  double g[ED_MAX_NORB];   /* coupling g_alpha of orbital alpha (unused: 0)  */
+  int32_t nph;             /* phonon cut-off N_ph, 0..ED_MAX_NPH             */
+  int32_t reserved;        /* 0                                              */
+} ed_phonon;
+#define ED_MAX_NPH 4095
+
+/* w = H v on the coupled sector of s (Eq. HephBuild): the electronic product
+ * of ed_matvec on every phonon slice, then the phonon terms
+ * w[p] += w0 p v[p] + N_g (sqrt(p) v[p-1] + sqrt(p+1) v[p+1]) in one pass over
+ * the slices.  v, w: device, n = D * (nph + 1) elements in the precision's
+ * type, distinct.  ED_ERR_ARG for a bad size, pointer or phonon record. */
+ed_status ed_eph_matvec(ed_sector s, const ed_phonon *ph, ed_precision prec, const void *d_v,
+                        void *d_w, int64_t n, void *stream);
+
+/* Lanczos ground state of the coupled sector (Sec. 4 with Sec. 6.6): plain
+ * Lanczos on the device (the vectors in padded block-major slices), the
+ * stopping rule of ed_lanczos_ground checked every 4 steps, psi from the
+ * second pass.  ED_FP32_POLISH runs `polish_steps` FP64 steps from the FP32
+ * vector.  d_psi (nullable) receives psi in coupled sector order (double for
+ * ED_FP64 / ED_FP32_POLISH, float for ED_FP32).  Fields of ed_lanczos_opts as
+ * for ed_lanczos_ground (basis_mib unused: always the second pass).
+ * Synchronises `stream`. */
+ed_status ed_eph_lanczos_ground(ed_sector s, const ed_phonon *ph, const ed_lanczos_opts *opts,
+                                ed_lanczos_result *res, void *d_psi, void *stream);
+
+/* G(z) of the coupled model at T = 0 (Eq. KLgf with the coupled H): chains
+ * started from c^+ psi and c psi, c acting on every phonon slice, on the
+ * coupled N+-1 sectors; arguments and output as ed_gf_lanczos_z, d_psi in
+ * coupled sector order. */
+ed_status ed_eph_gf_lanczos_z(ed_sector s, const ed_phonon *ph, ed_precision prec,
+                              const void *d_psi, double e0, int32_t orb, int32_t spin,
+                              int32_t nsteps, const double *host_z, int32_t nz, double *host_G,
+                              ed_gf_info *info, void *stream);
+
 /* One impurity solve: sector build, ground state, and G for every orbital and
  * both spins (the down spin is copied from the up spin when N_up = N_dw and
  * the model is spin symmetric, Sec. 6.6 twin symmetry).  The particle and

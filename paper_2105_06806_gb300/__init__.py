@@ -29,7 +29,8 @@ EXPORTED = [
     "ed_sector_free", "ed_matvec", "ed_matvec_blocked", "ed_sector_blocked_kernel",
     "ed_sector_tune_info", "ed_sector_set_kernel",
     "ed_sector_permute", "ed_lanczos_ground", "ed_gf_lanczos", "ed_gf_lanczos_z", "ed_sigma",
-    "ed_observables", "ed_solve",
+    "ed_observables", "ed_solve", "ed_eph_matvec", "ed_eph_lanczos_ground",
+    "ed_eph_gf_lanczos_z",
     "ed_server_create", "ed_submit", "ed_poll", "ed_wait", "ed_server_destroy",
     "ed_server_inject_alloc_failure", "ed_batch_stats", "ed_residual_noalloc", "ed_status_string",
     "ed_last_error",
@@ -85,6 +86,14 @@ class ed_lanczos_result(C.Structure):
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+ED_MAX_NORB = 5
+
+
+class ed_phonon(C.Structure):
+    _fields_ = [("w0", C.c_double), ("g", C.c_double * ED_MAX_NORB), ("nph", C.c_int32),
+                ("reserved", C.c_int32)]
 
 
 class ed_gf_info(C.Structure):
@@ -169,6 +178,11 @@ def lib():
                                 C.POINTER(ed_gf_info), vp],
             "ed_sigma": [C.POINTER(ed_model), i32, i32, vp, i32, vp, vp, vp],
             "ed_observables": [vp, C.c_int, vp, i64, vp, vp],
+            "ed_eph_matvec": [vp, C.POINTER(ed_phonon), C.c_int, vp, vp, i64, vp],
+            "ed_eph_lanczos_ground": [vp, C.POINTER(ed_phonon), C.POINTER(ed_lanczos_opts),
+                                      C.POINTER(ed_lanczos_result), vp, vp],
+            "ed_eph_gf_lanczos_z": [vp, C.POINTER(ed_phonon), C.c_int, vp, C.c_double, i32, i32,
+                                    i32, vp, i32, vp, C.POINTER(ed_gf_info), vp],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -439,6 +453,47 @@ def observables(sector: Sector, psi, precision="fp64", stream=None):
     return {"dens": out[:2 * no].reshape(2, no).copy(),
             "nn": out[2 * no:2 * no + 4 * no * no].reshape(2, 2, no, no).copy(),
             "e_int": float(out[-2]), "norm": float(out[-1])}
+
+
+def phonon(w0, g, nph):
+    """ed_phonon record: frequency w0, couplings g[alpha] (zero-padded), cut-off N_ph."""
+    gg = np.zeros(ED_MAX_NORB)
+    gv = np.atleast_1d(np.asarray(g, dtype=np.float64))
+    gg[:gv.size] = gv
+    return ed_phonon(float(w0), (C.c_double * ED_MAX_NORB)(*gg), int(nph), 0)
+
+
+def eph_matvec(sector: Sector, ph, v, w, precision="fp64", stream=None):
+    """w = H v on the coupled electron-phonon sector (ed_eph_matvec); v, w of
+    D * (nph + 1) elements, phonon index slowest."""
+    _check(lib().ed_eph_matvec(sector.h, C.byref(ph), _prec(precision), C.c_void_p(v.data_ptr()),
+                               C.c_void_p(w.data_ptr()), int(v.numel()),
+                               C.c_void_p(_stream_ptr(stream))), "ed_eph_matvec")
+
+
+def eph_lanczos_ground(sector: Sector, ph, precision="fp64", max_iter=0, tol=0.0, seed=0x5EED,
+                       polish_steps=0, psi=None, stream=None):
+    o = ed_lanczos_opts(_prec(precision), int(max_iter), float(tol), int(seed),
+                        int(polish_steps), 1, 0, 0)
+    r = ed_lanczos_result()
+    _check(lib().ed_eph_lanczos_ground(sector.h, C.byref(ph), C.byref(o), C.byref(r),
+                                       C.c_void_p(psi.data_ptr() if psi is not None else 0),
+                                       C.c_void_p(_stream_ptr(stream))), "ed_eph_lanczos_ground")
+    return r.as_dict()
+
+
+def eph_gf_lanczos_z(sector: Sector, ph, psi, e0, orb, spin, z, precision="fp64", nsteps=200,
+                     stream=None):
+    """G(z) of the coupled model (ed_eph_gf_lanczos_z)."""
+    zz = np.ascontiguousarray(np.asarray(z, dtype=np.complex128).reshape(-1))
+    G = np.zeros(zz.size, dtype=np.complex128)
+    info = ed_gf_info()
+    _check(lib().ed_eph_gf_lanczos_z(sector.h, C.byref(ph), _prec(precision),
+                                     C.c_void_p(psi.data_ptr()), float(e0), int(orb), int(spin),
+                                     int(nsteps), C.c_void_p(zz.ctypes.data), int(zz.size),
+                                     C.c_void_p(G.ctypes.data), C.byref(info),
+                                     C.c_void_p(_stream_ptr(stream))), "ed_eph_gf_lanczos_z")
+    return G, {k: getattr(info, k) for k, _ in info._fields_}
 
 
 def solve_opts(precision="fp32_polish", gf_precision=None, nmats=512, beta=100.0,

@@ -132,6 +132,52 @@ __global__ void k_cfrac_z(const LanczosState *st, double weight, double e0, cons
 
 static size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
 
+// c^+ / c of (orb, spin) from psi (sector order of s) into phi (block-major
+// order of the neighbour sector nb): one launch of k_apply_op.
+template <typename Ti, typename To>
+ed_status ed_apply_op_launch(ed_sector s, ed_sector nb, const Ti *psi, To *phi, int orb, int spin,
+                             int create, cudaStream_t cs) {
+  const int64_t n = nb->bdim;
+  const int64_t g2 = ed_reduce_grid(n);
+  void *part = nullptr;
+  ED_TRY(ed_dmalloc(&part, g2 * sizeof(double), cs, "apply partials"));
+  ApplyArgs a;
+  a.dst_map = nb->bk[spin].map;
+  a.dst_pother = nb->bi[1 - spin].pidx;
+  a.dst_padinv = nb->padinv;
+  a.dst_stride = nb->bstride;
+  a.dst_dim = n;
+  a.src_dup = s->sp[0].dim;
+  a.level = orb;  // impurity orbital alpha is level alpha
+  a.create = create;
+  a.spin = spin;
+  a.nup_src = s->nup;
+  k_apply_op<Ti, To><<<(unsigned)g2, GF_THREADS, 0, cs>>>(a, psi, phi, (double *)part);
+  ed_count_launches(1);
+  const cudaError_t e = cudaGetLastError();
+  ed_dfree(part, cs);
+  if (e != cudaSuccess) {
+    ed_set_cuda_error(e, "k_apply_op", __FILE__, __LINE__);
+    return ED_ERR_CUDA;
+  }
+  return ED_OK;
+}
+template ed_status ed_apply_op_launch<double, double>(ed_sector, ed_sector, const double *, double *,
+                                                      int, int, int, cudaStream_t);
+template ed_status ed_apply_op_launch<double, float>(ed_sector, ed_sector, const double *, float *,
+                                                     int, int, int, cudaStream_t);
+template ed_status ed_apply_op_launch<float, float>(ed_sector, ed_sector, const float *, float *,
+                                                    int, int, int, cudaStream_t);
+
+// G[n] += sgn * weight * [(e0 + sgn z_n - T)^-1]_00 for the chain held in st
+ed_status ed_cfrac_z_launch(const LanczosState *st, double weight, double e0, const double2 *dz,
+                            int nz, int sgn, double2 *dG, cudaStream_t cs) {
+  if (nz <= 0) return ED_OK;
+  k_cfrac_z<<<(nz + 31) / 32, 32, 0, cs>>>(st, weight, e0, dz, nz, sgn, dG);
+  ED_LAUNCHED(1);
+  return ED_OK;
+}
+
 // ----------------------------------------------------------------- batched chains
 //
 // All chains of a solve whose sectors are small run in one persistent launch:

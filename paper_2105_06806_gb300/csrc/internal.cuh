@@ -212,6 +212,15 @@ static __constant__ BinomTable c_binom_tab = ed_make_binom();
 #define c_binom (c_binom_tab.v)
 inline ed_status ed_upload_binomials() { return ED_OK; }
 
+// Output i of a SplitMix64 stream seeded with `seed` (Steele, Lea, Flood
+// 2014): the seeded start vectors of the Lanczos drivers.
+__device__ __forceinline__ uint64_t ed_splitmix64_at(uint64_t seed, uint64_t i) {
+  uint64_t z = seed + (i + 1ull) * 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
 __device__ __forceinline__ uint32_t ed_unrank(uint64_t r, int ns, int n) {
   // Combinatorial number system: the r-th Ns-bit string with n set bits in
   // ascending order has set bits p_1 < ... < p_n with r = sum_k C(p_k, k).
@@ -410,3 +419,50 @@ ed_status ed_neighbor_sector(ed_sector s, int spin, int create, cudaStream_t st,
 // Releases s (and its neighbour sectors) ordered on st, without
 // synchronising the device; no work that reads s may be pending elsewhere.
 void ed_sector_release(ed_sector s, cudaStream_t st);
+
+// ----------------------------------------------------------------- operator Lanczos (oplanczos.cu)
+
+#include <functional>
+
+// A linear operator on device vectors of n elements (padding included; it
+// must leave padding entries of w zero when those of v are zero).
+template <typename T>
+struct LinOp {
+  int64_t n = 0;
+  std::function<ed_status(const T *v, T *w, cudaStream_t)> apply;
+};
+
+struct OpRun {
+  std::vector<double> alpha, beta;  // beta[0] = 0; beta[j] couples v_{j-1}, v_j
+  int k = 0;                        // steps taken
+  int stop = 0;                     // 0 converged, 1 breakdown, 2 step limit
+  double theta = 0.0;               // lowest Ritz value (ground runs)
+  double resid_est = 0.0;           // beta_{k+1} |y_k|
+  double weight = 0.0;              // ||v0||^2
+  std::vector<double> y;            // Ritz vector of theta
+  int matvecs = 0;
+};
+
+// Lanczos from v0 (normalised inside): ground = stop on the lowest Ritz
+// value's residual estimate (checked every 4 steps), else run to maxit or
+// breakdown (a Green's-function chain).  alpha/beta also land in dst (device,
+// nullable).  With ground and psi: the second pass writes the normalised
+// Ritz vector into psi.
+template <typename T>
+ed_status ed_op_lanczos(const LinOp<T> &op, const T *v0, int maxit, double tol, bool ground,
+                        OpRun *out, LanczosState *dst, T *psi, cudaStream_t cs);
+ed_status ed_op_residual(const LinOp<double> &op, const double *psi, double *e, double *r,
+                         cudaStream_t cs);
+template <typename Ti, typename To>
+ed_status ed_op_normalised_copy(const Ti *x, To *y, int64_t n, cudaStream_t cs);
+
+// gf.cu: one c^+ / c application into a block-major slice, one continued fraction
+template <typename Ti, typename To>
+ed_status ed_apply_op_launch(ed_sector s, ed_sector nb, const Ti *psi, To *phi, int orb, int spin,
+                             int create, cudaStream_t cs);
+ed_status ed_cfrac_z_launch(const LanczosState *st, double weight, double e0, const double2 *dz,
+                            int nz, int sgn, double2 *dG, cudaStream_t cs);
+// lanczos.cu: sector order <-> block-major order of one vector
+ed_status ed_permute_vec(ed_sector s, ed_precision prec, bool to_blocked, const void *in,
+                         void *out, cudaStream_t cs);
+

@@ -424,12 +424,6 @@ __global__ void k_beta(LanczosState *st, const double *part, int64_t nparts) {
 // Start vector: element i = u_i - 1/2 with u_i the uniform double of output i
 // of a SplitMix64 stream seeded with `seed` (Steele, Lea, Flood 2014; top 53
 // bits times 2^-53), in sector order.  Partial sums of squares per CTA.
-__device__ __forceinline__ uint64_t splitmix64_at(uint64_t seed, uint64_t i) {
-  uint64_t z = seed + (i + 1ull) * 0x9E3779B97F4A7C15ull;
-  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
-  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
-  return z ^ (z >> 31);
-}
 
 // The vector lives in padded block-major order: element (r', pc) holds the
 // start value of sector index pidx_dw[r'] * D_up + pidx_up[padinv[pc]], and
@@ -452,7 +446,7 @@ __global__ void __launch_bounds__(AXPY_THREADS) k_start_vector(T *v, int64_t n, 
       T x = T(0);
       if (cb >= 0) {
         const uint64_t p = (uint64_t)pidx_dw[r] * (uint64_t)dup + (uint64_t)pidx_up[cb];
-        double u = (double)(splitmix64_at(seed, p) >> 11) * (1.0 / 9007199254740992.0);
+        double u = (double)(ed_splitmix64_at(seed, p) >> 11) * (1.0 / 9007199254740992.0);
         x = (T)(u - 0.5);
       }
       v[i] = x;
@@ -1185,6 +1179,13 @@ extern "C" ed_status ed_lanczos_ground(ed_sector s, const ed_lanczos_opts *opts,
                                        ed_lanczos_result *res, void *d_psi, void *stream) {
   if (!s || !opts || !res) return ED_ERR_ARG;
   return ed_lanczos_ground_impl(s, opts, res, d_psi, (cudaStream_t)stream);
+}
+
+ed_status ed_permute_vec(ed_sector s, ed_precision prec, bool to_blocked, const void *in,
+                         void *out, cudaStream_t cs) {
+  if (prec == ED_FP64)
+    return permute_layout<double, double>(s, (const double *)in, (double *)out, to_blocked, cs);
+  return permute_layout<float, float>(s, (const float *)in, (float *)out, to_blocked, cs);
 }
 
 extern "C" ed_status ed_sector_permute(ed_sector s, ed_precision prec, int32_t to_blocked,

@@ -56,6 +56,7 @@ STRUCTS = {
     "ed_server_opts": ["slots", "device_mem_budget", "queue_capacity"],
     "ed_request": ["model", "nup", "ndw", "opts"],
     "ed_result": ["status", "e0", "ground", "norb", "nmats", "t_submit_s", "t_done_s"],
+    "ed_phonon": ["w0", "g", "nph", "reserved"],
 }
 
 

@@ -242,6 +242,19 @@ def workload_full_ns18(seed: int = 0) -> Workload:
                     description=w.description.replace("J=0.4", "J=JX=JP=0.4"))
 
 
+def workload_eph_ns12(seed: int = 0, nph: int = 10) -> Workload:
+    """Electron-phonon (Holstein) AIM of the paper's phonon benchmark: Ns=12
+    (one orbital, Nbath=11), half-filled sector (6,6), D_e = 853,776, one
+    phonon mode w0 = 0.5 coupled with g = 0.3, cut-off N_ph (D = D_e (N_ph+1));
+    U = 2, e_d = -1, seeded random bath."""
+    e, v = random_bath(1, 11, seed)
+    m = make_model(1, 11, U=2.0, e_d=-1.0, e_bath=e, v_bath=v, name="holstein_ns12")
+    return Workload(f"holstein_norb1_ns12_n6_6_nph{nph}", m, 6, 6, gf_steps=200,
+                    extra={"w0": 0.5, "g": [0.3], "nph": nph},
+                    description=f"Norb=1 Nbath=11 Ns=12 sector (6,6) D_e=853776 w0=0.5 g=0.3 "
+                                f"N_ph={nph} U=2 seed={seed}")
+
+
 # Valid (norb, ns) pairs for the serving stream: ns must be a multiple of
 # norb (Ns = Norb (Nbath+1)), ns in {8,...,16}, norb in {1,2,3}.
 SERVING_PAIRS = [(no, ns) for no in (1, 2, 3) for ns in (8, 10, 12, 14, 16)
@@ -290,4 +303,5 @@ WORKLOADS = {
     "full3_ns15": workload_full_norb3_ns15,
     "full5_ns15": workload_full_norb5_ns15,
     "full_ns18": workload_full_ns18,
+    "eph_ns12": workload_eph_ns12,
 }
