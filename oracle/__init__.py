@@ -35,6 +35,12 @@ Modules
               Vdecomp2), its product slice by slice, c / c^+ on every phonon
               slice and the T = 0 Green's function from chains.
 
+``thermal``   Several low-lying states of a sector (ARPACK on the sector
+              operator, Sec. 5), the eigenspace list with the annealing
+              truncation of Sec. 6.2, the finite-temperature Green's function
+              as the Boltzmann-weighted sum of per-state chains (App. A), and
+              the exact finite-temperature Lehmann sum for pins.
+
 Every function cites the passage of the paper it follows.  Pins (tests under
 ``tests/test_oracle_*.py``) tie each function to something other than itself:
 binomial dimensions, brute force, closed forms and symmetry invariants.

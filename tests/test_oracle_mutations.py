@@ -262,3 +262,45 @@ def test_coupling_to_n_minus_one_is_caught(monkeypatch):
     monkeypatch.setattr(eph, "coupling_diagonal",
                         lambda m, ph, nu, nd: orig(m, ph, nu, nd) - float(np.sum(ph.g)))
     assert _polaron_error() > 1e-3
+
+
+# ------------------------------------------------------------ finite temperature
+
+def _thermal_mismatch():
+    from oracle import thermal
+    from workloads import ImpurityModel
+    b = make_model(1, 3, U=2.2, e_d=-0.9, seed=3)
+    r = np.random.default_rng(3)
+    m = ImpurityModel(norb=1, nbath=3, U=b.U, Ust=b.Ust, Jh=b.Jh,
+                      e_imp=b.e_imp + r.normal(0, .2, (2, 1)),
+                      e_bath=b.e_bath + r.normal(0, .2, b.e_bath.shape),
+                      v_bath=b.v_bath * r.uniform(.5, 1.5, b.v_bath.shape))
+    fock._SECTOR_CACHE.clear()
+    sectors = [(2, 2), (2, 1), (1, 2)]
+    per = [np.linalg.eigh(fock.get_sector(m, nu, nd).hamiltonian().toarray()) for nu, nd in sectors]
+    w, _ = thermal.espace_truncate([e for e, _ in per], 0.7, 0.0)
+    states = [(ws[i], nu, nd, V[:, i], E[i]) for (nu, nd), (E, V), ws in zip(sectors, per, w)
+              for i in range(len(E))]
+    z = 1j * (2 * np.arange(20) + 1) * np.pi / 0.7
+    G = thermal.thermal_gf_z(m, states, 0, 0, z, nsteps=64)
+    return np.abs(G - thermal.lehmann_thermal_z(m, sectors, 0.7, 0, 0, z)).max()
+
+
+def test_wrong_boltzmann_sign_is_caught(monkeypatch):
+    from oracle import thermal
+    assert _thermal_mismatch() < 1e-11
+    orig = thermal.espace_truncate
+    monkeypatch.setattr(thermal, "espace_truncate",
+                        lambda Es, beta, cutoff, *a, **k: orig(Es, -beta, cutoff, *a, **k))
+    assert _thermal_mismatch() > 1e-3
+
+
+def test_unnormalised_weights_are_caught(monkeypatch):
+    from oracle import thermal
+    orig = thermal.espace_truncate
+
+    def bad(*a, **k):
+        w, n = orig(*a, **k)
+        return [x * 2.0 for x in w], n
+    monkeypatch.setattr(thermal, "espace_truncate", bad)
+    assert _thermal_mismatch() > 1e-3
