@@ -301,6 +301,8 @@ def run_ours(args):
 
     if rank == 0 and args.full_kanamori:
         subs["full_kanamori"] = run_full_kanamori(E, stream, dev, hbm)
+    if rank == 0 and args.eph:
+        subs["electron_phonon_ns12"] = run_eph(E, stream, dev)
 
     # plain FP64 GPU Lanczos against FP32 + FP64 polish, ground state only,
     # time to solution at the same 1e-10 accuracy target
@@ -478,6 +480,49 @@ def run_full_kanamori(E, stream, dev, hbm):
         rec["nd_gbs"] = round(alg / (nd_ms / 1e3) / 1e9, 1) if nd_ms > 0 else None
         rec["nd_frac"] = round(alg / (nd_ms / 1e3) / 1e9 / hbm, 4) if nd_ms > 0 else None
         out[wl.name] = rec
+    return out
+
+
+def run_eph(E, stream, dev, nphs=(0, 2, 5, 10)):
+    """The electron-phonon extension (Sec. 4) on the paper's phonon benchmark
+    (Ns = 12, half-filled (6,6), one mode): ground state (FP32 + FP64 polish)
+    time against the phonon cut-off N_ph, and the FP32 coupled product in
+    sector order (CUDA events, median of 10)."""
+    import torch
+    import workloads
+    out = {}
+    for nph in nphs:
+        wl = workloads.workload_eph_ns12(0, nph)
+        x = wl.extra
+        ph = E.phonon(x["w0"], x["g"], x["nph"])
+        s = E.Sector(wl.model, wl.nup, wl.ndw, stream=stream)
+        D = s.dim * (nph + 1)
+        best, r = None, None
+        for _ in range(2):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            r = E.eph_lanczos_ground(s, ph, "fp32_polish", stream=stream)
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+            best = dt if best is None else min(best, dt)
+        v = torch.randn(D, dtype=torch.float32, device=dev)
+        w = torch.empty_like(v)
+        for _ in range(2):
+            E.eph_matvec(s, ph, v, w, "fp32", stream=stream)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        durs = []
+        for _ in range(10):
+            a.record(stream)
+            E.eph_matvec(s, ph, v, w, "fp32", stream=stream)
+            b.record(stream)
+            b.synchronize()
+            durs.append(a.elapsed_time(b))
+        del v, w
+        s.free()
+        out[f"nph{nph}"] = {"dim": D, "ground_fp32_polish_s": round(best, 4), "e0": r["e0"],
+                            "iterations": r["iterations"] + r["polish_iterations"],
+                            "residual": r["residual"],
+                            "product_fp32_ms": round(statistics.median(durs), 4)}
     return out
 
 
@@ -728,6 +773,7 @@ def main():
     ap.add_argument("--no-compare", dest="compare", action="store_false")
     ap.add_argument("--no-sub-ns16", dest="sub_ns16", action="store_false")
     ap.add_argument("--no-full-kanamori", dest="full_kanamori", action="store_false")
+    ap.add_argument("--no-eph", dest="eph", action="store_false")
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--cpu-steps", type=int, default=3)
     ap.add_argument("--serving", type=int, default=1000,

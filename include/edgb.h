@@ -316,6 +316,52 @@ ed_status ed_sigma(const ed_model *model, int32_t orb, int32_t spin, const doubl
 ed_status ed_observables(ed_sector s, ed_precision prec, const void *d_psi, int64_t n,
                          double *host_out, void *stream);
 
+/* ---------------------------------------------------------------- several states, finite T
+ * The nstates lowest eigenpairs of the sector (the states of the eigenspace
+ * list, Sec. 6.2; the paper takes them from P-ARPACK, Sec. 5): Lanczos on
+ * the block-major vectors, state k found as the lowest eigenpair of
+ *   H + sigma sum_{j<k} |psi_j><psi_j|
+ * (shift deflation: the states already found are moved above the top of the
+ * spectrum; sigma = 1.05 (theta_max - E_0) + 1e-6, theta_max the highest Ritz
+ * value of the first run), each with the stopping rule and the second pass
+ * of ed_lanczos_ground; ED_FP32_POLISH runs every state in FP32, then
+ * polish_steps FP64 steps on the FP64 deflated operator.  host_e receives the
+ * nstates energies in the order found (ascending up to the tolerance), res
+ * (nullable) nstates results (residuals of the undeflated H), d_psis
+ * (nullable) nstates consecutive normalised vectors of D elements in sector
+ * order (double for ED_FP64 / ED_FP32_POLISH, float for ED_FP32).
+ * ED_ERR_ARG unless 1 <= nstates <= min(D, ED_MAX_STATES).  Synchronises
+ * `stream`. */
+#define ED_MAX_STATES 256
+ed_status ed_lanczos_states(ed_sector s, const ed_lanczos_opts *opts, int32_t nstates,
+                            double *host_e, ed_lanczos_result *res, void *d_psis, void *stream);
+
+/* Annealing truncation of the eigenspace list (Sec. 6.2; host only).  The
+ * states of nsectors sectors, counts[q] of sector q with their energies
+ * ascending and consecutive in `energies`: E0 the lowest; a state is kept when
+ * e^{-beta (E - E0)} >= cutoff (the paper's "<" read as the condition for
+ * dropping it), lowest first, at most ntotal states; weights (one per state,
+ * 0 for a dropped one) = e^{-beta (E - E0)} / Z over the kept states.
+ * next_counts[q]: counts[q] + step when the highest computed state of sector
+ * q was kept (the sector may hold more states under the threshold), else one
+ * more than the sector kept.  *nkept receives the kept count. */
+ed_status ed_espace_truncate(int32_t nsectors, const int32_t *counts, const double *energies,
+                             double beta, double cutoff, int32_t ntotal, int32_t step,
+                             double *weights, int32_t *next_counts, int32_t *nkept);
+
+/* Finite-temperature Green's function (App. A: the thermal average over the
+ * eigenstates of Eq. KLgf): G(z) = sum_i w_i G_i(z), G_i the
+ * ed_gf_lanczos_z function of state i (sector sectors[i], normalised vector
+ * d_psis[i] in sector order, energy energies[i]) and w_i the weights of
+ * ed_espace_truncate over the nstates states (one list).  host_w (nullable)
+ * receives the weights; dropped states run no chains.  Other arguments as
+ * ed_gf_lanczos_z.  Synchronises `stream`. */
+ed_status ed_gf_thermal_z(int32_t nstates, const ed_sector *sectors, const void *const *d_psis,
+                          const double *energies, double beta, double cutoff, int32_t ntotal,
+                          ed_precision prec, int32_t orb, int32_t spin, int32_t nsteps,
+                          const double *host_z, int32_t nz, double *host_G, double *host_w,
+                          void *stream);
+
 /* ---------------------------------------------------------------- electron-phonon
  * One local phonon mode coupled to the impurity densities (Sec. 4):
  *   H = H_e + w0 b^+ b + sum_{alpha sigma} g_alpha d^+_{alpha sigma} d_{alpha sigma} (b + b^+),

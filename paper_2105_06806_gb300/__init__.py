@@ -30,7 +30,7 @@ EXPORTED = [
     "ed_sector_tune_info", "ed_sector_set_kernel",
     "ed_sector_permute", "ed_lanczos_ground", "ed_gf_lanczos", "ed_gf_lanczos_z", "ed_sigma",
     "ed_observables", "ed_solve", "ed_eph_matvec", "ed_eph_lanczos_ground",
-    "ed_eph_gf_lanczos_z",
+    "ed_eph_gf_lanczos_z", "ed_lanczos_states", "ed_espace_truncate", "ed_gf_thermal_z",
     "ed_server_create", "ed_submit", "ed_poll", "ed_wait", "ed_server_destroy",
     "ed_server_inject_alloc_failure", "ed_batch_stats", "ed_residual_noalloc", "ed_status_string",
     "ed_last_error",
@@ -183,6 +183,12 @@ def lib():
                                       C.POINTER(ed_lanczos_result), vp, vp],
             "ed_eph_gf_lanczos_z": [vp, C.POINTER(ed_phonon), C.c_int, vp, C.c_double, i32, i32,
                                     i32, vp, i32, vp, C.POINTER(ed_gf_info), vp],
+            "ed_lanczos_states": [vp, C.POINTER(ed_lanczos_opts), i32, vp,
+                                  C.POINTER(ed_lanczos_result), vp, vp],
+            "ed_espace_truncate": [i32, vp, vp, C.c_double, C.c_double, i32, i32, vp, vp,
+                                   C.POINTER(i32)],
+            "ed_gf_thermal_z": [i32, vp, vp, vp, C.c_double, C.c_double, i32, C.c_int, i32, i32,
+                                i32, vp, i32, vp, vp, vp],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -494,6 +500,61 @@ def eph_gf_lanczos_z(sector: Sector, ph, psi, e0, orb, spin, z, precision="fp64"
                                      C.c_void_p(G.ctypes.data), C.byref(info),
                                      C.c_void_p(_stream_ptr(stream))), "ed_eph_gf_lanczos_z")
     return G, {k: getattr(info, k) for k, _ in info._fields_}
+
+
+def lanczos_states(sector: Sector, nstates, precision="fp64", max_iter=0, tol=0.0,
+                   seed=0x5EED, polish_steps=0, psis=None, stream=None):
+    """The nstates lowest eigenpairs of the sector (ed_lanczos_states): returns
+    (energies, [result dicts]); psis (optional device tensor of nstates x D)
+    receives the states in sector order."""
+    o = ed_lanczos_opts(_prec(precision), int(max_iter), float(tol), int(seed),
+                        int(polish_steps), 1, 0, 0)
+    E = np.zeros(int(nstates))
+    res = (ed_lanczos_result * int(nstates))()
+    _check(lib().ed_lanczos_states(sector.h, C.byref(o), int(nstates), C.c_void_p(E.ctypes.data),
+                                   res, C.c_void_p(psis.data_ptr() if psis is not None else 0),
+                                   C.c_void_p(_stream_ptr(stream))), "ed_lanczos_states")
+    return E, [r.as_dict() for r in res]
+
+
+def espace_truncate(energies_per_sector, beta, cutoff, ntotal=0, step=2):
+    """Annealing truncation of the eigenspace list (ed_espace_truncate):
+    returns (weights per sector, next state counts, number kept)."""
+    counts = np.array([len(e) for e in energies_per_sector], dtype=np.int32)
+    flat = np.ascontiguousarray(np.concatenate([np.asarray(e, dtype=np.float64)
+                                                for e in energies_per_sector]))
+    w = np.zeros(flat.size)
+    nxt = np.zeros(counts.size, dtype=np.int32)
+    nk = C.c_int32()
+    _check(lib().ed_espace_truncate(int(counts.size), C.c_void_p(counts.ctypes.data),
+                                    C.c_void_p(flat.ctypes.data), float(beta), float(cutoff),
+                                    int(ntotal), int(step), C.c_void_p(w.ctypes.data),
+                                    C.c_void_p(nxt.ctypes.data), C.byref(nk)),
+           "ed_espace_truncate")
+    out, o = [], 0
+    for c in counts:
+        out.append(w[o:o + c].copy())
+        o += c
+    return out, [int(x) for x in nxt], int(nk.value)
+
+
+def gf_thermal_z(sectors, psis, energies, beta, cutoff, orb, spin, z, precision="fp64",
+                 nsteps=200, ntotal=0, stream=None):
+    """Finite-temperature G(z) = sum_i w_i G_i(z) (ed_gf_thermal_z): returns
+    (G, weights)."""
+    n = len(sectors)
+    hs = (C.c_void_p * n)(*[s.h for s in sectors])
+    ps = (C.c_void_p * n)(*[p.data_ptr() for p in psis])
+    E = np.ascontiguousarray(np.asarray(energies, dtype=np.float64))
+    zz = np.ascontiguousarray(np.asarray(z, dtype=np.complex128).reshape(-1))
+    G = np.zeros(zz.size, dtype=np.complex128)
+    w = np.zeros(n)
+    _check(lib().ed_gf_thermal_z(n, hs, ps, C.c_void_p(E.ctypes.data), float(beta), float(cutoff),
+                                 int(ntotal), _prec(precision), int(orb), int(spin), int(nsteps),
+                                 C.c_void_p(zz.ctypes.data), int(zz.size),
+                                 C.c_void_p(G.ctypes.data), C.c_void_p(w.ctypes.data),
+                                 C.c_void_p(_stream_ptr(stream))), "ed_gf_thermal_z")
+    return G, w
 
 
 def solve_opts(precision="fp32_polish", gf_precision=None, nmats=512, beta=100.0,

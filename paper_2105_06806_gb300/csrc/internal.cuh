@@ -437,6 +437,7 @@ struct OpRun {
   int k = 0;                        // steps taken
   int stop = 0;                     // 0 converged, 1 breakdown, 2 step limit
   double theta = 0.0;               // lowest Ritz value (ground runs)
+  double theta_max = 0.0;           // highest Ritz value (ground runs)
   double resid_est = 0.0;           // beta_{k+1} |y_k|
   double weight = 0.0;              // ||v0||^2
   std::vector<double> y;            // Ritz vector of theta

@@ -149,6 +149,25 @@ int sturm_below(const std::vector<double> &a, const std::vector<double> &b, int 
   return cnt;
 }
 
+// Largest eigenvalue of T_k (Sturm bisection): the top of the spectrum seen
+// by the run, used to place deflated states above it.
+double highest_ritz(const std::vector<double> &a, const std::vector<double> &b, int k) {
+  double lo = a[0], hi = a[0];
+  for (int i = 0; i < k; ++i) {
+    const double r = (i ? fabs(b[i]) : 0.0) + (i + 1 < k ? fabs(b[i + 1]) : 0.0);
+    lo = std::min(lo, a[i] - r);
+    hi = std::max(hi, a[i] + r);
+  }
+  for (int it = 0; it < 200 && hi - lo > 1e-15 * std::max(1.0, fabs(hi)); ++it) {
+    const double mid = 0.5 * (lo + hi);
+    if (sturm_below(a, b, k, mid) >= k)
+      hi = mid;
+    else
+      lo = mid;
+  }
+  return 0.5 * (lo + hi);
+}
+
 double lowest_ritz(const std::vector<double> &a, const std::vector<double> &b, int k) {
   double lo = a[0], hi = a[0];
   for (int i = 0; i < k; ++i) {
@@ -278,6 +297,7 @@ ed_status ed_op_lanczos(const LinOp<T> &op, const T *v0, int maxit, double tol, 
     }
     if (ground && (stop || k % 4 == 0 || k == maxit)) {
       out->theta = lowest_ritz(A, B, k);
+      out->theta_max = highest_ritz(A, B, k);
       out->y = ritz_vector_host(A, B, k, out->theta);
       out->resid_est = h[1] * fabs(out->y[k - 1]);
       if (!stop && out->resid_est <= tol * std::max(1.0, fabs(out->theta))) {
