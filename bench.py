@@ -534,6 +534,10 @@ def run_matvec_only(args):
     import paper_2105_06806_gb300 as E
     torch.cuda.set_device(0)
     wl = _workload(args.workload)
+    if args.sector:
+        import workloads
+        nup, ndw = (int(x) for x in args.sector.split(","))
+        wl = workloads.Workload(f"{wl.name}_sector_{nup}_{ndw}", wl.model, nup, ndw)
     which = tuple(args.matvec_only.split(","))
     r = time_products(E, wl, torch.cuda.current_stream(), torch.device("cuda", 0),
                       reps=args.steps, which=which, kernel=args.kernel or None)
@@ -781,6 +785,8 @@ def main():
     ap.add_argument("--serving-max-ns", type=int, default=12)
     ap.add_argument("--matvec-only", default="",
                     help="comma list of {blocked,sector}_{fp32,fp64}: time products only")
+    ap.add_argument("--sector", default="",
+                    help="with --matvec-only: another sector 'NUP,NDW' of the workload's model")
     ap.add_argument("--kernel", default="",
                     help="with --matvec-only: pin the block-major kernel "
                          "(tiled, two_pass, elementwise)")
