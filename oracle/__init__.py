@@ -41,6 +41,10 @@ Modules
               as the Boltzmann-weighted sum of per-state chains (App. A), and
               the exact finite-temperature Lehmann sum for pins.
 
+``chi``       Spin, charge and s-wave pair susceptibilities at T = 0 (Sec. 6.8,
+              Eq. KLgf with the bosonic sign) from two Lanczos chains, and the
+              exact Lehmann sum for small sectors.
+
 Every function cites the passage of the paper it follows.  Pins (tests under
 ``tests/test_oracle_*.py``) tie each function to something other than itself:
 binomial dimensions, brute force, closed forms and symmetry invariants.

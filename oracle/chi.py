@@ -1,0 +1,107 @@
+"""Impurity susceptibilities at T = 0 (oracle, test only).
+
+Sec. 6.8, Eq. KLgf with the bosonic sign: for an operator O,
+C_O(z) = <O (z - (H - E0))^-1 O^+> - <O^+ (z + (H - E0))^-1 O>,
+evaluated with a Lanczos chain started from O^+|gs> (first term) and one
+from O|gs> (second term):
+C_O(z) = n+ [(E0 + z - T+)^-1]_00 + n- [(E0 - z - T-)^-1]_00
+(the second term's 1/(z + E_m - E0) = -[(E0 - z) - E_m]^-1 and the bosonic
+"-" in front give "+"); n+- are the squared norms of the start vectors.
+
+Operators (orbital-diagonal):
+* spin   O = S^z_a = (n_{a up} - n_{a dw}) / 2,
+* charge O = n_a = n_{a up} + n_{a dw},
+* pair   O = d_{a dw} d_{a up} (s-wave; O^+ = d^+_{a up} d^+_{a dw}).
+Reading: the spin and charge functions use the connected operator
+O - <O> (for a hermitian O both terms then start from (O - <O>)|gs>, and the
+E_m = E0 component, which would make C(0) singular, is removed).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import fock, gf
+from .lanczos import lanczos_chain
+
+KINDS = ("spin", "charge", "pair")
+
+# sign with which the O|gs> chain enters C_O (bosonic: +, see the module text)
+HOLE_TERM_SIGN = +1.0
+
+
+def diagonal_values(model, nup, ndw, kind, orb):
+    """O of a diagonal operator on every basis state (sector order)."""
+    s = fock.get_sector(model, nup, ndw)
+    nu = np.array([(int(I) >> orb) & 1 for I in s.map_up], dtype=np.float64)
+    nd = np.array([(int(I) >> orb) & 1 for I in s.map_dw], dtype=np.float64)
+    if kind == "spin":
+        return (0.5 * (nu[None, :] - nd[:, None])).reshape(-1)
+    if kind == "charge":
+        return (nu[None, :] + nd[:, None]).reshape(-1)
+    raise ValueError(kind)
+
+
+def start_vectors(model, nup, ndw, psi, kind, orb):
+    """[(vector, (nup', ndw'), create)] for the two terms: create = +1 for
+    O^+|gs>, -1 for O|gs>."""
+    if kind in ("spin", "charge"):
+        o = diagonal_values(model, nup, ndw, kind, orb)
+        avg = float(psi @ (o * psi)) / float(psi @ psi)
+        phi = (o - avg) * psi
+        return [(phi, (nup, ndw), +1), (phi, (nup, ndw), -1)]
+    out = []
+    # O^+ = d^+_{a up} d^+_{a dw}: d^+_{a dw} first, then d^+_{a up}
+    p1, s1 = gf._apply(model, psi, nup, ndw, orb, 1, +1)
+    if p1 is not None:
+        p2, s2 = gf._apply(model, p1, s1[0], s1[1], orb, 0, +1)
+        if p2 is not None:
+            out.append((p2, s2, +1))
+    # O = d_{a dw} d_{a up}: d_{a up} first, then d_{a dw}
+    q1, t1 = gf._apply(model, psi, nup, ndw, orb, 0, -1)
+    if q1 is not None:
+        q2, t2 = gf._apply(model, q1, t1[0], t1[1], orb, 1, -1)
+        if q2 is not None:
+            out.append((q2, t2, -1))
+    return out
+
+
+def chi_z(model, nup, ndw, psi, e0, kind, orb, z, nsteps=200, return_parts=False):
+    """C_O(z) from the two chains."""
+    z = np.asarray(z, dtype=np.complex128)
+    C = np.zeros(z.shape, dtype=np.complex128)
+    parts = {}
+    for phi, (n2u, n2d), create in start_vectors(model, nup, ndw, psi, kind, orb):
+        nrm2 = float(phi @ phi)
+        parts[create] = nrm2
+        if nrm2 == 0.0:
+            continue
+        sec = fock.get_sector(model, n2u, n2d)
+        a, b = lanczos_chain(sec.matvec, phi, nsteps)
+        if create > 0:
+            C += nrm2 * gf.continued_fraction(a, b, e0 + z)
+        else:
+            C += HOLE_TERM_SIGN * nrm2 * gf.continued_fraction(a, b, e0 - z)
+    if return_parts:
+        return C, parts
+    return C
+
+
+def lehmann_chi_z(model, nup, ndw, kind, orb, z):
+    """The exact T = 0 sum of Eq. KLgf (bosonic sign) from dense eigenvectors:
+    sum_m |<m|O^+|0>|^2 / (z - (E_m - E0)) - |<m|O|0>|^2 / (z + (E_m - E0))."""
+    z = np.asarray(z, dtype=np.complex128)
+    s0 = fock.get_sector(model, nup, ndw)
+    E, U = np.linalg.eigh(s0.hamiltonian().toarray())
+    e0, gs = E[0], U[:, 0]
+    C = np.zeros(z.shape, dtype=np.complex128)
+    for phi, (n2u, n2d), create in start_vectors(model, nup, ndw, gs, kind, orb):
+        if not np.any(phi):
+            continue
+        s1 = fock.get_sector(model, n2u, n2d)
+        E1, U1 = np.linalg.eigh(s1.hamiltonian().toarray())
+        w = (U1.T @ phi) ** 2
+        if create > 0:
+            C += (w[None, :] / (z[:, None] - (E1 - e0)[None, :])).sum(1)
+        else:
+            C -= (w[None, :] / (z[:, None] + (E1 - e0)[None, :])).sum(1)
+    return C, e0

@@ -1,0 +1,105 @@
+"""Pins of the susceptibility oracle (oracle/chi.py), no GPU.
+
+* chains = the exact Lehmann sum of Eq. KLgf with the bosonic sign (every
+  kind, chains long enough to be exact);
+* U = 0 closed forms from the one-body eigenvectors (an independent route:
+  the ground state is a Slater determinant per spin):
+  - spin / charge: sum_sigma c_sigma^2 sum_{k occ, l empty} (u_l u_k)^2
+    [1/(z - (e_l - e_k)) - 1/(z + (e_l - e_k))], c = (1/2, -1/2) or (1, 1);
+  - pair: sum_{l, m empty} (u_l u_m)^2 / (z - (e_l + e_m))
+    - sum_{k, q occ} (u_k u_q)^2 / (z - (e_k + e_q));
+* the atom: an empty level e with interaction U has the pair function
+  1 / (z - (2e + U));
+* C(i nu) of a hermitian operator is real, even in nu and negative.
+"""
+import numpy as np
+import pytest
+
+from oracle import chi, fock, lanczos
+from workloads import ImpurityModel, make_model
+
+
+def _asym(model, seed):
+    r = np.random.default_rng(seed)
+    return ImpurityModel(norb=model.norb, nbath=model.nbath, U=model.U, Ust=model.Ust,
+                         Jh=model.Jh, e_imp=model.e_imp + r.normal(0, .2, (2, model.norb)),
+                         e_bath=model.e_bath + r.normal(0, .2, model.e_bath.shape),
+                         v_bath=model.v_bath * r.uniform(.5, 1.5, model.v_bath.shape))
+
+
+Z = np.concatenate([1j * 2 * np.pi * np.arange(1, 30) / 10.0, np.linspace(-4, 4, 33) + 0.25j])
+
+
+@pytest.mark.parametrize("kind", chi.KINDS)
+def test_chains_equal_lehmann_sum(kind):
+    m = _asym(make_model(2, 1, U=2.4, Jh=0.4, seed=41), 41)
+    fock._SECTOR_CACHE.clear()
+    s = fock.Sector(m, 2, 1)
+    r = lanczos.ground_state(s.matvec, s.dim)
+    for orb in range(2):
+        C = chi.chi_z(m, 2, 1, r["psi"], r["e0"], kind, orb, Z, nsteps=64)
+        Cx, e0 = chi.lehmann_chi_z(m, 2, 1, kind, orb, Z)
+        assert abs(e0 - r["e0"]) < 1e-12
+        assert np.abs(C - Cx).max() < 1e-10, (kind, orb)
+
+
+def _one_body(m, spin):
+    h = np.diag(fock.level_energies(m, spin))
+    for a in range(m.norb):
+        for nu in range(m.nbath):
+            i, j = fock.level_of_impurity(m, a), fock.level_of_bath(m, a, nu)
+            h[i, j] = h[j, i] = m.v_bath[spin, a, nu]
+    return np.linalg.eigh(h)
+
+
+@pytest.mark.parametrize("kind", chi.KINDS)
+def test_u0_closed_forms(kind):
+    b = make_model(1, 5, U=0.0, Jh=0.0, e_d=0.1, seed=42)
+    m = _asym(ImpurityModel(norb=1, nbath=5, U=0.0, Ust=0.0, Jh=0.0, e_imp=b.e_imp,
+                            e_bath=b.e_bath, v_bath=b.v_bath), 42)
+    nup, ndw = 3, 2
+    fock._SECTOR_CACHE.clear()
+    s = fock.Sector(m, nup, ndw)
+    r = lanczos.ground_state(s.matvec, s.dim)
+    C = chi.chi_z(m, nup, ndw, r["psi"], r["e0"], kind, 0, Z, nsteps=300)
+    (eu, Uu), (ed, Ud) = _one_body(m, 0), _one_body(m, 1)
+    uu, ud = Uu[0, :], Ud[0, :]
+    want = np.zeros(Z.shape, dtype=np.complex128)
+    if kind in ("spin", "charge"):
+        cs = (0.5, -0.5) if kind == "spin" else (1.0, 1.0)
+        for c, e, u, n in ((cs[0], eu, uu, nup), (cs[1], ed, ud, ndw)):
+            for k in range(n):
+                for l in range(n, len(e)):
+                    d = e[l] - e[k]
+                    want += c * c * (u[l] * u[k]) ** 2 * (1 / (Z - d) - 1 / (Z + d))
+    else:
+        for l in range(nup, len(eu)):
+            for q in range(ndw, len(ed)):
+                want += (uu[l] * ud[q]) ** 2 / (Z - (eu[l] + ed[q]))
+        for k in range(nup):
+            for q in range(ndw):
+                want -= (uu[k] * ud[q]) ** 2 / (Z - (eu[k] + ed[q]))
+    assert np.abs(C - want).max() < 1e-9
+
+
+def test_pair_function_of_the_empty_atom():
+    e, U = 0.7, 1.3
+    m = ImpurityModel(norb=1, nbath=0, U=U, Ust=U, Jh=0.0, e_imp=np.array([e]),
+                      e_bath=np.zeros((1, 0)), v_bath=np.zeros((1, 0)))
+    fock._SECTOR_CACHE.clear()
+    C = chi.chi_z(m, 0, 0, np.array([1.0]), 0.0, "pair", 0, Z, nsteps=4)
+    assert np.abs(C - 1.0 / (Z - (2 * e + U))).max() < 1e-14
+
+
+@pytest.mark.parametrize("kind", ("spin", "charge"))
+def test_hermitian_functions_real_even_negative(kind):
+    m = _asym(make_model(1, 5, U=2.0, e_d=-1.0, seed=43), 43)
+    fock._SECTOR_CACHE.clear()
+    s = fock.Sector(m, 3, 3)
+    r = lanczos.ground_state(s.matvec, s.dim)
+    nu = 2 * np.pi * np.arange(1, 20) / 10.0
+    Cp = chi.chi_z(m, 3, 3, r["psi"], r["e0"], kind, 0, 1j * nu, nsteps=200)
+    Cm = chi.chi_z(m, 3, 3, r["psi"], r["e0"], kind, 0, -1j * nu, nsteps=200)
+    assert np.abs(Cp.imag).max() < 1e-12
+    assert np.abs(Cp - Cm).max() < 1e-12
+    assert np.all(Cp.real < 0)

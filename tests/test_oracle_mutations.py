@@ -304,3 +304,37 @@ def test_unnormalised_weights_are_caught(monkeypatch):
         return [x * 2.0 for x in w], n
     monkeypatch.setattr(thermal, "espace_truncate", bad)
     assert _thermal_mismatch() > 1e-3
+
+
+# ------------------------------------------------------------ susceptibilities
+
+def test_fermionic_sign_in_susceptibility_is_caught(monkeypatch):
+    """The O|gs> chain entered with the fermionic sign: the U = 0 charge
+    function no longer matches its closed form from the one-body
+    eigenvectors."""
+    from oracle import chi
+    from workloads import ImpurityModel
+    m0 = make_model(1, 5, U=0.0, Jh=0.0, e_d=0.1, seed=42)
+    m = ImpurityModel(norb=1, nbath=5, U=0.0, Ust=0.0, Jh=0.0, e_imp=m0.e_imp,
+                      e_bath=m0.e_bath, v_bath=m0.v_bath)
+    fock._SECTOR_CACHE.clear()
+    s = fock.Sector(m, 3, 2)
+    r = lanczos.ground_state(s.matvec, s.dim)
+    z = 1j * 2 * np.pi * np.arange(1, 20) / 10.0
+    want = np.zeros(z.shape, dtype=np.complex128)
+    for spin, n in ((0, 3), (1, 2)):
+        h = np.diag(fock.level_energies(m, spin))
+        for nu in range(5):
+            h[0, 1 + nu] = h[1 + nu, 0] = m.v_bath[spin, 0, nu]
+        e, U = np.linalg.eigh(h)
+        u = U[0, :]
+        for k in range(n):
+            for l in range(n, 6):
+                d = e[l] - e[k]
+                want += (u[l] * u[k]) ** 2 * (1 / (z - d) - 1 / (z + d))
+
+    def err():
+        return np.abs(chi.chi_z(m, 3, 2, r["psi"], r["e0"], "charge", 0, z, nsteps=300) - want).max()
+    assert err() < 1e-9
+    monkeypatch.setattr(chi, "HOLE_TERM_SIGN", -1.0)
+    assert err() > 1e-3
