@@ -316,6 +316,22 @@ ed_status ed_sigma(const ed_model *model, int32_t orb, int32_t spin, const doubl
 ed_status ed_observables(ed_sector s, ed_precision prec, const void *d_psi, int64_t n,
                          double *host_out, void *stream);
 
+/* Impurity susceptibility at T = 0 (Sec. 6.8: Eq. KLgf with the bosonic sign),
+ *   C_O(z) = <O (z - (H - E0))^-1 O^+> - <O^+ (z + (H - E0))^-1 O>
+ *          = n+ [(e0 + z - T+)^-1]_00 + n- [(e0 - z - T-)^-1]_00,
+ * T+- the tridiagonal matrices of `nsteps`-step chains started from O^+ psi
+ * and O psi, n+- their squared norms.  kind: ED_CHI_SPIN, O = S^z_orb =
+ * (n_{orb up} - n_{orb dw})/2, and ED_CHI_CHARGE, O = n_orb, both as the
+ * connected O - <O> (one chain serves both terms); ED_CHI_PAIR, O =
+ * d_{orb dw} d_{orb up} (chains on the (N_up+1, N_dw+1) and (N_up-1, N_dw-1)
+ * sectors).  d_psi, prec, host_z / host_C (nz complex values each) as for
+ * ed_gf_lanczos_z; host_w (nullable) receives n+ and n-.  Synchronises
+ * `stream`. */
+enum { ED_CHI_SPIN = 0, ED_CHI_CHARGE = 1, ED_CHI_PAIR = 2 };
+ed_status ed_chi_z(ed_sector s, ed_precision prec, const void *d_psi, double e0, int32_t kind,
+                   int32_t orb, int32_t nsteps, const double *host_z, int32_t nz, double *host_C,
+                   double *host_w, void *stream);
+
 /* ---------------------------------------------------------------- several states, finite T
  * The nstates lowest eigenpairs of the sector (the states of the eigenspace
  * list, Sec. 6.2; the paper takes them from P-ARPACK, Sec. 5): Lanczos on

@@ -31,6 +31,7 @@ EXPORTED = [
     "ed_sector_permute", "ed_lanczos_ground", "ed_gf_lanczos", "ed_gf_lanczos_z", "ed_sigma",
     "ed_observables", "ed_solve", "ed_eph_matvec", "ed_eph_lanczos_ground",
     "ed_eph_gf_lanczos_z", "ed_lanczos_states", "ed_espace_truncate", "ed_gf_thermal_z",
+    "ed_chi_z",
     "ed_server_create", "ed_submit", "ed_poll", "ed_wait", "ed_server_destroy",
     "ed_server_inject_alloc_failure", "ed_batch_stats", "ed_residual_noalloc", "ed_status_string",
     "ed_last_error",
@@ -189,6 +190,7 @@ def lib():
                                    C.POINTER(i32)],
             "ed_gf_thermal_z": [i32, vp, vp, vp, C.c_double, C.c_double, i32, C.c_int, i32, i32,
                                 i32, vp, i32, vp, vp, vp],
+            "ed_chi_z": [vp, C.c_int, vp, C.c_double, i32, i32, i32, vp, i32, vp, vp, vp],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -500,6 +502,22 @@ def eph_gf_lanczos_z(sector: Sector, ph, psi, e0, orb, spin, z, precision="fp64"
                                      C.c_void_p(G.ctypes.data), C.byref(info),
                                      C.c_void_p(_stream_ptr(stream))), "ed_eph_gf_lanczos_z")
     return G, {k: getattr(info, k) for k, _ in info._fields_}
+
+
+CHI_KINDS = {"spin": 0, "charge": 1, "pair": 2}
+
+
+def chi_z(sector: Sector, psi, e0, kind, orb, z, precision="fp64", nsteps=200, stream=None):
+    """Impurity susceptibility C_O(z) at T = 0 (ed_chi_z): kind "spin"
+    (S^z), "charge" (n) or "pair" (d_dw d_up); returns (C, (n+, n-))."""
+    zz = np.ascontiguousarray(np.asarray(z, dtype=np.complex128).reshape(-1))
+    out = np.zeros(zz.size, dtype=np.complex128)
+    w = np.zeros(2)
+    _check(lib().ed_chi_z(sector.h, _prec(precision), C.c_void_p(psi.data_ptr()), float(e0),
+                          CHI_KINDS[kind], int(orb), int(nsteps), C.c_void_p(zz.ctypes.data),
+                          int(zz.size), C.c_void_p(out.ctypes.data), C.c_void_p(w.ctypes.data),
+                          C.c_void_p(_stream_ptr(stream))), "ed_chi_z")
+    return out, (float(w[0]), float(w[1]))
 
 
 def lanczos_states(sector: Sector, nstates, precision="fp64", max_iter=0, tol=0.0,

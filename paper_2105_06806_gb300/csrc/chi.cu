@@ -1,0 +1,242 @@
+// Impurity susceptibilities at T = 0 (Sec. 6.8: Eq. KLgf with the bosonic
+// sign), C_O(z) = n+ [(E0 + z - T+)^-1]_00 + n- [(E0 - z - T-)^-1]_00 for
+// the spin (S^z), charge (n) and s-wave pair (d_dw d_up) operators of one
+// orbital.
+//
+// Spin and charge are diagonal in the basis: one pass forms <O> (FP64
+// partials of O |psi|^2 and |psi|^2 over the impurity masks of each
+// element), one pass writes (O - <O>) psi into the block-major order of the
+// same sector, and one chain serves both terms.  The pair operator changes
+// both electron numbers: two c^+ (or c) applications through the Green's
+// function's gather kernel with a layout permutation between them, one chain
+// per term.  The chains run through the operator-generic Lanczos driver and
+// the continued fractions through the Green's function's kernel.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "internal.cuh"
+
+namespace {
+
+constexpr int CHI_THREADS = 256;
+constexpr int CHI_PARTS = 1024;
+
+struct OTable {
+  double v[1 << ED_MAX_NORB][1 << ED_MAX_NORB];  // O on impurity masks (m_up, m_dw)
+};
+
+OTable make_table(int norb, int kind, int orb) {
+  OTable t;
+  memset(&t, 0, sizeof(t));
+  for (int mu = 0; mu < (1 << norb); ++mu)
+    for (int md = 0; md < (1 << norb); ++md) {
+      const double nu = (mu >> orb) & 1, nd = (md >> orb) & 1;
+      t.v[mu][md] = kind == ED_CHI_SPIN ? 0.5 * (nu - nd) : nu + nd;
+    }
+  return t;
+}
+
+// parts[cta] = sum O psi^2, parts[CHI_PARTS + cta] = sum psi^2 (sector order)
+template <typename T>
+__global__ void __launch_bounds__(CHI_THREADS) k_chi_expect(const T *psi, int64_t dup, int64_t n,
+                                                            const uint8_t *mup,
+                                                            const uint8_t *mdw, OTable ot,
+                                                            double *parts) {
+  __shared__ double red[2][CHI_THREADS / 32];
+  double a = 0.0, b = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = i / dup, c = i - r * dup;
+    const double x = (double)psi[i];
+    a += ot.v[mup[c]][mdw[r]] * x * x;
+    b += x * x;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_down_sync(0xffffffffu, a, o);
+    b += __shfl_down_sync(0xffffffffu, b, o);
+  }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) {
+    red[0][wid] = a;
+    red[1][wid] = b;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double sa = 0.0, sb = 0.0;
+    for (int k = 0; k < CHI_THREADS / 32; ++k) {
+      sa += red[0][k];
+      sb += red[1][k];
+    }
+    parts[blockIdx.x] = sa;
+    parts[CHI_PARTS + blockIdx.x] = sb;
+  }
+}
+
+// avg[0] = sum of the O psi^2 partials / sum of the psi^2 partials (fixed order)
+__global__ void k_chi_avg(const double *parts, int np, double *avg) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double a = 0.0, b = 0.0;
+  for (int k = 0; k < np; ++k) {
+    a += parts[k];
+    b += parts[CHI_PARTS + k];
+  }
+  avg[0] = b > 0.0 ? a / b : 0.0;
+}
+
+// phi (padded block-major) = (O - <O>) psi (sector order), padding zero
+template <typename Ti, typename To>
+__global__ void k_chi_apply(const Ti *psi, To *phi, const int32_t *pidx_dw, const int32_t *pidx_up,
+                            const int32_t *padinv, const uint8_t *bk_mup, const uint8_t *bk_mdw,
+                            int64_t dup, int64_t stride, int64_t ddw, OTable ot,
+                            const double *avg) {
+  const double o0 = avg[0];
+  for (int64_t r = blockIdx.y; r < ddw; r += gridDim.y) {
+    const Ti *src = psi + (int64_t)pidx_dw[r] * dup;
+    To *dst = phi + r * stride;
+    const int md = bk_mdw[r];
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < stride;
+         c += (int64_t)gridDim.x * blockDim.x) {
+      const int32_t cb = padinv[c];
+      dst[c] = cb < 0 ? To(0) : (To)((ot.v[bk_mup[cb]][md] - o0) * (double)src[pidx_up[cb]]);
+    }
+  }
+}
+
+struct Mem {
+  void *p = nullptr;
+  cudaStream_t cs = nullptr;
+  ~Mem() {
+    if (p) ed_dfree(p, cs);
+  }
+  ed_status alloc(size_t bytes, cudaStream_t st, const char *what) {
+    cs = st;
+    return ed_dmalloc(&p, std::max<size_t>(bytes, 256), st, what);
+  }
+};
+
+template <typename T>
+LinOp<T> plain_op(ed_sector s) {
+  LinOp<T> op;
+  op.n = s->bdim;
+  op.apply = [s](const T *v, T *w, cudaStream_t cs) {
+    return ed_launch_hv<T>(s, ed_hv_tables<T>(s, 1), HV_PLAIN, v, w, nullptr, nullptr, nullptr,
+                           nullptr, nullptr, cs);
+  };
+  return op;
+}
+
+// chain on sector nb from phi (block-major), then C += sgn-term (see ed_chi_z)
+template <typename T>
+ed_status chain_and_cfrac(ed_sector nb, const T *phi, int nsteps, double e0, const double2 *dz,
+                          int nz, bool both, int which, double2 *dC, LanczosState *st,
+                          double *weight, cudaStream_t cs) {
+  ED_TRY(ed_build_items(nb, 1, (int)sizeof(T)));
+  OpRun run;
+  ED_TRY(ed_op_lanczos<T>(plain_op<T>(nb), phi, nsteps, 0.0, false, &run, st, nullptr, cs));
+  *weight = run.weight;
+  if (run.weight <= 0.0 || run.k <= 0) return ED_OK;
+  // n+ [(e0 + z - T)^-1]_00 (sgn +1) and + n- [(e0 - z - T)^-1]_00: the
+  // launcher adds sgn * weight * [(e0 + sgn z - T)^-1]_00, so the second
+  // term takes sgn = -1 with weight -n-
+  if (both || which > 0) ED_TRY(ed_cfrac_z_launch(st, run.weight, e0, dz, nz, +1, dC, cs));
+  if (both || which < 0) ED_TRY(ed_cfrac_z_launch(st, -run.weight, e0, dz, nz, -1, dC, cs));
+  return ED_OK;
+}
+
+template <typename Ti, typename To>
+ed_status chi_impl(ed_sector s, ed_precision prec, const Ti *psi, double e0, int kind, int orb,
+                   int nsteps, const double2 *dz, int nz, double2 *dC, LanczosState *st,
+                   double *w, cudaStream_t cs) {
+  if (kind == ED_CHI_SPIN || kind == ED_CHI_CHARGE) {
+    const OTable ot = make_table(s->mp.norb, kind, orb);
+    const int64_t n = s->dim, bn = s->bdim, dup = s->sp[0].dim, ddw = s->sp[1].dim;
+    Mem scratch, phi;
+    ED_TRY(scratch.alloc((2 * CHI_PARTS + 8) * sizeof(double), cs, "susceptibility partials"));
+    ED_TRY(phi.alloc((size_t)bn * sizeof(To), cs, "susceptibility start vector"));
+    double *parts = (double *)scratch.p, *avg = parts + 2 * CHI_PARTS;
+    const unsigned g = (unsigned)std::max<int64_t>(
+        1, std::min<int64_t>((n + 4 * CHI_THREADS - 1) / (4 * CHI_THREADS), CHI_PARTS));
+    k_chi_expect<Ti><<<g, CHI_THREADS, 0, cs>>>(psi, dup, n, s->sp[0].imask, s->sp[1].imask, ot,
+                                                parts);
+    ED_LAUNCHED(1);
+    k_chi_avg<<<1, 32, 0, cs>>>(parts, (int)g, avg);
+    ED_LAUNCHED(1);
+    const dim3 grid((unsigned)std::max<int64_t>(1, std::min<int64_t>((s->bstride + 255) / 256, 64)),
+                    (unsigned)std::max<int64_t>(1, std::min<int64_t>(ddw, 65535)));
+    k_chi_apply<Ti, To><<<grid, 256, 0, cs>>>(psi, (To *)phi.p, s->bi[1].pidx, s->bi[0].pidx,
+                                              s->padinv, s->bk[0].imask, s->bk[1].imask, dup,
+                                              s->bstride, ddw, ot, avg);
+    ED_LAUNCHED(1);
+    double wt = 0.0;
+    ED_TRY(chain_and_cfrac<To>(s, (const To *)phi.p, nsteps, e0, dz, nz, true, 0, dC, st, &wt, cs));
+    w[0] = w[1] = wt;
+    return ED_OK;
+  }
+  // pair: O^+ = d^+_up d^+_dw (d^+_dw first), O = d_dw d_up (d_up first)
+  const ed_precision sp = sizeof(To) == 8 ? ED_FP64 : ED_FP32;
+  for (int term = +1; term >= -1; term -= 2) {
+    const int first = term > 0 ? 1 : 0, second = term > 0 ? 0 : 1;
+    ed_sector s1 = nullptr, s2 = nullptr;
+    ED_TRY(ed_neighbor_sector(s, first, term, cs, &s1));
+    if (!s1 || s1->dim == 0) continue;
+    ED_TRY(ed_neighbor_sector(s1, second, term, cs, &s2));
+    if (!s2 || s2->dim == 0) continue;
+    Mem a, b, c;
+    ED_TRY(a.alloc((size_t)s1->bdim * sizeof(To), cs, "pair operator"));
+    ED_TRY(b.alloc((size_t)s1->dim * sizeof(To), cs, "pair operator"));
+    ED_TRY(c.alloc((size_t)s2->bdim * sizeof(To), cs, "pair operator"));
+    ED_TRY((ed_apply_op_launch<Ti, To>(s, s1, psi, (To *)a.p, orb, first, term, cs)));
+    ED_TRY(ed_permute_vec(s1, sp, false, a.p, b.p, cs));
+    ED_TRY((ed_apply_op_launch<To, To>(s1, s2, (const To *)b.p, (To *)c.p, orb, second, term, cs)));
+    double wt = 0.0;
+    ED_TRY(chain_and_cfrac<To>(s2, (const To *)c.p, nsteps, e0, dz, nz, false, term, dC, st, &wt,
+                               cs));
+    w[term > 0 ? 0 : 1] = wt;
+  }
+  (void)prec;
+  return ED_OK;
+}
+
+}  // namespace
+
+extern "C" ed_status ed_chi_z(ed_sector s, ed_precision prec, const void *d_psi, double e0,
+                              int32_t kind, int32_t orb, int32_t nsteps, const double *host_z,
+                              int32_t nz, double *host_C, double *host_w, void *stream) {
+  if (!s || !d_psi || !host_C || nz < 0 || (nz > 0 && !host_z)) return ED_ERR_ARG;
+  if (kind != ED_CHI_SPIN && kind != ED_CHI_CHARGE && kind != ED_CHI_PAIR) return ED_ERR_ARG;
+  if (orb < 0 || orb >= s->mp.norb) return ED_ERR_ARG;
+  if (prec != ED_FP64 && prec != ED_FP32 && prec != ED_FP32_POLISH) return ED_ERR_ARG;
+  if (nsteps <= 0) nsteps = 200;
+  if (nsteps > ED_MAX_LANCZOS) return ED_ERR_ARG;
+  cudaStream_t cs = (cudaStream_t)stream;
+  Mem buf;
+  const size_t zb = (size_t)std::max(nz, 1) * sizeof(double2);
+  ED_TRY(buf.alloc(2 * zb + ((sizeof(LanczosState) + 255) & ~(size_t)255), cs, "susceptibility"));
+  double2 *dz = (double2 *)buf.p, *dC = (double2 *)((char *)buf.p + zb);
+  LanczosState *st = (LanczosState *)((char *)buf.p + 2 * zb);
+  if (nz > 0) {
+    ED_TRY_CUDA(cudaMemcpyAsync(dz, host_z, nz * sizeof(double2), cudaMemcpyHostToDevice, cs));
+    ED_TRY_CUDA(cudaMemsetAsync(dC, 0, nz * sizeof(double2), cs));
+  }
+  double w[2] = {0.0, 0.0};
+  if (prec == ED_FP64)
+    ED_TRY((chi_impl<double, double>(s, prec, (const double *)d_psi, e0, kind, orb, nsteps, dz, nz,
+                                     dC, st, w, cs)));
+  else if (prec == ED_FP32)
+    ED_TRY((chi_impl<float, float>(s, prec, (const float *)d_psi, e0, kind, orb, nsteps, dz, nz,
+                                   dC, st, w, cs)));
+  else
+    ED_TRY((chi_impl<double, float>(s, prec, (const double *)d_psi, e0, kind, orb, nsteps, dz, nz,
+                                    dC, st, w, cs)));
+  if (nz > 0)
+    ED_TRY_CUDA(cudaMemcpyAsync(host_C, dC, nz * sizeof(double2), cudaMemcpyDeviceToHost, cs));
+  ED_TRY_CUDA(cudaStreamSynchronize(cs));
+  if (host_w) {
+    host_w[0] = w[0];
+    host_w[1] = w[1];
+  }
+  return ED_OK;
+}

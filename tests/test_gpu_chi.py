@@ -1,0 +1,68 @@
+"""f1 susceptibilities on the GPU (ed_chi_z): spin, charge and s-wave pair
+functions against the oracle (oracle/chi.py, pinned by
+tests/test_oracle_chi.py): the same two-chain algorithm, FP64 <= 1e-8 on the
+Matsubara axis and the real axis at eta = 0.5; FP32 chains on the polished
+state <= 3e-5; the empty-atom pair function 1/(z - (2e + U))."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import chi, fock, lanczos
+from workloads import ImpurityModel, make_model, with_exchange
+
+pytestmark = pytest.mark.gpu
+
+
+def _asym(model, seed):
+    r = np.random.default_rng(seed)
+    return ImpurityModel(norb=model.norb, nbath=model.nbath, U=model.U, Ust=model.Ust,
+                         Jh=model.Jh, e_imp=model.e_imp + r.normal(0, .2, (2, model.norb)),
+                         e_bath=model.e_bath + r.normal(0, .2, model.e_bath.shape),
+                         v_bath=model.v_bath * r.uniform(.5, 1.5, model.v_bath.shape),
+                         Jx=model.Jx, Jp=model.Jp)
+
+
+CASES = {
+    "norb1_ns8": (_asym(make_model(1, 7, U=2.0, e_d=-1.0, seed=51), 51), 4, 4),
+    "norb2_ns8": (_asym(make_model(2, 3, U=2.5, Jh=0.4, seed=52), 52), 4, 3),
+    "norb2_ns10": (_asym(make_model(2, 4, U=3.0, Jh=0.5, seed=53), 53), 5, 5),
+    "kanamori_ns9": (_asym(with_exchange(make_model(3, 2, U=2.6, Jh=0.4, seed=54)), 54), 4, 5),
+}
+Z = np.concatenate([1j * 2 * np.pi * np.arange(1, 40) / 20.0, np.linspace(-6, 6, 61) + 0.5j])
+
+
+@pytest.mark.parametrize("case", sorted(CASES))
+@pytest.mark.parametrize("kind", chi.KINDS)
+def test_chi_against_oracle(ed, case, kind):
+    m, nup, ndw = CASES[case]
+    fock._SECTOR_CACHE.clear()
+    ref = fock.Sector(m, nup, ndw)
+    ro = lanczos.ground_state(ref.matvec, ref.dim)
+    s = ed.Sector(m, nup, ndw)
+    psi = torch.empty(s.dim, dtype=torch.float64, device="cuda")
+    r = ed.lanczos_ground(s, "fp64", psi=psi)
+    for orb in range(m.norb):
+        Co, parts = chi.chi_z(m, nup, ndw, ro["psi"], ro["e0"], kind, orb, Z, nsteps=150,
+                              return_parts=True)
+        C, w = ed.chi_z(s, psi, r["e0"], kind, orb, Z, "fp64", nsteps=150)
+        assert np.abs(C - Co).max() <= 1e-8 * max(1.0, np.abs(Co).max()), (orb, kind)
+        assert abs(w[0] - parts.get(1, 0.0)) < 1e-10 and abs(w[1] - parts.get(-1, 0.0)) < 1e-10
+    # FP32 chains from the polished state
+    psi2 = torch.empty(s.dim, dtype=torch.float64, device="cuda")
+    r2 = ed.lanczos_ground(s, "fp32_polish", psi=psi2)
+    Co = chi.chi_z(m, nup, ndw, ro["psi"], ro["e0"], kind, 0, Z, nsteps=150)
+    C2, _ = ed.chi_z(s, psi2, r2["e0"], kind, 0, Z, "fp32_polish", nsteps=150)
+    assert np.abs(C2 - Co).max() <= 3e-5 * max(1.0, np.abs(Co).max())
+    s.free()
+
+
+def test_pair_function_of_the_empty_atom(ed):
+    e, U = 0.7, 1.3
+    m = ImpurityModel(norb=1, nbath=0, U=U, Ust=U, Jh=0.0, e_imp=np.array([e]),
+                      e_bath=np.zeros((1, 0)), v_bath=np.zeros((1, 0)))
+    s = ed.Sector(m, 0, 0)
+    psi = torch.ones(1, dtype=torch.float64, device="cuda")
+    C, w = ed.chi_z(s, psi, 0.0, "pair", 0, Z, "fp64", nsteps=4)
+    assert np.abs(C - 1.0 / (Z - (2 * e + U))).max() < 1e-14
+    assert w == (1.0, 0.0)
+    s.free()
