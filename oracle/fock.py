@@ -297,6 +297,30 @@ class Sector:
         return sp.csr_matrix(H)
 
 
+def orbital_occupations(model, I: int) -> tuple:
+    """Per-orbital electron numbers of one spin string: the impurity level of
+    orbital alpha plus its Nbath bath levels (the per-orbital quantum numbers
+    of Sec. 2.2, N_ud = Norb, conserved by a diagonal H^loc, a normal bath and
+    the density-density interaction)."""
+    out = []
+    for a in range(model.norb):
+        n = (I >> level_of_impurity(model, a)) & 1
+        for nu in range(model.nbath):
+            n += (I >> level_of_bath(model, a, nu)) & 1
+        out.append(n)
+    return tuple(out)
+
+
+def orbital_sector_indices(model, nup, ndw, nup_orb, ndw_orb) -> np.ndarray:
+    """Sector indices (i_up + i_dw D_up) of the states of S[nup, ndw] whose
+    per-orbital occupations are nup_orb (up) and ndw_orb (dw): the finer
+    sector of Sec. 2.2."""
+    s = get_sector(model, nup, ndw)
+    iu = [i for i, I in enumerate(s.map_up) if orbital_occupations(model, int(I)) == tuple(nup_orb)]
+    idw = [i for i, I in enumerate(s.map_dw) if orbital_occupations(model, int(I)) == tuple(ndw_orb)]
+    return np.array([u + d * s.dim_up for d in idw for u in iu], dtype=np.int64)
+
+
 _SECTOR_CACHE: dict = {}
 
 
