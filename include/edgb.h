@@ -316,6 +316,24 @@ ed_status ed_sigma(const ed_model *model, int32_t orb, int32_t spin, const doubl
 ed_status ed_observables(ed_sector s, ed_precision prec, const void *d_psi, int64_t n,
                          double *host_out, void *stream);
 
+/* Per-orbital sectors (Sec. 2.2, N_ud = Norb): with J_X = J_P = 0, a diagonal
+ * H^loc and a normal bath the electron number of every orbital group (the
+ * impurity level and its bath levels) is conserved per spin, and S[N_up,
+ * N_dw] splits into finer sectors labelled by the per-orbital occupations
+ * nup_orb[alpha], ndw_orb[alpha] (sums N_up, N_dw).  ed_orbital_sector_dims
+ * gives the finer sector's D_up, D_dw (ED_ERR_ARG when no state of s has
+ * those occupations).  ed_lanczos_ground_orbital finds its ground state: the
+ * product kernels run over that block pair's work items only, on vectors of
+ * the finer sector alone, through the operator-generic Lanczos driver
+ * (options and result as ed_lanczos_ground); d_psi (nullable) receives psi
+ * as a sector-order vector of s (D elements, zero outside the finer
+ * sector).  ED_ERR_UNSUPPORTED when J_X or J_P != 0. */
+ed_status ed_orbital_sector_dims(ed_sector s, const int32_t *nup_orb, const int32_t *ndw_orb,
+                                 int64_t *dim_up, int64_t *dim_dw);
+ed_status ed_lanczos_ground_orbital(ed_sector s, const int32_t *nup_orb, const int32_t *ndw_orb,
+                                    const ed_lanczos_opts *opts, ed_lanczos_result *res,
+                                    void *d_psi, void *stream);
+
 /* Impurity susceptibility at T = 0 (Sec. 6.8: Eq. KLgf with the bosonic sign),
  *   C_O(z) = <O (z - (H - E0))^-1 O^+> - <O^+ (z + (H - E0))^-1 O>
  *          = n+ [(e0 + z - T+)^-1]_00 + n- [(e0 - z - T-)^-1]_00,

@@ -31,7 +31,7 @@ EXPORTED = [
     "ed_sector_permute", "ed_lanczos_ground", "ed_gf_lanczos", "ed_gf_lanczos_z", "ed_sigma",
     "ed_observables", "ed_solve", "ed_eph_matvec", "ed_eph_lanczos_ground",
     "ed_eph_gf_lanczos_z", "ed_lanczos_states", "ed_espace_truncate", "ed_gf_thermal_z",
-    "ed_chi_z",
+    "ed_chi_z", "ed_orbital_sector_dims", "ed_lanczos_ground_orbital",
     "ed_server_create", "ed_submit", "ed_poll", "ed_wait", "ed_server_destroy",
     "ed_server_inject_alloc_failure", "ed_batch_stats", "ed_residual_noalloc", "ed_status_string",
     "ed_last_error",
@@ -191,6 +191,9 @@ def lib():
             "ed_gf_thermal_z": [i32, vp, vp, vp, C.c_double, C.c_double, i32, C.c_int, i32, i32,
                                 i32, vp, i32, vp, vp, vp],
             "ed_chi_z": [vp, C.c_int, vp, C.c_double, i32, i32, i32, vp, i32, vp, vp, vp],
+            "ed_orbital_sector_dims": [vp, vp, vp, C.POINTER(i64), C.POINTER(i64)],
+            "ed_lanczos_ground_orbital": [vp, vp, vp, C.POINTER(ed_lanczos_opts),
+                                          C.POINTER(ed_lanczos_result), vp, vp],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -502,6 +505,35 @@ def eph_gf_lanczos_z(sector: Sector, ph, psi, e0, orb, spin, z, precision="fp64"
                                      C.c_void_p(G.ctypes.data), C.byref(info),
                                      C.c_void_p(_stream_ptr(stream))), "ed_eph_gf_lanczos_z")
     return G, {k: getattr(info, k) for k, _ in info._fields_}
+
+
+def _occ(t):
+    a = np.ascontiguousarray(np.asarray(t, dtype=np.int32))
+    return a, C.c_void_p(a.ctypes.data)
+
+
+def orbital_sector_dims(sector: Sector, nup_orb, ndw_orb):
+    """(D_up, D_dw) of the finer sector with these per-orbital occupations."""
+    (a, pa), (b, pb) = _occ(nup_orb), _occ(ndw_orb)
+    du, dd = C.c_int64(), C.c_int64()
+    _check(lib().ed_orbital_sector_dims(sector.h, pa, pb, C.byref(du), C.byref(dd)),
+           "ed_orbital_sector_dims")
+    return int(du.value), int(dd.value)
+
+
+def lanczos_ground_orbital(sector: Sector, nup_orb, ndw_orb, precision="fp64", max_iter=0,
+                           tol=0.0, seed=0x5EED, polish_steps=0, psi=None, stream=None):
+    """Ground state of a finer (per-orbital) sector (ed_lanczos_ground_orbital);
+    psi (optional, D elements) receives it in the sector order of `sector`."""
+    (a, pa), (b, pb) = _occ(nup_orb), _occ(ndw_orb)
+    o = ed_lanczos_opts(_prec(precision), int(max_iter), float(tol), int(seed),
+                        int(polish_steps), 1, 0, 0)
+    r = ed_lanczos_result()
+    _check(lib().ed_lanczos_ground_orbital(sector.h, pa, pb, C.byref(o), C.byref(r),
+                                           C.c_void_p(psi.data_ptr() if psi is not None else 0),
+                                           C.c_void_p(_stream_ptr(stream))),
+           "ed_lanczos_ground_orbital")
+    return r.as_dict()
 
 
 CHI_KINDS = {"spin": 0, "charge": 1, "pair": 2}
