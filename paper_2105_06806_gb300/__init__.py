@@ -341,6 +341,17 @@ def _prec(p):
     return PRECISIONS[p] if isinstance(p, str) else int(p)
 
 
+def _psi_ptr(psi, precision):
+    """Device pointer of a ground state handed to a chain or an observable:
+    a contiguous CUDA tensor, float64 for fp64 / fp32_polish, float32 for
+    fp32 (the layout the C-ABI reads)."""
+    import torch
+    want = torch.float32 if _prec(precision) == PRECISIONS["fp32"] else torch.float64
+    if not (psi.is_cuda and psi.is_contiguous() and psi.dtype == want):
+        raise ValueError(f"psi must be a contiguous CUDA {want} tensor for {precision!r}")
+    return C.c_void_p(psi.data_ptr())
+
+
 def matvec(sector: Sector, v, w, precision="fp64", stream=None):
     """w = H v for device tensors (float64 for fp64, float32 otherwise)."""
     if v.numel() != w.numel():
@@ -416,7 +427,7 @@ def gf_lanczos(sector: Sector, psi, e0, orb, spin, precision="fp64", nsteps=200,
                nmats=512, stream=None):
     G = np.zeros(2 * nmats, dtype=np.float64)
     info = ed_gf_info()
-    _check(lib().ed_gf_lanczos(sector.h, _prec(precision), C.c_void_p(psi.data_ptr()),
+    _check(lib().ed_gf_lanczos(sector.h, _prec(precision), _psi_ptr(psi, precision),
                                float(e0), int(orb), int(spin), int(nsteps), float(beta),
                                int(nmats), G.ctypes.data, C.byref(info),
                                C.c_void_p(_stream_ptr(stream))), "ed_gf_lanczos")
@@ -430,7 +441,7 @@ def gf_lanczos_z(sector: Sector, psi, e0, orb, spin, z, precision="fp64", nsteps
     zz = np.ascontiguousarray(np.asarray(z, dtype=np.complex128).reshape(-1))
     G = np.zeros(zz.size, dtype=np.complex128)
     info = ed_gf_info()
-    _check(lib().ed_gf_lanczos_z(sector.h, _prec(precision), C.c_void_p(psi.data_ptr()),
+    _check(lib().ed_gf_lanczos_z(sector.h, _prec(precision), _psi_ptr(psi, precision),
                                  float(e0), int(orb), int(spin), int(nsteps),
                                  C.c_void_p(zz.ctypes.data), int(zz.size),
                                  C.c_void_p(G.ctypes.data), C.byref(info),
@@ -458,7 +469,7 @@ def observables(sector: Sector, psi, precision="fp64", stream=None):
     nn[2][2][norb][norb], e_int, norm."""
     no = sector.info["norb"]
     out = np.zeros(2 * no + 4 * no * no + 2, dtype=np.float64)
-    _check(lib().ed_observables(sector.h, _prec(precision), C.c_void_p(psi.data_ptr()),
+    _check(lib().ed_observables(sector.h, _prec(precision), _psi_ptr(psi, precision),
                                 int(psi.numel()), C.c_void_p(out.ctypes.data),
                                 C.c_void_p(_stream_ptr(stream))), "ed_observables")
     return {"dens": out[:2 * no].reshape(2, no).copy(),
@@ -545,7 +556,7 @@ def chi_z(sector: Sector, psi, e0, kind, orb, z, precision="fp64", nsteps=200, s
     zz = np.ascontiguousarray(np.asarray(z, dtype=np.complex128).reshape(-1))
     out = np.zeros(zz.size, dtype=np.complex128)
     w = np.zeros(2)
-    _check(lib().ed_chi_z(sector.h, _prec(precision), C.c_void_p(psi.data_ptr()), float(e0),
+    _check(lib().ed_chi_z(sector.h, _prec(precision), _psi_ptr(psi, precision), float(e0),
                           CHI_KINDS[kind], int(orb), int(nsteps), C.c_void_p(zz.ctypes.data),
                           int(zz.size), C.c_void_p(out.ctypes.data), C.c_void_p(w.ctypes.data),
                           C.c_void_p(_stream_ptr(stream))), "ed_chi_z")
@@ -594,7 +605,7 @@ def gf_thermal_z(sectors, psis, energies, beta, cutoff, orb, spin, z, precision=
     (G, weights)."""
     n = len(sectors)
     hs = (C.c_void_p * n)(*[s.h for s in sectors])
-    ps = (C.c_void_p * n)(*[p.data_ptr() for p in psis])
+    ps = (C.c_void_p * n)(*[_psi_ptr(p, precision).value for p in psis])
     E = np.ascontiguousarray(np.asarray(energies, dtype=np.float64))
     zz = np.ascontiguousarray(np.asarray(z, dtype=np.complex128).reshape(-1))
     G = np.zeros(zz.size, dtype=np.complex128)

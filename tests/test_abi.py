@@ -81,3 +81,13 @@ def test_struct_layout_matches_c(tmp_path):
             assert C.sizeof(cls) == int(v), s
         else:
             assert getattr(cls, f).offset == int(v), (s, f)
+
+
+def test_psi_dtype_is_checked_before_the_call():
+    """A ground state of the wrong type or device is refused by the binding
+    before any pointer reaches the library (no GPU needed)."""
+    torch = pytest.importorskip("torch")
+    import paper_2105_06806_gb300 as ed
+    for prec in ("fp64", "fp32_polish", "fp32"):
+        with pytest.raises(ValueError):
+            ed._psi_ptr(torch.zeros(4, dtype=torch.float64), prec)   # host tensor
