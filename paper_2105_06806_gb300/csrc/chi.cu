@@ -15,6 +15,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <type_traits>
 #include <vector>
 
 #include "internal.cuh"
@@ -117,27 +118,32 @@ struct Mem {
   }
 };
 
-template <typename T>
-LinOp<T> plain_op(ed_sector s) {
-  LinOp<T> op;
-  op.n = s->bdim;
-  op.apply = [s](const T *v, T *w, cudaStream_t cs) {
-    return ed_launch_hv<T>(s, ed_hv_tables<T>(s, 1), HV_PLAIN, v, w, nullptr, nullptr, nullptr,
-                           nullptr, nullptr, cs);
-  };
-  return op;
-}
-
 // chain on sector nb from phi (block-major), then C += sgn-term (see ed_chi_z)
 template <typename T>
 ed_status chain_and_cfrac(ed_sector nb, const T *phi, int nsteps, double e0, const double2 *dz,
                           int nz, bool both, int which, double2 *dC, LanczosState *st,
                           double *weight, cudaStream_t cs) {
   ED_TRY(ed_build_items(nb, 1, (int)sizeof(T)));
+  // FP32 chains run on H - e0, with the one-body diagonal tables shifted in
+  // FP64 before their rounding (as the Green's-function chains)
+  HvTables<T> tb = ed_hv_tables<T>(nb, 1);
+  Mem shifted;
+  double sigma = 0.0;
+  if constexpr (std::is_same<T, float>::value) {
+    ED_TRY(shifted.alloc(ed_shift_diag_bytes(nb), cs, "shifted diagonal"));
+    ED_TRY(ed_shift_diag32(nb, e0, shifted.p, &tb, cs));
+    sigma = e0;
+  }
+  LinOp<T> op;
+  op.n = nb->bdim;
+  op.apply = [nb, tb](const T *v, T *w, cudaStream_t s2) {
+    return ed_launch_hv<T>(nb, tb, HV_PLAIN, v, w, nullptr, nullptr, nullptr, nullptr, nullptr, s2);
+  };
   OpRun run;
-  ED_TRY(ed_op_lanczos<T>(plain_op<T>(nb), phi, nsteps, 0.0, false, &run, st, nullptr, cs));
+  ED_TRY(ed_op_lanczos<T>(op, phi, nsteps, 0.0, false, &run, st, nullptr, cs));
   *weight = run.weight;
   if (run.weight <= 0.0 || run.k <= 0) return ED_OK;
+  e0 -= sigma;
   // n+ [(e0 + z - T)^-1]_00 (sgn +1) and + n- [(e0 - z - T)^-1]_00: the
   // launcher adds sgn * weight * [(e0 + sgn z - T)^-1]_00, so the second
   // term takes sgn = -1 with weight -n-

@@ -169,6 +169,52 @@ template ed_status ed_apply_op_launch<double, float>(ed_sector, ed_sector, const
 template ed_status ed_apply_op_launch<float, float>(ed_sector, ed_sector, const float *, float *,
                                                     int, int, int, cudaStream_t);
 
+// ----------------------------------------------------------------- FP32 chains on H - sigma
+//
+// An FP32 chain runs on H - sigma with sigma = the energy the continued
+// fraction is centred on (E0 of the state the chain starts from).  The
+// diagonal of the product is E_up[c] + E_dw[r] + W in FP32 from tables
+// rounded to FP32; each rounding costs up to 2^-24 of the entry's magnitude,
+// and for total energies of order |E0| that puts the poles near E0 off by
+// about |E0| 2^-24, which the low Matsubara frequencies magnify (a pole error
+// d shifts G(i w) by about weight d / (w^2 + eps^2)).  The shifted tables
+// E_up - s_up and E_dw - (sigma - s_up), s_up = min E_up, are formed in FP64
+// and rounded once, so that the diagonal entries of the low-lying states are
+// of the order of their excitation energy; alpha_j comes out shifted by
+// -sigma and the continued fraction takes e0 - sigma.  The vectors, the
+// product and the recurrence are unchanged.
+__global__ void k_shift_diag(const double *eu, int64_t nu, const double *ed, int64_t nd,
+                             double sigma, float *ou, float *od) {
+  __shared__ double red[32];
+  double m = 1e300;
+  for (int64_t i = threadIdx.x; i < nu; i += blockDim.x) m = fmin(m, eu[i]);
+  for (int o = 16; o > 0; o >>= 1) m = fmin(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+  __syncthreads();
+  double su = red[0];
+  for (int k = 1; k < (int)(blockDim.x >> 5); ++k) su = fmin(su, red[k]);
+  if (nu == 0) su = 0.0;
+  const double sd = sigma - su;
+  for (int64_t i = threadIdx.x; i < nu; i += blockDim.x) ou[i] = (float)(eu[i] - su);
+  for (int64_t i = threadIdx.x; i < nd; i += blockDim.x) od[i] = (float)(ed[i] - sd);
+}
+
+size_t ed_shift_diag_bytes(ed_sector s) {
+  return al256((size_t)s->bk[0].dim * sizeof(float)) + al256((size_t)s->bk[1].dim * sizeof(float));
+}
+
+ed_status ed_shift_diag32(ed_sector s, double sigma, void *mem, HvTables<float> *tb,
+                          cudaStream_t cs) {
+  float *ou = (float *)mem;
+  float *od = (float *)((char *)mem + al256((size_t)s->bk[0].dim * sizeof(float)));
+  k_shift_diag<<<1, 1024, 0, cs>>>(s->bk[0].ediag, s->bk[0].dim, s->bk[1].ediag, s->bk[1].dim,
+                                   sigma, ou, od);
+  ED_LAUNCHED(1);
+  tb->e_up = ou;
+  tb->e_dw = od;
+  return ED_OK;
+}
+
 // G[n] += sgn * weight * [(e0 + sgn z_n - T)^-1]_00 for the chain held in st
 ed_status ed_cfrac_z_launch(const LanczosState *st, double weight, double e0, const double2 *dz,
                             int nz, int sgn, double2 *dG, cudaStream_t cs) {
@@ -401,7 +447,9 @@ static ed_status one_chain(ed_sector s, const Ti *psi, int orb, int spin, int cr
   const int64_t g2 = ed_reduce_grid(n);
   const int64_t nparts = std::max<int64_t>(np1, 3 * g2);
   const size_t vb = al256(n * sizeof(To));
-  const size_t bytes = 3 * vb + al256(sizeof(LanczosState)) + 2 * al256(nparts * sizeof(double));
+  constexpr bool shift = std::is_same<To, float>::value;  // FP32 chains run on H - e0
+  const size_t bytes = 3 * vb + al256(sizeof(LanczosState)) + 2 * al256(nparts * sizeof(double)) +
+                       (shift ? ed_shift_diag_bytes(nb) : 0);
   void *mem = nullptr;
   ED_TRY(ed_dmalloc(&mem, bytes, cs, "gf chain workspace"));
   cudaError_t e = cudaSuccess;
@@ -416,6 +464,7 @@ static ed_status one_chain(ed_sector s, const Ti *psi, int orb, int spin, int cr
   double *part = (double *)p;
   p += al256(nparts * sizeof(double));
   double *part2 = (double *)p;
+  p += al256(nparts * sizeof(double));
 
   ApplyArgs a;
   a.dst_map = nb->bk[spin].map;
@@ -438,7 +487,14 @@ static ed_status one_chain(ed_sector s, const Ti *psi, int orb, int spin, int cr
     ed_count_launches(1);
     if (cudaGetLastError() != cudaSuccess) rs = ED_ERR_CUDA;
   }
-  if (rs == ED_OK) rs = ed_lanczos_chain<To>(nb, bufs, st, part, part2, g2, nsteps, cs, flag.p);
+  // the product's tables: shifted by sigma = e0 for FP32 chains
+  if (rs == ED_OK) rs = ed_build_items(nb, 1, (int)sizeof(To));
+  HvTables<To> tb = ed_hv_tables<To>(nb, 1);
+  const double sigma = shift ? e0 : 0.0;
+  if constexpr (shift) {
+    if (rs == ED_OK) rs = ed_shift_diag32(nb, sigma, p, &tb, cs);
+  }
+  if (rs == ED_OK) rs = ed_lanczos_chain<To>(nb, bufs, st, part, part2, g2, nsteps, cs, flag.p, &tb);
   double hw[2] = {0, 0};
   int32_t hj = 0;
   if (rs == ED_OK) {
@@ -454,9 +510,9 @@ static ed_status one_chain(ed_sector s, const Ti *psi, int orb, int spin, int cr
   if (rs == ED_OK && hw[0] > 0.0 && nmats > 0) {
     // 32 frequencies per CTA: the FP64 recurrences spread over many SMs
     if (dz)  // nmats arbitrary complex frequencies
-      k_cfrac_z<<<(nmats + 31) / 32, 32, 0, cs>>>(st, hw[0], e0, dz, nmats, create, dG);
+      k_cfrac_z<<<(nmats + 31) / 32, 32, 0, cs>>>(st, hw[0], e0 - sigma, dz, nmats, create, dG);
     else
-      k_cfrac<<<(nmats + 31) / 32, 32, 0, cs>>>(st, hw[0], e0, beta, nmats, create, dG);
+      k_cfrac<<<(nmats + 31) / 32, 32, 0, cs>>>(st, hw[0], e0 - sigma, beta, nmats, create, dG);
     ed_count_launches(1);
     if (cudaGetLastError() != cudaSuccess) rs = ED_ERR_CUDA;
   }
@@ -807,9 +863,11 @@ static ed_status chain_batch(ed_sector s, const Ti *psi, double e0, int nsteps, 
                              int nmats, int njobs, const int *orb, const int *spin,
                              const int *create, double *host_G, double *weight, int *steps,
                              int64_t *dim, cudaStream_t cs) {
+  constexpr bool shift = std::is_same<To, float>::value;  // FP32 chains run on H - e0
   std::vector<ChainTask<Ti, To>> tasks;
   std::vector<int> job_of, sgn;
   std::vector<size_t> off;
+  std::vector<ed_sector> nbs;
   size_t bytes = 0;
   for (int q = 0; q < njobs; ++q) {
     weight[q] = 0.0;
@@ -836,7 +894,9 @@ static ed_status chain_batch(ed_sector s, const Ti *psi, double e0, int nsteps, 
     t.psi = psi;
     t.nsteps = nsteps;
     off.push_back(bytes);
-    bytes += 3 * al256(nb->bdim * sizeof(To)) + al256(sizeof(LanczosState));
+    bytes += 3 * al256(nb->bdim * sizeof(To)) + al256(sizeof(LanczosState)) +
+             (shift ? ed_shift_diag_bytes(nb) : 0);
+    nbs.push_back(nb);
     tasks.push_back(t);
     job_of.push_back(q);
     sgn.push_back(create[q]);
@@ -862,11 +922,22 @@ static ed_status chain_batch(ed_sector s, const Ti *psi, double e0, int nsteps, 
     tasks[i].st = (LanczosState *)(p + 3 * vb);
     m.sts.push_back(tasks[i].st);
     m.sgn.push_back(sgn[i]);
-    m.e0.push_back(e0);
+    m.e0.push_back(shift ? 0.0 : e0);  // the continued fraction's e0 - sigma
+  }
+  ed_status rs = ED_OK;
+  if constexpr (shift) {
+    for (int i = 0; i < nt && rs == ED_OK; ++i)
+      rs = ed_shift_diag32(nbs[i], e0,
+                           base + off[i] + 3 * al256(tasks[i].a.dst_dim * sizeof(To)) +
+                               al256(sizeof(LanczosState)),
+                           &tasks[i].tb, cs);
+  }
+  if (rs != ED_OK) {
+    ed_dfree(mem, cs);
+    return rs;
   }
   m.tasks.resize((size_t)nt * sizeof(ChainTask<Ti, To>));
   memcpy(m.tasks.data(), tasks.data(), m.tasks.size());
-  ed_status rs = ED_OK;
   if (cudaEventCreateWithFlags(&m.ready, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventRecord(m.ready, cs) != cudaSuccess)
     rs = ED_ERR_CUDA;

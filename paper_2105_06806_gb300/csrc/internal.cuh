@@ -380,7 +380,11 @@ struct LanczosState {
   int32_t j;          // completed steps
   int32_t done;       // 0 running, 1 converged, 2 breakdown, 3 max_iter
   int32_t maxit;
-  int32_t check_every;
+  int32_t check_every;  // fewest steps between two Ritz-value tests
+  int32_t next_check;   // step of the next scheduled test
+  int32_t pad_;
+  double check_growth;  // a test at step k schedules the next one
+                        // max(check_every, ceil(check_growth * k)) steps later
   double tol;
   double tnorm;
   double theta, rest;
@@ -407,10 +411,12 @@ ed_status ed_hv_prepare();
 
 // lanczos.cu
 int64_t ed_reduce_grid(int64_t n);
+// a chain of nsteps from bufs[0]; `tables` (nullable) replaces the sector's
+// product tables (the shifted diagonal of FP32 chains)
 template <typename T>
 ed_status ed_lanczos_chain(ed_sector s, T *const *bufs, LanczosState *st, double *part,
                            double *part2, int64_t nparts_start, int nsteps, cudaStream_t cs,
-                           int32_t *h_flag);
+                           int32_t *h_flag, const HvTables<T> *tables = nullptr);
 ed_status ed_lanczos_ground_impl(ed_sector s, const ed_lanczos_opts *o, ed_lanczos_result *res,
                                  void *d_psi, cudaStream_t cs);
 
@@ -463,7 +469,14 @@ ed_status ed_apply_op_launch(ed_sector s, ed_sector nb, const Ti *psi, To *phi, 
                              int create, cudaStream_t cs);
 ed_status ed_cfrac_z_launch(const LanczosState *st, double weight, double e0, const double2 *dz,
                             int nz, int sgn, double2 *dG, cudaStream_t cs);
+// gf.cu: the FP32 product tables of an FP32 chain on H - sigma (the one-body
+// diagonal tables shifted in FP64, then rounded): ed_shift_diag_bytes(s) bytes
+// of device scratch at `mem` receive them, tb->e_up / tb->e_dw point there
+size_t ed_shift_diag_bytes(ed_sector s);
+ed_status ed_shift_diag32(ed_sector s, double sigma, void *mem, HvTables<float> *tb,
+                          cudaStream_t cs);
 // lanczos.cu: sector order <-> block-major order of one vector
 ed_status ed_permute_vec(ed_sector s, ed_precision prec, bool to_blocked, const void *in,
                          void *out, cudaStream_t cs);
+
 

@@ -81,6 +81,21 @@ __device__ __forceinline__ double mulT<double>(double a, double b) { return __dm
 // b[i] = beta_i, b2[i] = beta_i^2 (i < k; b[0] unused), so that their serial
 // recurrences wait on shared rather than global loads.
 
+// FP64 is the slow pipe of this part, so the recurrences below keep only
+// their arithmetic there: the sign, zero and range tests read the bits of a
+// double in the integer pipe.  The rescaling multiplies by a power of two,
+// which is exact, so where it happens does not change any result.
+__device__ __forceinline__ bool neg_bit(double x) { return __double2hiint(x) < 0; }
+__device__ __forceinline__ bool is_zero(double x) { return (__double_as_longlong(x) << 1) == 0; }
+// biased exponent of |x| (0 for zero and subnormals)
+__device__ __forceinline__ int bexp(double x) { return (__double2hiint(x) >> 20) & 0x7ff; }
+// |x| above about 1e200 or (nonzero and) below about 1e-200
+__device__ __forceinline__ bool out_of_range(int e) { return e > 1023 + 664 || e < 1023 - 664; }
+// 2^(1022 - e): brings a double of biased exponent e into [0.5, 1) in magnitude
+__device__ __forceinline__ double rescale_factor(int e) {
+  return __hiloint2double((2045 - e) << 20, 0);
+}
+
 // Sturm count: eigenvalues of T_k below x = sign changes of the leading
 // principal minors p_i = det(T_i - x) (division-free recurrence, rescaled by
 // powers of two; an exact zero counts as a change, as a tiny negative pivot).
@@ -93,15 +108,13 @@ __device__ int sturm_count(const double *a, const double *b2, int k, double x) {
   }
   for (int i = 1; i < k; ++i) {
     double pn = (a[i] - x) * p - b2[i] * pm;
-    if (pn == 0.0) pn = -copysign(1e-300, p);
-    if ((pn < 0.0) != (p < 0.0)) ++cnt;
+    if (is_zero(pn)) pn = neg_bit(p) ? 1e-300 : -1e-300;
+    cnt += neg_bit(pn) != neg_bit(p);
     pm = p;
     p = pn;
-    double ap = fabs(p);
-    if (ap > 1e200 || ap < 1e-200) {
-      int e;
-      frexp(p, &e);
-      double f = ldexp(1.0, -e);
+    const int e = bexp(p);
+    if (out_of_range(e)) {
+      const double f = rescale_factor(e);
       p *= f;
       pm *= f;
     }
@@ -121,11 +134,11 @@ __device__ double last_component_sq(const double *a, const double *b2, int k, do
     p = pn;
     dpm = dp;
     dp = dpn;
-    double m = fmax(fmax(fabs(p), fabs(pm)), fmax(fabs(dp), fabs(dpm)));
-    if (m > 1e200 || (m < 1e-200 && m > 0.0)) {
-      int e;
-      frexp(m, &e);
-      double f = ldexp(1.0, -e);
+    // rescaled by the largest magnitude of the four (none when all are zero)
+    const int e = max(max(bexp(p), bexp(pm)), max(bexp(dp), bexp(dpm)));
+    if (e > 1023 + 664 ||
+        (e < 1023 - 664 && !(is_zero(p) && is_zero(pm) && is_zero(dp) && is_zero(dpm)))) {
+      const double f = rescale_factor(e);
       p *= f;
       pm *= f;
       dp *= f;
@@ -351,8 +364,8 @@ __global__ void __launch_bounds__(AXPY_THREADS) k_axpy_norm(LanczosState *st, T 
   }
 }
 
-// beta_{j+1}, scale, Ritz value and stop test.  `check` = 1 evaluates the
-// Ritz value every `check_every` steps (and always at the last step).
+// beta_{j+1}, scale, Ritz value and stop test.  The Ritz value is evaluated
+// at steps 1 and 2, at the scheduled steps (next_check) and at the last step.
 __global__ void k_beta(LanczosState *st, const double *part, int64_t nparts) {
   __shared__ double red[SCALAR_THREADS / 32];
   __shared__ int stop;
@@ -379,7 +392,8 @@ __global__ void k_beta(LanczosState *st, const double *part, int64_t nparts) {
   }
   __syncthreads();
   const int k = j + 1;
-  const bool want = st->tol > 0.0 && (stop != 0 || (k % st->check_every) == 0 || k <= 2);
+  const bool scheduled = k >= st->next_check;
+  const bool want = st->tol > 0.0 && (stop != 0 || scheduled || k <= 2);
   if (want) {
     stage_tridiag(st, k, s_a, s_b, s_b2);
     const double prev = st->theta;
@@ -409,6 +423,8 @@ __global__ void k_beta(LanczosState *st, const double *part, int64_t nparts) {
       st->theta = th;
       st->rest = rest;
       if (stop == 0 && rest <= st->tol * fmax(1.0, fabs(th)) && k >= 2) stop = 1;
+      if (scheduled)
+        st->next_check = k + max(st->check_every, (int)ceil(st->check_growth * (double)k));
     }
     __syncthreads();
     if (ritz)
@@ -489,7 +505,7 @@ __global__ void __launch_bounds__(AXPY_THREADS) k_norm2(const T *v, int64_t n, d
 
 // Initialise the recurrence state: v_0 = buffer 0 scaled by 1/||buffer 0||.
 __global__ void k_state_init(LanczosState *st, const double *part, int64_t nparts, int maxit,
-                             double tol, int check_every) {
+                             double tol, int check_every, double check_growth) {
   __shared__ double red[SCALAR_THREADS / 32];
   double s = cta_sum_parts(part, nparts, red);
   if (threadIdx.x == 0) {
@@ -497,6 +513,8 @@ __global__ void k_state_init(LanczosState *st, const double *part, int64_t npart
     st->done = s > 0.0 ? 0 : 2;
     st->maxit = maxit;
     st->check_every = check_every;
+    st->next_check = check_every;
+    st->check_growth = check_growth;
     st->tol = tol;
     st->tnorm = 0.0;
     st->theta = INFINITY;
@@ -910,6 +928,21 @@ static ed_status second_pass(ed_sector s, const HvTables<T> &tb, T *const *bufs,
   return ED_OK;
 }
 
+// Spacing of the Ritz-value tests.  A test at step k costs about
+// kTestCostMs * k (the FP64 recurrences over T_k in sturm_count and
+// last_component_sq, on one warp), a step about step_ms (the product and its
+// reductions, estimated from the bytes they move at 1 TB/s plus the launch
+// cost).  Testing every d steps spends kTestCostMs * k / d per step and runs
+// d / 2 steps past convergence on average; d = k sqrt(2 kTestCostMs /
+// step_ms) balances the two, so the tests fall on geometrically spaced steps
+// with this growth.  The schedule depends on the sector size only, never on
+// a timing, so a solve stops at the same step on every run.
+constexpr double kTestCostMs = 2e-3;  // per unit of k, measured on GB300
+static double test_growth(int64_t n, size_t elem) {
+  const double step_ms = 0.012 + 2.0 * (double)n * (double)elem * 1e-9;
+  return sqrt(2.0 * kTestCostMs / step_ms);
+}
+
 // One Lanczos solve in precision T on sector s, starting from either the
 // seeded vector or (start != nullptr) a given vector in precision T.
 template <typename T>
@@ -977,8 +1010,9 @@ static ed_status lanczos_solve(ed_sector s, int maxit, double tol, uint64_t seed
     return ED_ERR_OOM;
   }
   // Ritz-value tests cost FP64 latency on one warp: below 2^20 elements a
-  // Lanczos step is cheaper than a test, so test every 8 steps there
+  // Lanczos step is cheaper than a test, so test at most every 8 steps there
   const int check_every = n > (1 << 22) ? 1 : (n > (1 << 20) ? 4 : 8);
+  const double growth = test_growth(n, sizeof(T));
   auto init = [&]() -> ed_status {
     if (start) {
       ED_TRY_CUDA(cudaMemcpyAsync(bufs[0], start, n * sizeof(T), cudaMemcpyDeviceToDevice, cs));
@@ -989,7 +1023,7 @@ static ed_status lanczos_solve(ed_sector s, int maxit, double tol, uint64_t seed
           part);
     }
     ED_LAUNCHED(1);
-    k_state_init<<<1, SCALAR_THREADS, 0, cs>>>(st, part, g2, maxit, tol, check_every);
+    k_state_init<<<1, SCALAR_THREADS, 0, cs>>>(st, part, g2, maxit, tol, check_every, growth);
     ED_LAUNCHED(1);
     return ED_OK;
   };
@@ -1159,19 +1193,21 @@ ed_status ed_lanczos_ground_impl(ed_sector s, const ed_lanczos_opts *o, ed_lancz
 template <typename T>
 ed_status ed_lanczos_chain(ed_sector s, T *const *bufs, LanczosState *st, double *part,
                            double *part2, int64_t nparts_start, int nsteps, cudaStream_t cs,
-                           int32_t *h_flag) {
-  k_state_init<<<1, SCALAR_THREADS, 0, cs>>>(st, part, nparts_start, nsteps, 0.0, 1);
+                           int32_t *h_flag, const HvTables<T> *tables) {
+  k_state_init<<<1, SCALAR_THREADS, 0, cs>>>(st, part, nparts_start, nsteps, 0.0, 1, 0.0);
   ED_LAUNCHED(1);
   ED_TRY(ed_build_items(s, 1, (int)sizeof(T)));
-  HvTables<T> tb = ed_hv_tables<T>(s, 1);
+  const HvTables<T> tb = tables ? *tables : ed_hv_tables<T>(s, 1);
   int launched = 0;
   return run_steps<T>(s, tb, bufs, st, part, part2, s->bdim, nsteps, cs, &launched, h_flag);
 }
 
 template ed_status ed_lanczos_chain<float>(ed_sector, float *const *, LanczosState *, double *,
-                                           double *, int64_t, int, cudaStream_t, int32_t *);
+                                           double *, int64_t, int, cudaStream_t, int32_t *,
+                                           const HvTables<float> *);
 template ed_status ed_lanczos_chain<double>(ed_sector, double *const *, LanczosState *, double *,
-                                            double *, int64_t, int, cudaStream_t, int32_t *);
+                                            double *, int64_t, int, cudaStream_t, int32_t *,
+                                            const HvTables<double> *);
 
 int64_t ed_reduce_grid(int64_t n) { return reduce_grid(n); }
 

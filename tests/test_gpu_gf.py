@@ -99,7 +99,7 @@ def test_ns16_benchmark_sector_against_golden(ed):
     oracle's stored FP64 run (tests/golden/make_golden.py ns16): E0 of the
     FP64 path, of the raw FP32 Lanczos (1e-6) and of FP32 + polish (1e-10);
     256 samples of psi; G_{0,up}(i w_n) and the chain weights from FP64
-    chains (1e-8) and from FP32 chains on the polished state (3e-5)."""
+    chains (1e-8) and from FP32 chains on the polished state (1e-5)."""
     g, Gref = _gold("oracle_ns16.json")
     wl = workload_ns16(0)
     s = ed.Sector(wl.model, wl.nup, wl.ndw)
@@ -119,9 +119,10 @@ def test_ns16_benchmark_sector_against_golden(ed):
     assert abs(rp["e0"] - e) <= 1e-10 * abs(e)
     G2, _ = ed.gf_lanczos(s, psip, rp["e0"], 0, 0, "fp32_polish", nsteps=200, beta=100.0,
                           nmats=512)
-    # FP32 chains: the error grows with the sector dimension (about 5e-7 at
-    # D = 4.9e3, 3e-6 at 1.2e7, 1.3e-5 at 1.7e8), set by the FP32 vectors
-    assert np.abs(G2 - Gref).max() <= 3e-5
+    # FP32 chains run on H - E0 (diagonal tables shifted before their FP32
+    # rounding): 3.3e-7 here, against 1.3e-5 for chains on H itself, whose
+    # diagonal entries of order |E0| = 22 round to 2^-24 |E0|
+    assert np.abs(G2 - Gref).max() <= 1e-5
     s.free()
 
 
