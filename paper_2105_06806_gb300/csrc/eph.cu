@@ -110,10 +110,12 @@ unsigned grid_of(int64_t n) {
 }
 
 // The coupled operator on `layout` (0: sector order, 1: padded block-major)
+// (`tables`, nullable: the electronic product's tables instead of the
+// sector's, e.g. the shifted diagonal of an FP32 chain)
 template <typename T>
 ed_status eph_apply(ed_sector s, const PhParams &ph, int layout, const T *v, T *w,
-                    cudaStream_t cs) {
-  const HvTables<T> tb = ed_hv_tables<T>(s, layout);
+                    cudaStream_t cs, const HvTables<T> *tables = nullptr) {
+  const HvTables<T> tb = tables ? *tables : ed_hv_tables<T>(s, layout);
   const int64_t slice = layout == 1 ? s->bdim : s->dim;
   for (int p = 0; p <= ph.nph; ++p)
     ED_TRY(ed_launch_hv<T>(s, tb, HV_PLAIN, v + (int64_t)p * slice, w + (int64_t)p * slice,
@@ -131,6 +133,17 @@ LinOp<T> eph_op(ed_sector s, const PhParams &ph) {
   LinOp<T> op;
   op.n = s->bdim * (int64_t)(ph.nph + 1);
   op.apply = [s, ph](const T *v, T *w, cudaStream_t cs) { return eph_apply<T>(s, ph, 1, v, w, cs); };
+  return op;
+}
+
+// the coupled operator with the electronic product on the given tables
+template <typename T>
+LinOp<T> eph_op(ed_sector s, const PhParams &ph, const HvTables<T> &tb) {
+  LinOp<T> op;
+  op.n = s->bdim * (int64_t)(ph.nph + 1);
+  op.apply = [s, ph, tb](const T *v, T *w, cudaStream_t cs) {
+    return eph_apply<T>(s, ph, 1, v, w, cs, &tb);
+  };
   return op;
 }
 
@@ -288,6 +301,7 @@ extern "C" ed_status ed_eph_gf_lanczos_z(ed_sector s, const ed_phonon *ph, ed_pr
     if (!nb || nb->dim == 0) continue;
     const int64_t n = nb->bdim * (int64_t)dph;
     OpRun run;
+    double sigma = 0.0;  // the chain's operator is H - sigma
     if (prec == ED_FP64) {
       ED_TRY(ed_build_items(nb, 1, 8));
       Buf phi;
@@ -312,8 +326,16 @@ extern "C" ed_status ed_eph_gf_lanczos_z(ed_sector s, const ed_phonon *ph, ed_pr
                                                     (const double *)d_psi + (int64_t)p * s->dim,
                                                     dst, orb, spin, create, cs)));
       }
-      ED_TRY(ed_op_lanczos<float>(eph_op<float>(nb, pp), (const float *)phi.p, nsteps, 0.0,
+      // FP32 chains run on H - e0: the electronic diagonal tables shifted in
+      // FP64 before their rounding (the phonon terms are unchanged), so that
+      // the continued fraction takes e0 - e0 = 0
+      HvTables<float> tb = ed_hv_tables<float>(nb, 1);
+      Buf shifted;
+      ED_TRY(shifted.alloc(ed_shift_diag_bytes(nb), cs, "shifted diagonal"));
+      ED_TRY(ed_shift_diag32(nb, e0, shifted.p, &tb, cs));
+      ED_TRY(ed_op_lanczos<float>(eph_op<float>(nb, pp, tb), (const float *)phi.p, nsteps, 0.0,
                                   false, &run, st, nullptr, cs));
+      sigma = e0;
     }
     if (info) {
       if (create > 0) {
@@ -325,7 +347,7 @@ extern "C" ed_status ed_eph_gf_lanczos_z(ed_sector s, const ed_phonon *ph, ed_pr
       }
     }
     if (run.weight > 0.0 && run.k > 0)
-      ED_TRY(ed_cfrac_z_launch(st, run.weight, e0, dz, nz, create, dG, cs));
+      ED_TRY(ed_cfrac_z_launch(st, run.weight, e0 - sigma, dz, nz, create, dG, cs));
   }
   if (nz > 0)
     ED_TRY_CUDA(cudaMemcpyAsync(host_G, dG, nz * sizeof(double2), cudaMemcpyDeviceToHost, cs));

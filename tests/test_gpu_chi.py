@@ -52,7 +52,7 @@ def test_chi_against_oracle(ed, case, kind):
     r2 = ed.lanczos_ground(s, "fp32_polish", psi=psi2)
     Co = chi.chi_z(m, nup, ndw, ro["psi"], ro["e0"], kind, 0, Z, nsteps=150)
     C2, _ = ed.chi_z(s, psi2, r2["e0"], kind, 0, Z, "fp32_polish", nsteps=150)
-    assert np.abs(C2 - Co).max() <= 3e-5 * max(1.0, np.abs(Co).max())
+    assert np.abs(C2 - Co).max() <= 1e-5 * max(1.0, np.abs(Co).max())
     s.free()
 
 

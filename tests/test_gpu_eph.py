@@ -152,7 +152,7 @@ def test_eph_gf_against_oracle(ed, case):
     r2 = ed.eph_lanczos_ground(s, pp, "fp32_polish", psi=psi2)
     Go = eph.impurity_gf_z(m, ph, nup, ndw, ro["psi"], ro["e0"], 0, 0, z, nsteps=120)
     G2, _ = ed.eph_gf_lanczos_z(s, pp, psi2, r2["e0"], 0, 0, z, "fp32_polish", nsteps=120)
-    assert np.abs(G2 - Go).max() <= 3e-5
+    assert np.abs(G2 - Go).max() <= 1e-5
     s.free()
 
 
