@@ -555,6 +555,22 @@ ed_status ed_server_inject_alloc_failure(ed_server srv, int32_t count);
 ed_status ed_residual_noalloc(ed_sector s, const double *d_psi, int64_t n, double *host_e_r,
                               void *stream);
 
+/* Device memory of the library (current device).  Every device buffer comes
+ * from one stream-ordered pool per device, and freed blocks stay cached in
+ * it for later allocations (the first use of fresh device memory costs about
+ * 5.6 ms per GB on GB300, a large share of a solve that allocates its Krylov
+ * basis as it goes).  Other allocators in the process (PyTorch's, for one)
+ * cannot use the cached blocks: ed_memory_trim returns the cached blocks
+ * beyond keep_bytes (>= 0; 0 returns all that are not in use) to the device,
+ * as torch.cuda.empty_cache does for PyTorch.  ed_memory_cached reports the
+ * pool's reserved bytes and the part of them in use by live buffers.  The
+ * budgets that look at free memory (the Krylov basis of ed_lanczos_ground,
+ * the admission of ed_server_create with device_mem_budget = 0) count the
+ * cached blocks as available.  ED_ERR_ARG on a negative keep_bytes or a
+ * NULL output. */
+ed_status ed_memory_trim(int64_t keep_bytes);
+ed_status ed_memory_cached(int64_t *reserved, int64_t *used);
+
 const char *ed_status_string(ed_status st);
 const char *ed_last_error(void);
 /* Number of kernels this library has launched in the calling process. */

@@ -35,7 +35,7 @@ EXPORTED = [
     "ed_server_create", "ed_submit", "ed_poll", "ed_wait", "ed_server_destroy",
     "ed_server_inject_alloc_failure", "ed_batch_stats", "ed_residual_noalloc", "ed_status_string",
     "ed_last_error",
-    "ed_kernel_launches",
+    "ed_kernel_launches", "ed_memory_trim", "ed_memory_cached",
 ]
 
 
@@ -175,6 +175,8 @@ def lib():
             "ed_server_inject_alloc_failure": [vp, i32],
             "ed_residual_noalloc": [vp, vp, i64, vp, vp],
             "ed_batch_stats": [C.POINTER(i64), C.POINTER(i64), C.POINTER(i64)],
+            "ed_memory_trim": [i64],
+            "ed_memory_cached": [C.POINTER(i64), C.POINTER(i64)],
             "ed_gf_lanczos_z": [vp, C.c_int, vp, C.c_double, i32, i32, i32, vp, i32, vp,
                                 C.POINTER(ed_gf_info), vp],
             "ed_sigma": [C.POINTER(ed_model), i32, i32, vp, i32, vp, vp, vp],
@@ -376,6 +378,19 @@ def permute(sector: Sector, x, out, to_blocked=True, precision="fp64", stream=No
                                    C.c_void_p(x.data_ptr()), int(x.numel()),
                                    C.c_void_p(out.data_ptr()), int(out.numel()),
                                    C.c_void_p(_stream_ptr(stream))), "ed_sector_permute")
+
+
+def trim_memory(keep_bytes=0):
+    """Return the library pool's cached device blocks beyond keep_bytes to
+    the device (ed_memory_trim; like torch.cuda.empty_cache for PyTorch)."""
+    _check(lib().ed_memory_trim(int(keep_bytes)), "ed_memory_trim")
+
+
+def memory_cached():
+    """(reserved, used) bytes of the library's device pool (ed_memory_cached)."""
+    r, u = C.c_int64(), C.c_int64()
+    _check(lib().ed_memory_cached(C.byref(r), C.byref(u)), "ed_memory_cached")
+    return r.value, u.value
 
 
 def batch_stats():

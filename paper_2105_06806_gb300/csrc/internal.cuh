@@ -45,6 +45,9 @@ void ed_count_launches(int64_t n);
 // synchronises the device); ed_dfree orders the release on `st`.
 ed_status ed_dmalloc(void **p, size_t bytes, cudaStream_t st, const char *what);
 void ed_dfree(void *p, cudaStream_t st);
+// Device memory a new allocation can use: free device memory plus the
+// blocks cached in the library's pool (current device).
+ed_status ed_device_available(size_t *bytes);
 // Non-blocking stream private to the calling host thread (current device).
 cudaStream_t ed_private_stream(ed_status *st);
 // Page-locked 4-byte host word for polling a device flag, from a recycled pool.

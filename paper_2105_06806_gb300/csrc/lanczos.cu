@@ -1011,8 +1011,8 @@ static ed_status lanczos_solve(ed_sector s, int maxit, double tol, uint64_t seed
     } else if (basis_mib > 0) {
       bs.budget = (size_t)basis_mib << 20;
     } else {
-      size_t fr = 0, tot = 0;
-      bs.budget = cudaMemGetInfo(&fr, &tot) == cudaSuccess ? (size_t)(0.4 * (double)fr) : 0;
+      size_t avail = 0;
+      bs.budget = ed_device_available(&avail) == ED_OK ? (size_t)(0.4 * (double)avail) : 0;
     }
   }
 

@@ -173,14 +173,13 @@ extern "C" ed_status ed_server_create(const ed_server_opts *opts, ed_server *out
   if (s->opts.device_mem_budget > 0) {
     s->budget = s->opts.device_mem_budget;
   } else {
-    size_t fr = 0, tot = 0;
-    e = cudaMemGetInfo(&fr, &tot);
-    if (e != cudaSuccess) {
-      ed_set_cuda_error(e, "cudaMemGetInfo", __FILE__, __LINE__);
+    size_t avail = 0;
+    const ed_status as = ed_device_available(&avail);
+    if (as != ED_OK) {
       delete s;
-      return ED_ERR_CUDA;
+      return as;
     }
-    s->budget = (int64_t)(fr / 2);
+    s->budget = (int64_t)(avail / 2);
   }
   ed_status bs = ed_upload_binomials();
   if (bs != ED_OK) {

@@ -24,3 +24,20 @@ def ed():
     import paper_2105_06806_gb300 as E
     E.lib()
     return E
+
+
+@pytest.fixture(autouse=True, scope="module")
+def _release_device_memory():
+    """After each GPU test module, the library pool's cached blocks and
+    PyTorch's go back to the device, so that one module's peak does not
+    crowd the next module's allocations (a no-op where the library was not
+    loaded)."""
+    yield
+    E = sys.modules.get("paper_2105_06806_gb300")
+    if E is None or getattr(E, "_lib", None) is None:
+        return
+    import torch
+    if torch.cuda.is_available():
+        torch.cuda.synchronize()
+        E.trim_memory()
+        torch.cuda.empty_cache()
