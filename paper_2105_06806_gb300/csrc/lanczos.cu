@@ -422,7 +422,8 @@ __global__ void k_beta(LanczosState *st, const double *part, int64_t nparts) {
       st->acc[3] = isfinite(prev) ? th - prev : 1e300;
       st->theta = th;
       st->rest = rest;
-      if (stop == 0 && rest <= st->tol * fmax(1.0, fabs(th)) && k >= 2) stop = 1;
+      // converged, also when the test falls on the max_iter step
+      if ((stop == 0 || stop == 3) && rest <= st->tol * fmax(1.0, fabs(th)) && k >= 2) stop = 1;
       if (scheduled)
         st->next_check = k + max(st->check_every, (int)ceil(st->check_growth * (double)k));
     }
@@ -1213,7 +1214,10 @@ ed_status ed_lanczos_ground_impl(ed_sector s, const ed_lanczos_opts *o, ed_lancz
   ED_TRY_CUDA(cudaStreamSynchronize(cs));
   res->matvecs = mv;
   res->matvecs_fp64 = mv - mv32;
-  if (res->stop_reason == 2) return ED_ERR_NOT_CONVERGED;
+  if (res->stop_reason == 2) {
+    ed_set_error_msg("max_iter reached before the Lanczos tolerance");
+    return ED_ERR_NOT_CONVERGED;
+  }
   return ED_OK;
 }
 

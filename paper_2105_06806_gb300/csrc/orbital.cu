@@ -249,6 +249,9 @@ extern "C" ed_status ed_lanczos_ground_orbital(ed_sector s, const int32_t *nup_o
   ED_TRY_CUDA(cudaStreamSynchronize(cs));
   res->matvecs = mv;
   res->matvecs_fp64 = mv - mv32;
-  if (run.stop == 2) return ED_ERR_NOT_CONVERGED;
+  if (run.stop == 2) {
+    ed_set_error_msg("max_iter reached before the Lanczos tolerance");
+    return ED_ERR_NOT_CONVERGED;
+  }
   return ED_OK;
 }
