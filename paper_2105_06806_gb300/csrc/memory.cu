@@ -55,6 +55,13 @@ ed_status device_pool(cudaMemPool_t *out) {
     ED_TRY_CUDA(cudaMemPoolCreate(&p, &props));
     uint64_t keep = ~0ull;  // freed blocks stay cached (see the file comment)
     cudaError_t e = cudaMemPoolSetAttribute(p, cudaMemPoolAttrReleaseThreshold, &keep);
+    // a block freed on another stream is reused only once its free has
+    // completed, never by making the new stream wait on the old one:
+    // concurrent requests (the server's slots, the concurrent chains) would
+    // otherwise wait on each other through the memory they exchange
+    int no = 0;
+    if (e == cudaSuccess)
+      e = cudaMemPoolSetAttribute(p, cudaMemPoolReuseAllowInternalDependencies, &no);
     if (e != cudaSuccess) {
       cudaMemPoolDestroy(p);
       ed_set_cuda_error(e, "cudaMemPoolSetAttribute", __FILE__, __LINE__);
@@ -86,6 +93,14 @@ ed_status ed_dmalloc(void **p, size_t bytes, cudaStream_t st, const char *what) 
   cudaMemPool_t pool = nullptr;
   ED_TRY(device_pool(&pool));
   cudaError_t e = cudaMallocFromPoolAsync(p, bytes > 0 ? bytes : 1, pool, st);
+  if (e == cudaErrorMemoryAllocation) {
+    // the device is full of this pool's cached blocks that this stream
+    // cannot use (split into other sizes, or freed on streams it does not
+    // follow): return the free ones to the device and try once more
+    cudaGetLastError();
+    cudaMemPoolTrimTo(pool, 0);
+    e = cudaMallocFromPoolAsync(p, bytes > 0 ? bytes : 1, pool, st);
+  }
   if (e != cudaSuccess) {
     *p = nullptr;
     ed_set_cuda_error(e, what ? what : "cudaMallocFromPoolAsync", __FILE__, __LINE__);
