@@ -299,7 +299,7 @@ struct Vec16<double> {
 template <typename T>
 __global__ void __launch_bounds__(AXPY_THREADS) k_axpy_norm(LanczosState *st, T *b0, T *b1, T *b2,
                                                             T *const *basis, int64_t n,
-                                                            double *part) {
+                                                            double *part, T *psi = nullptr) {
   __shared__ double red[2][AXPY_THREADS / 32];
   if (st->done) return;
   const int j = st->j;
@@ -320,6 +320,10 @@ __global__ void __launch_bounds__(AXPY_THREADS) k_axpy_norm(LanczosState *st, T 
   const typename VT::V *vv = reinterpret_cast<const typename VT::V *>(v);
   const typename VT::V *pv = reinterpret_cast<const typename VT::V *>(prev);
   typename VT::V *wv = reinterpret_cast<typename VT::V *>(w);
+  // second pass of a two-pass sector: psi += y_j v_j (the same operation as
+  // the fused second-pass epilogue of the product)
+  typename VT::V *psv = reinterpret_cast<typename VT::V *>(psi);
+  const T yj = psi ? (T)st->y[j] : T(0);
   const int64_t nv = n / NV;
   double accd = 0.0, cvvd = 0.0;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -342,6 +346,13 @@ __global__ void __launch_bounds__(AXPY_THREADS) k_axpy_norm(LanczosState *st, T 
         cvv = fmaT<T>(x[q], vi[q], cvv);
       }
       wv[i] = VT::make(x);
+      if (psi) {
+        T ps[NV];
+        VT::get(psv[i], ps);
+#pragma unroll
+        for (int q = 0; q < NV; ++q) ps[q] = fmaT<T>(yj, vi[q], ps[q]);
+        psv[i] = VT::make(ps);
+      }
     }
     accd += (double)acc;
     cvvd += (double)cvv;
@@ -557,6 +568,7 @@ __global__ void k_second_advance(LanczosState *st) {
 __global__ void k_second_resume(LanczosState *st, int m) {
   const double s0 = st->acc[0] > 0.0 ? 1.0 / sqrt(st->acc[0]) : 0.0;  // v_0 = start / ||start||
   st->j = m;
+  st->done = 0;  // the Lanczos-mode kernels of the split second pass test it
   st->scale[m % 3] = m == 0 ? s0 : (st->beta[m] > 0.0 ? 1.0 / st->beta[m] : 0.0);
   if (m > 0)
     st->scale[(m - 1) % 3] = m == 1 ? s0 : (st->beta[m - 1] > 0.0 ? 1.0 / st->beta[m - 1] : 0.0);
@@ -928,14 +940,30 @@ static ed_status run_steps(ed_sector s, const HvTables<T> &tb, T *const *bufs, L
 // was resumed at step j0).
 template <typename T>
 static ed_status second_pass(ed_sector s, const HvTables<T> &tb, T *const *bufs, T *psi,
-                             LanczosState *st, int j0, int k, int64_t n, cudaStream_t cs) {
+                             LanczosState *st, int j0, int k, int64_t n, double *part,
+                             double *part2, cudaStream_t cs) {
   if (j0 == 0) ED_TRY_CUDA(cudaMemsetAsync(psi, 0, n * sizeof(T), cs));
+  const int64_t g = reduce_grid(n);
+  // Two-pass product: the first pass's own kernels (the Lanczos-mode product,
+  // then the streaming update, which here also adds y_j v_j into psi) instead
+  // of the fused second-pass H_dw epilogue: 14.3 + 3 ms against 19.6 ms per
+  // step at Ns=18; the same operations, so the same vectors bit for bit.
+  const bool split = tb.ditems && !tb.small_cols;
   for (int j = j0; j + 1 < k; ++j) {
-    ED_TRY(ed_launch_hv<T>(s, tb, HV_SECOND, nullptr, nullptr, bufs, psi, st, nullptr, nullptr, cs));
+    if (split) {
+      int64_t np1 = 0;
+      ED_TRY(ed_launch_hv<T>(s, tb, HV_LANCZOS, nullptr, nullptr, bufs, nullptr, st, part, &np1,
+                             cs));
+      k_axpy_norm<T><<<(unsigned)g, AXPY_THREADS, 0, cs>>>(st, bufs[0], bufs[1], bufs[2], nullptr,
+                                                            n, part2, psi);
+      ED_LAUNCHED(1);
+    } else {
+      ED_TRY(ed_launch_hv<T>(s, tb, HV_SECOND, nullptr, nullptr, bufs, psi, st, nullptr, nullptr,
+                             cs));
+    }
     k_second_advance<<<1, 1, 0, cs>>>(st);
     ED_LAUNCHED(1);
   }
-  int64_t g = reduce_grid(n);
   k_psi_tail<T><<<(unsigned)g, AXPY_THREADS, 0, cs>>>(st, bufs[0], bufs[1], bufs[2], psi, n);
   ED_LAUNCHED(1);
   return ED_OK;
@@ -1076,12 +1104,12 @@ static ed_status lanczos_solve(ed_sector s, int maxit, double tol, uint64_t seed
       rot2[(m + 1) % 3] = bufs[1];
       k_second_resume<<<1, 1, 0, cs>>>(st, m);
       ED_LAUNCHED(1);
-      ED_TRY(second_pass<T>(s, tb, rot2, psi, st, m, k, n, cs));
+      ED_TRY(second_pass<T>(s, tb, rot2, psi, st, m, k, n, part, part2, cs));
       mv += k - 1 - m;
     } else {
       // restart the recurrence bookkeeping for the second pass
       ED_TRY(init());
-      ED_TRY(second_pass<T>(s, tb, bufs, psi, st, 0, k, n, cs));
+      ED_TRY(second_pass<T>(s, tb, bufs, psi, st, 0, k, n, part, part2, cs));
       mv += k - 1;
     }
     // normalise psi into the output
