@@ -150,6 +150,26 @@ def test_ns18_ground_state(ed):
     s.free()
 
 
+def test_ns18_partial_basis_equals_second_pass(ed):
+    """Ns=18 (two-pass product): psi from the part of the Krylov basis that
+    fits the default budget plus the second pass resumed from the last stored
+    pair, against no stored basis (the second pass from v_0); both second
+    passes run the first pass's product and update kernels.  The same psi
+    bit for bit, the same energies and residual, fewer products."""
+    wl = workload_ns18(0)
+    s = ed.Sector(wl.model, 9, 9)
+    pa = torch.empty(s.dim, dtype=torch.float64, device="cuda")
+    ra = ed.lanczos_ground(s, "fp32_polish", psi=pa)
+    pb = torch.empty(s.dim, dtype=torch.float64, device="cuda")
+    rb = ed.lanczos_ground(s, "fp32_polish", psi=pb, basis_mib=-1)
+    assert ra["e0"] == rb["e0"] and ra["e0_raw"] == rb["e0_raw"]
+    assert ra["residual"] == rb["residual"]
+    assert torch.equal(pa, pb)
+    assert ra["matvecs"] < rb["matvecs"]
+    del pa, pb
+    s.free()
+
+
 def test_chunked_elementwise_lanczos_against_tiled(ed):
     """Ns=15 (D = 41,409,225): the element-parallel product takes 3 elements
     per thread here (its Lanczos partials are capped at 2^16), so the
