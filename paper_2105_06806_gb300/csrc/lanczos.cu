@@ -320,10 +320,13 @@ __global__ void __launch_bounds__(AXPY_THREADS) k_axpy_norm(LanczosState *st, T 
   const typename VT::V *vv = reinterpret_cast<const typename VT::V *>(v);
   const typename VT::V *pv = reinterpret_cast<const typename VT::V *>(prev);
   typename VT::V *wv = reinterpret_cast<typename VT::V *>(w);
-  // second pass of a two-pass sector: psi += y_j v_j (the same operation as
-  // the fused second-pass epilogue of the product)
+  // second pass of a two-pass sector, every other step: psi += y_{j-1} v_{j-1}
+  // then psi += y_j v_j (v_{j-1} is read for the update anyway; the same two
+  // operations as two one-vector steps, so the same psi bit for bit, at half
+  // its traffic)
   typename VT::V *psv = reinterpret_cast<typename VT::V *>(psi);
   const T yj = psi ? (T)st->y[j] : T(0);
+  const T yp = psi && j > 0 ? (T)st->y[j - 1] : T(0);
   const int64_t nv = n / NV;
   double accd = 0.0, cvvd = 0.0;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -350,7 +353,10 @@ __global__ void __launch_bounds__(AXPY_THREADS) k_axpy_norm(LanczosState *st, T 
         T ps[NV];
         VT::get(psv[i], ps);
 #pragma unroll
-        for (int q = 0; q < NV; ++q) ps[q] = fmaT<T>(yj, vi[q], ps[q]);
+        for (int q = 0; q < NV; ++q) {
+          ps[q] = fmaT<T>(yp, mulT<T>(pr[q], s_prev), ps[q]);
+          ps[q] = fmaT<T>(yj, vi[q], ps[q]);
+        }
         psv[i] = VT::make(ps);
       }
     }
@@ -574,18 +580,25 @@ __global__ void k_second_resume(LanczosState *st, int m) {
     st->scale[(m - 1) % 3] = m == 1 ? s0 : (st->beta[m - 1] > 0.0 ? 1.0 / st->beta[m - 1] : 0.0);
 }
 
-// psi += y_j * scale * buf (last vector of the second pass).
+// psi += y_j * scale * buf (last vector of the second pass), preceded by
+// psi += y_{j-1} v_{j-1} when that vector is still pending (paired steps).
 template <typename T>
 __global__ void k_psi_tail(const LanczosState *st, const T *b0, const T *b1, const T *b2, T *psi,
-                           int64_t n) {
+                           int64_t n, int pending) {
   const int j = st->j;
   const T *bufs[3] = {b0, b1, b2};
   const T *v = bufs[j % 3];
   const T s = (T)st->scale[j % 3];
   const T y = (T)st->y[j];
+  const T *vp = bufs[(j + 2) % 3];
+  const T sp = (T)st->scale[(j + 2) % 3];
+  const T yp = pending && j > 0 ? (T)st->y[j - 1] : T(0);
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += stride)
-    psi[i] = fmaT<T>(y, mulT<T>(v[i], s), psi[i]);
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += stride) {
+    T p = psi[i];
+    if (pending) p = fmaT<T>(yp, mulT<T>(vp[i], sp), p);
+    psi[i] = fmaT<T>(y, mulT<T>(v[i], s), p);
+  }
 }
 
 template <typename Ti, typename To>
@@ -954,8 +967,10 @@ static ed_status second_pass(ed_sector s, const HvTables<T> &tb, T *const *bufs,
       int64_t np1 = 0;
       ED_TRY(ed_launch_hv<T>(s, tb, HV_LANCZOS, nullptr, nullptr, bufs, nullptr, st, part, &np1,
                              cs));
+      // psi takes v_{j-1} and v_j on every other step (see k_axpy_norm)
       k_axpy_norm<T><<<(unsigned)g, AXPY_THREADS, 0, cs>>>(st, bufs[0], bufs[1], bufs[2], nullptr,
-                                                            n, part2, psi);
+                                                            n, part2,
+                                                            ((j - j0) & 1) ? psi : nullptr);
       ED_LAUNCHED(1);
     } else {
       ED_TRY(ed_launch_hv<T>(s, tb, HV_SECOND, nullptr, nullptr, bufs, psi, st, nullptr, nullptr,
@@ -964,7 +979,11 @@ static ed_status second_pass(ed_sector s, const HvTables<T> &tb, T *const *bufs,
     k_second_advance<<<1, 1, 0, cs>>>(st);
     ED_LAUNCHED(1);
   }
-  k_psi_tail<T><<<(unsigned)g, AXPY_THREADS, 0, cs>>>(st, bufs[0], bufs[1], bufs[2], psi, n);
+  // with paired steps, v_{k-2} is still pending when the pass ran an odd
+  // number of steps
+  const int pending = split && ((k - 1 - j0) & 1) ? 1 : 0;
+  k_psi_tail<T><<<(unsigned)g, AXPY_THREADS, 0, cs>>>(st, bufs[0], bufs[1], bufs[2], psi, n,
+                                                       pending);
   ED_LAUNCHED(1);
   return ED_OK;
 }
