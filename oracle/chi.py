@@ -15,6 +15,14 @@ Operators (orbital-diagonal):
 Reading: the spin and charge functions use the connected operator
 O - <O> (for a hermitian O both terms then start from (O - <O>)|gs>, and the
 E_m = E0 component, which would make C(0) singular, is removed).
+
+Inter-orbital functions (Sec. 6.8, the auxiliary-operator construction of
+non-diagonal correlation functions): C_ab(z) = <A (z - (H - E0))^-1 B> -
+<B (z + (H - E0))^-1 A> for A = O_a, B = O_b from the chains of O_a + O_b,
+O_a and O_b.  Reading: for the real diagonal spin and charge operators, a
+real symmetric H and a real ground state, C_ab = C_ba, so the paper's second
+auxiliary operator A - iB is not needed and
+C_ab = [C(O_a + O_b) - C_aa - C_bb] / 2.
 """
 from __future__ import annotations
 
@@ -27,6 +35,10 @@ KINDS = ("spin", "charge", "pair")
 
 # sign with which the O|gs> chain enters C_O (bosonic: +, see the module text)
 HOLE_TERM_SIGN = +1.0
+
+# C_ab = c0 C(O_a + O_b) + c1 C_aa + c2 C_bb (the auxiliary-operator
+# construction, real form: see the module text)
+AB_COEFFS = (0.5, -0.5, -0.5)
 
 
 def diagonal_values(model, nup, ndw, kind, orb):
@@ -41,11 +53,18 @@ def diagonal_values(model, nup, ndw, kind, orb):
     raise ValueError(kind)
 
 
+def diagonal_values_sum(model, nup, ndw, kind, orbs):
+    """O_{a_1} + O_{a_2} + ... on every basis state (orbitals may repeat)."""
+    return sum(diagonal_values(model, nup, ndw, kind, a) for a in orbs)
+
+
 def start_vectors(model, nup, ndw, psi, kind, orb):
     """[(vector, (nup', ndw'), create)] for the two terms: create = +1 for
-    O^+|gs>, -1 for O|gs>."""
+    O^+|gs>, -1 for O|gs>.  For spin and charge, `orb` may be a tuple of
+    orbitals: O is then the sum of their operators."""
     if kind in ("spin", "charge"):
-        o = diagonal_values(model, nup, ndw, kind, orb)
+        orbs = orb if isinstance(orb, tuple) else (orb,)
+        o = diagonal_values_sum(model, nup, ndw, kind, orbs)
         avg = float(psi @ (o * psi)) / float(psi @ psi)
         phi = (o - avg) * psi
         return [(phi, (nup, ndw), +1), (phi, (nup, ndw), -1)]
@@ -105,3 +124,34 @@ def lehmann_chi_z(model, nup, ndw, kind, orb, z):
         else:
             C -= (w[None, :] / (z[:, None] + (E1 - e0)[None, :])).sum(1)
     return C, e0
+
+
+def chi_ab_z(model, nup, ndw, psi, e0, kind, a, b, z, nsteps=200):
+    """Inter-orbital C_ab(z) for kind = spin or charge, from the chains of
+    O_a + O_b, O_a and O_b (the auxiliary-operator construction, real form:
+    see the module text)."""
+    if kind not in ("spin", "charge"):
+        raise ValueError(kind)
+    cs = chi_z(model, nup, ndw, psi, e0, kind, (a, b), z, nsteps)
+    ca = chi_z(model, nup, ndw, psi, e0, kind, a, z, nsteps)
+    cb = chi_z(model, nup, ndw, psi, e0, kind, b, z, nsteps)
+    c0, c1, c2 = AB_COEFFS
+    return c0 * cs + c1 * ca + c2 * cb
+
+
+def lehmann_chi_ab_z(model, nup, ndw, kind, a, b, z):
+    """The exact T = 0 off-diagonal function from dense eigenvectors:
+    sum_m <0|A|m><m|B|0> [1/(z - (E_m - E0)) - 1/(z + (E_m - E0))] with the
+    connected A = O_a - <O_a>, B = O_b - <O_b>."""
+    z = np.asarray(z, dtype=np.complex128)
+    s0 = fock.get_sector(model, nup, ndw)
+    E, U = np.linalg.eigh(s0.hamiltonian().toarray())
+    gs = U[:, 0]
+    oa = diagonal_values(model, nup, ndw, kind, a)
+    ob = diagonal_values(model, nup, ndw, kind, b)
+    pa = (oa - gs @ (oa * gs)) * gs
+    pb = (ob - gs @ (ob * gs)) * gs
+    wa, wb = U.T @ pa, U.T @ pb
+    d = E - E[0]
+    w = wa * wb
+    return (w[None, :] * (1.0 / (z[:, None] - d[None, :]) - 1.0 / (z[:, None] + d[None, :]))).sum(1)

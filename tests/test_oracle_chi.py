@@ -10,7 +10,12 @@
     - sum_{k, q occ} (u_k u_q)^2 / (z - (e_k + e_q));
 * the atom: an empty level e with interaction U has the pair function
   1 / (z - (2e + U));
-* C(i nu) of a hermitian operator is real, even in nu and negative.
+* C(i nu) of a hermitian operator is real, even in nu and negative;
+* inter-orbital C_ab (spin, charge) from the chains of O_a + O_b, O_a, O_b
+  = the exact off-diagonal Lehmann sum; C_ab = C_ba; C_aa = the one-orbital
+  function; C_ab = 0 at U = 0 with each orbital on its own bath (the
+  particle-hole excitations of the two orbitals never mix), while each
+  orbital's own function does not vanish.
 """
 import numpy as np
 import pytest
@@ -103,3 +108,34 @@ def test_hermitian_functions_real_even_negative(kind):
     assert np.abs(Cp.imag).max() < 1e-12
     assert np.abs(Cp - Cm).max() < 1e-12
     assert np.all(Cp.real < 0)
+
+
+@pytest.mark.parametrize("kind", ("spin", "charge"))
+def test_inter_orbital_chains_equal_lehmann_sum(kind):
+    m = _asym(make_model(2, 2, U=2.4, Jh=0.4, seed=44), 44)
+    fock._SECTOR_CACHE.clear()
+    s = fock.Sector(m, 3, 2)
+    r = lanczos.ground_state(s.matvec, s.dim)
+    C01 = chi.chi_ab_z(m, 3, 2, r["psi"], r["e0"], kind, 0, 1, Z, nsteps=120)
+    C10 = chi.chi_ab_z(m, 3, 2, r["psi"], r["e0"], kind, 1, 0, Z, nsteps=120)
+    Cx = chi.lehmann_chi_ab_z(m, 3, 2, kind, 0, 1, Z)
+    assert np.abs(Cx).max() > 1e-3                 # a non-trivial function here
+    assert np.abs(C01 - Cx).max() < 1e-10
+    assert np.abs(C01 - C10).max() < 1e-12
+    Caa = chi.chi_ab_z(m, 3, 2, r["psi"], r["e0"], kind, 1, 1, Z, nsteps=120)
+    C1 = chi.chi_z(m, 3, 2, r["psi"], r["e0"], kind, 1, Z, nsteps=120)
+    assert np.abs(Caa - C1).max() < 1e-10
+
+
+@pytest.mark.parametrize("kind", ("spin", "charge"))
+def test_inter_orbital_function_vanishes_at_u0(kind):
+    b = make_model(2, 3, U=0.0, Jh=0.0, seed=45)
+    m = _asym(ImpurityModel(norb=2, nbath=3, U=0.0, Ust=0.0, Jh=0.0, e_imp=b.e_imp,
+                            e_bath=b.e_bath, v_bath=b.v_bath), 45)
+    fock._SECTOR_CACHE.clear()
+    s = fock.Sector(m, 4, 3)
+    r = lanczos.ground_state(s.matvec, s.dim)
+    C01 = chi.chi_ab_z(m, 4, 3, r["psi"], r["e0"], kind, 0, 1, Z, nsteps=200)
+    C0 = chi.chi_z(m, 4, 3, r["psi"], r["e0"], kind, 0, Z, nsteps=200)
+    assert np.abs(C0).max() > 1e-2
+    assert np.abs(C01).max() < 1e-9

@@ -338,3 +338,37 @@ def test_fermionic_sign_in_susceptibility_is_caught(monkeypatch):
     assert err() < 1e-9
     monkeypatch.setattr(chi, "HOLE_TERM_SIGN", -1.0)
     assert err() > 1e-3
+
+
+def test_wrong_inter_orbital_combination_is_caught(monkeypatch):
+    """The auxiliary-operator combination of the inter-orbital function with
+    its 1/2 dropped no longer matches the exact off-diagonal Lehmann sum, and
+    with the sign of C_bb flipped it no longer vanishes at U = 0 (orbitals on
+    their own baths)."""
+    from oracle import chi
+    from workloads import ImpurityModel
+    z = 1j * 2 * np.pi * np.arange(1, 20) / 10.0
+    m = make_model(2, 2, U=2.4, Jh=0.4, seed=44)
+    fock._SECTOR_CACHE.clear()
+    s = fock.Sector(m, 3, 2)
+    r = lanczos.ground_state(s.matvec, s.dim)
+    want = chi.lehmann_chi_ab_z(m, 3, 2, "spin", 0, 1, z)
+
+    def err_lehmann():
+        return np.abs(chi.chi_ab_z(m, 3, 2, r["psi"], r["e0"], "spin", 0, 1, z, nsteps=120)
+                      - want).max()
+    b = make_model(2, 3, U=0.0, Jh=0.0, seed=45)
+    m0 = ImpurityModel(norb=2, nbath=3, U=0.0, Ust=0.0, Jh=0.0, e_imp=b.e_imp,
+                       e_bath=b.e_bath, v_bath=b.v_bath)
+    fock._SECTOR_CACHE.clear()
+    s0 = fock.Sector(m0, 4, 3)
+    r0 = lanczos.ground_state(s0.matvec, s0.dim)
+
+    def size_u0():
+        return np.abs(chi.chi_ab_z(m0, 4, 3, r0["psi"], r0["e0"], "charge", 0, 1, z,
+                                   nsteps=200)).max()
+    assert err_lehmann() < 1e-10 and size_u0() < 1e-9
+    monkeypatch.setattr(chi, "AB_COEFFS", (1.0, -1.0, -1.0))
+    assert err_lehmann() > 1e-3
+    monkeypatch.setattr(chi, "AB_COEFFS", (0.5, -0.5, 0.5))
+    assert size_u0() > 1e-3
