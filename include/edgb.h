@@ -350,6 +350,20 @@ ed_status ed_chi_z(ed_sector s, ed_precision prec, const void *d_psi, double e0,
                    int32_t orb, int32_t nsteps, const double *host_z, int32_t nz, double *host_C,
                    double *host_w, void *stream);
 
+/* Inter-orbital spin or charge function (Sec. 6.8, the auxiliary-operator
+ * construction of non-diagonal correlation functions):
+ *   C_ab(z) = <A (z - (H - E0))^-1 B> - <B (z + (H - E0))^-1 A>,
+ * A = O_a - <O_a>, B = O_b - <O_b>, O the ED_CHI_SPIN or ED_CHI_CHARGE
+ * operator of one orbital, from the chains of O_a + O_b, O_a and O_b:
+ * C_ab = [C(O_a + O_b) - C_aa - C_bb] / 2 (for these real operators and a
+ * real symmetric H, C_ab = C_ba, so the paper's second auxiliary operator
+ * A - iB is not needed); orb_a = orb_b gives ed_chi_z's C_aa.  Arguments,
+ * precisions and outputs as ed_chi_z (no weights); ED_ERR_ARG for
+ * ED_CHI_PAIR or an orbital out of range.  Synchronises `stream`. */
+ed_status ed_chi_ab_z(ed_sector s, ed_precision prec, const void *d_psi, double e0, int32_t kind,
+                      int32_t orb_a, int32_t orb_b, int32_t nsteps, const double *host_z,
+                      int32_t nz, double *host_C, void *stream);
+
 /* ---------------------------------------------------------------- several states, finite T
  * The nstates lowest eigenpairs of the sector (the states of the eigenspace
  * list, Sec. 6.2; the paper takes them from P-ARPACK, Sec. 5): Lanczos on

@@ -31,7 +31,7 @@ EXPORTED = [
     "ed_sector_permute", "ed_lanczos_ground", "ed_gf_lanczos", "ed_gf_lanczos_z", "ed_sigma",
     "ed_observables", "ed_solve", "ed_eph_matvec", "ed_eph_lanczos_ground",
     "ed_eph_gf_lanczos_z", "ed_lanczos_states", "ed_espace_truncate", "ed_gf_thermal_z",
-    "ed_chi_z", "ed_orbital_sector_dims", "ed_lanczos_ground_orbital",
+    "ed_chi_z", "ed_chi_ab_z", "ed_orbital_sector_dims", "ed_lanczos_ground_orbital",
     "ed_server_create", "ed_submit", "ed_poll", "ed_wait", "ed_server_destroy",
     "ed_server_inject_alloc_failure", "ed_batch_stats", "ed_residual_noalloc", "ed_status_string",
     "ed_last_error",
@@ -193,6 +193,7 @@ def lib():
             "ed_gf_thermal_z": [i32, vp, vp, vp, C.c_double, C.c_double, i32, C.c_int, i32, i32,
                                 i32, vp, i32, vp, vp, vp],
             "ed_chi_z": [vp, C.c_int, vp, C.c_double, i32, i32, i32, vp, i32, vp, vp, vp],
+            "ed_chi_ab_z": [vp, C.c_int, vp, C.c_double, i32, i32, i32, i32, vp, i32, vp, vp],
             "ed_orbital_sector_dims": [vp, vp, vp, C.POINTER(i64), C.POINTER(i64)],
             "ed_lanczos_ground_orbital": [vp, vp, vp, C.POINTER(ed_lanczos_opts),
                                           C.POINTER(ed_lanczos_result), vp, vp],
@@ -576,6 +577,19 @@ def chi_z(sector: Sector, psi, e0, kind, orb, z, precision="fp64", nsteps=200, s
                           int(zz.size), C.c_void_p(out.ctypes.data), C.c_void_p(w.ctypes.data),
                           C.c_void_p(_stream_ptr(stream))), "ed_chi_z")
     return out, (float(w[0]), float(w[1]))
+
+
+def chi_ab_z(sector: Sector, psi, e0, kind, orb_a, orb_b, z, precision="fp64", nsteps=200,
+             stream=None):
+    """Inter-orbital spin or charge function C_ab(z) at T = 0 (ed_chi_ab_z)."""
+    zz = np.ascontiguousarray(np.asarray(z, dtype=np.complex128).reshape(-1))
+    out = np.zeros(zz.size, dtype=np.complex128)
+    _check(lib().ed_chi_ab_z(sector.h, _prec(precision), _psi_ptr(psi, precision), float(e0),
+                             CHI_KINDS[kind], int(orb_a), int(orb_b), int(nsteps),
+                             C.c_void_p(zz.ctypes.data), int(zz.size),
+                             C.c_void_p(out.ctypes.data), C.c_void_p(_stream_ptr(stream))),
+           "ed_chi_ab_z")
+    return out
 
 
 def lanczos_states(sector: Sector, nstates, precision="fp64", max_iter=0, tol=0.0,

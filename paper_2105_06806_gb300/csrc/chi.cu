@@ -29,13 +29,19 @@ struct OTable {
   double v[1 << ED_MAX_NORB][1 << ED_MAX_NORB];  // O on impurity masks (m_up, m_dw)
 };
 
-OTable make_table(int norb, int kind, int orb) {
+// O = sum_a wts[a] O_a on the impurity masks (O_a the spin or charge
+// operator of orbital a)
+OTable make_table(int norb, int kind, const int *wts) {
   OTable t;
   memset(&t, 0, sizeof(t));
   for (int mu = 0; mu < (1 << norb); ++mu)
     for (int md = 0; md < (1 << norb); ++md) {
-      const double nu = (mu >> orb) & 1, nd = (md >> orb) & 1;
-      t.v[mu][md] = kind == ED_CHI_SPIN ? 0.5 * (nu - nd) : nu + nd;
+      double v = 0.0;
+      for (int a = 0; a < norb; ++a) {
+        const double nu = (mu >> a) & 1, nd = (md >> a) & 1;
+        v += wts[a] * (kind == ED_CHI_SPIN ? 0.5 * (nu - nd) : nu + nd);
+      }
+      t.v[mu][md] = v;
     }
   return t;
 }
@@ -122,7 +128,7 @@ struct Mem {
 template <typename T>
 ed_status chain_and_cfrac(ed_sector nb, const T *phi, int nsteps, double e0, const double2 *dz,
                           int nz, bool both, int which, double2 *dC, LanczosState *st,
-                          double *weight, cudaStream_t cs) {
+                          double *weight, cudaStream_t cs, double coef = 1.0) {
   ED_TRY(ed_build_items(nb, 1, (int)sizeof(T)));
   // FP32 chains run on H - e0, with the one-body diagonal tables shifted in
   // FP64 before their rounding (as the Green's-function chains)
@@ -147,17 +153,21 @@ ed_status chain_and_cfrac(ed_sector nb, const T *phi, int nsteps, double e0, con
   // n+ [(e0 + z - T)^-1]_00 (sgn +1) and + n- [(e0 - z - T)^-1]_00: the
   // launcher adds sgn * weight * [(e0 + sgn z - T)^-1]_00, so the second
   // term takes sgn = -1 with weight -n-
-  if (both || which > 0) ED_TRY(ed_cfrac_z_launch(st, run.weight, e0, dz, nz, +1, dC, cs));
-  if (both || which < 0) ED_TRY(ed_cfrac_z_launch(st, -run.weight, e0, dz, nz, -1, dC, cs));
+  if (both || which > 0) ED_TRY(ed_cfrac_z_launch(st, coef * run.weight, e0, dz, nz, +1, dC, cs));
+  if (both || which < 0) ED_TRY(ed_cfrac_z_launch(st, -coef * run.weight, e0, dz, nz, -1, dC, cs));
   return ED_OK;
 }
 
+// (spin and charge: O = sum_a wts[a] O_a, nullable wts = orbital `orb` alone;
+// the chain's terms enter C with the factor `coef`)
 template <typename Ti, typename To>
 ed_status chi_impl(ed_sector s, ed_precision prec, const Ti *psi, double e0, int kind, int orb,
                    int nsteps, const double2 *dz, int nz, double2 *dC, LanczosState *st,
-                   double *w, cudaStream_t cs) {
+                   double *w, cudaStream_t cs, const int *wts = nullptr, double coef = 1.0) {
   if (kind == ED_CHI_SPIN || kind == ED_CHI_CHARGE) {
-    const OTable ot = make_table(s->mp.norb, kind, orb);
+    int one[ED_MAX_NORB] = {0};
+    one[orb] = 1;
+    const OTable ot = make_table(s->mp.norb, kind, wts ? wts : one);
     const int64_t n = s->dim, bn = s->bdim, dup = s->sp[0].dim, ddw = s->sp[1].dim;
     Mem scratch, phi;
     ED_TRY(scratch.alloc((2 * CHI_PARTS + 8) * sizeof(double), cs, "susceptibility partials"));
@@ -177,7 +187,8 @@ ed_status chi_impl(ed_sector s, ed_precision prec, const Ti *psi, double e0, int
                                               s->bstride, ddw, ot, avg);
     ED_LAUNCHED(1);
     double wt = 0.0;
-    ED_TRY(chain_and_cfrac<To>(s, (const To *)phi.p, nsteps, e0, dz, nz, true, 0, dC, st, &wt, cs));
+    ED_TRY(chain_and_cfrac<To>(s, (const To *)phi.p, nsteps, e0, dz, nz, true, 0, dC, st, &wt, cs,
+                               coef));
     w[0] = w[1] = wt;
     return ED_OK;
   }
@@ -206,6 +217,47 @@ ed_status chi_impl(ed_sector s, ed_precision prec, const Ti *psi, double e0, int
   return ED_OK;
 }
 
+// The device buffers of a susceptibility call (the frequencies, the
+// accumulated C, one Lanczos state) around `run`, then C and the weights to
+// the host.
+template <typename F>
+ed_status chi_call(const double *host_z, int32_t nz, double *host_C, double *host_w,
+                   cudaStream_t cs, F run) {
+  Mem buf;
+  const size_t zb = (size_t)std::max(nz, 1) * sizeof(double2);
+  ED_TRY(buf.alloc(2 * zb + ((sizeof(LanczosState) + 255) & ~(size_t)255), cs, "susceptibility"));
+  double2 *dz = (double2 *)buf.p, *dC = (double2 *)((char *)buf.p + zb);
+  LanczosState *st = (LanczosState *)((char *)buf.p + 2 * zb);
+  if (nz > 0) {
+    ED_TRY_CUDA(cudaMemcpyAsync(dz, host_z, nz * sizeof(double2), cudaMemcpyHostToDevice, cs));
+    ED_TRY_CUDA(cudaMemsetAsync(dC, 0, nz * sizeof(double2), cs));
+  }
+  double w[2] = {0.0, 0.0};
+  ED_TRY(run(dz, dC, st, w));
+  if (nz > 0)
+    ED_TRY_CUDA(cudaMemcpyAsync(host_C, dC, nz * sizeof(double2), cudaMemcpyDeviceToHost, cs));
+  ED_TRY_CUDA(cudaStreamSynchronize(cs));
+  if (host_w) {
+    host_w[0] = w[0];
+    host_w[1] = w[1];
+  }
+  return ED_OK;
+}
+
+// chi_impl in the precisions of `prec`
+ed_status chi_prec(ed_sector s, ed_precision prec, const void *d_psi, double e0, int kind, int orb,
+                   int nsteps, const double2 *dz, int nz, double2 *dC, LanczosState *st,
+                   double *w, cudaStream_t cs, const int *wts = nullptr, double coef = 1.0) {
+  if (prec == ED_FP64)
+    return chi_impl<double, double>(s, prec, (const double *)d_psi, e0, kind, orb, nsteps, dz, nz,
+                                    dC, st, w, cs, wts, coef);
+  if (prec == ED_FP32)
+    return chi_impl<float, float>(s, prec, (const float *)d_psi, e0, kind, orb, nsteps, dz, nz, dC,
+                                  st, w, cs, wts, coef);
+  return chi_impl<double, float>(s, prec, (const double *)d_psi, e0, kind, orb, nsteps, dz, nz, dC,
+                                 st, w, cs, wts, coef);
+}
+
 }  // namespace
 
 extern "C" ed_status ed_chi_z(ed_sector s, ed_precision prec, const void *d_psi, double e0,
@@ -218,31 +270,38 @@ extern "C" ed_status ed_chi_z(ed_sector s, ed_precision prec, const void *d_psi,
   if (nsteps <= 0) nsteps = 200;
   if (nsteps > ED_MAX_LANCZOS) return ED_ERR_ARG;
   cudaStream_t cs = (cudaStream_t)stream;
-  Mem buf;
-  const size_t zb = (size_t)std::max(nz, 1) * sizeof(double2);
-  ED_TRY(buf.alloc(2 * zb + ((sizeof(LanczosState) + 255) & ~(size_t)255), cs, "susceptibility"));
-  double2 *dz = (double2 *)buf.p, *dC = (double2 *)((char *)buf.p + zb);
-  LanczosState *st = (LanczosState *)((char *)buf.p + 2 * zb);
-  if (nz > 0) {
-    ED_TRY_CUDA(cudaMemcpyAsync(dz, host_z, nz * sizeof(double2), cudaMemcpyHostToDevice, cs));
-    ED_TRY_CUDA(cudaMemsetAsync(dC, 0, nz * sizeof(double2), cs));
-  }
-  double w[2] = {0.0, 0.0};
-  if (prec == ED_FP64)
-    ED_TRY((chi_impl<double, double>(s, prec, (const double *)d_psi, e0, kind, orb, nsteps, dz, nz,
-                                     dC, st, w, cs)));
-  else if (prec == ED_FP32)
-    ED_TRY((chi_impl<float, float>(s, prec, (const float *)d_psi, e0, kind, orb, nsteps, dz, nz,
-                                   dC, st, w, cs)));
-  else
-    ED_TRY((chi_impl<double, float>(s, prec, (const double *)d_psi, e0, kind, orb, nsteps, dz, nz,
-                                    dC, st, w, cs)));
-  if (nz > 0)
-    ED_TRY_CUDA(cudaMemcpyAsync(host_C, dC, nz * sizeof(double2), cudaMemcpyDeviceToHost, cs));
-  ED_TRY_CUDA(cudaStreamSynchronize(cs));
-  if (host_w) {
-    host_w[0] = w[0];
-    host_w[1] = w[1];
-  }
-  return ED_OK;
+  return chi_call(host_z, nz, host_C, host_w, cs,
+                  [&](const double2 *dz, double2 *dC, LanczosState *st, double *w) {
+                    return chi_prec(s, prec, d_psi, e0, kind, orb, nsteps, dz, nz, dC, st, w, cs);
+                  });
+}
+
+// Inter-orbital spin / charge function: the auxiliary-operator construction
+// of Sec. 6.8, C_ab = [C(O_a + O_b) - C_aa - C_bb] / 2 (real operators, real
+// symmetric H: C_ab = C_ba), three chains accumulated into one C.
+extern "C" ed_status ed_chi_ab_z(ed_sector s, ed_precision prec, const void *d_psi, double e0,
+                                 int32_t kind, int32_t orb_a, int32_t orb_b, int32_t nsteps,
+                                 const double *host_z, int32_t nz, double *host_C, void *stream) {
+  if (!s || !d_psi || !host_C || nz < 0 || (nz > 0 && !host_z)) return ED_ERR_ARG;
+  if (kind != ED_CHI_SPIN && kind != ED_CHI_CHARGE) return ED_ERR_ARG;
+  const int norb = s->mp.norb;
+  if (orb_a < 0 || orb_a >= norb || orb_b < 0 || orb_b >= norb) return ED_ERR_ARG;
+  if (prec != ED_FP64 && prec != ED_FP32 && prec != ED_FP32_POLISH) return ED_ERR_ARG;
+  if (nsteps <= 0) nsteps = 200;
+  if (nsteps > ED_MAX_LANCZOS) return ED_ERR_ARG;
+  cudaStream_t cs = (cudaStream_t)stream;
+  int wab[ED_MAX_NORB] = {0}, wa[ED_MAX_NORB] = {0}, wb[ED_MAX_NORB] = {0};
+  wab[orb_a] += 1;
+  wab[orb_b] += 1;  // a = b: 2 O_a, and the combination gives C_aa
+  wa[orb_a] = 1;
+  wb[orb_b] = 1;
+  return chi_call(host_z, nz, host_C, nullptr, cs,
+                  [&](const double2 *dz, double2 *dC, LanczosState *st, double *w) {
+                    ED_TRY(chi_prec(s, prec, d_psi, e0, kind, orb_a, nsteps, dz, nz, dC, st, w,
+                                    cs, wab, 0.5));
+                    ED_TRY(chi_prec(s, prec, d_psi, e0, kind, orb_a, nsteps, dz, nz, dC, st, w,
+                                    cs, wa, -0.5));
+                    return chi_prec(s, prec, d_psi, e0, kind, orb_b, nsteps, dz, nz, dC, st, w, cs,
+                                    wb, -0.5);
+                  });
 }

@@ -2,7 +2,10 @@
 functions against the oracle (oracle/chi.py, pinned by
 tests/test_oracle_chi.py): the same two-chain algorithm, FP64 <= 1e-8 on the
 Matsubara axis and the real axis at eta = 0.5; FP32 chains on the polished
-state <= 3e-5; the empty-atom pair function 1/(z - (2e + U))."""
+state <= 1e-5 (relative); the empty-atom pair function 1/(z - (2e + U));
+inter-orbital spin and charge functions (ed_chi_ab_z) against the oracle's
+auxiliary-operator construction, C_aa = ed_chi_z, C_ab = C_ba, and C_ab = 0
+at U = 0 with each orbital on its own bath."""
 import numpy as np
 import pytest
 import torch
@@ -65,4 +68,48 @@ def test_pair_function_of_the_empty_atom(ed):
     C, w = ed.chi_z(s, psi, 0.0, "pair", 0, Z, "fp64", nsteps=4)
     assert np.abs(C - 1.0 / (Z - (2 * e + U))).max() < 1e-14
     assert w == (1.0, 0.0)
+    s.free()
+
+
+@pytest.mark.parametrize("case", ["norb2_ns8", "norb2_ns10", "kanamori_ns9"])
+@pytest.mark.parametrize("kind", ("spin", "charge"))
+def test_inter_orbital_chi_against_oracle(ed, case, kind):
+    m, nup, ndw = CASES[case]
+    fock._SECTOR_CACHE.clear()
+    ref = fock.Sector(m, nup, ndw)
+    ro = lanczos.ground_state(ref.matvec, ref.dim)
+    s = ed.Sector(m, nup, ndw)
+    psi = torch.empty(s.dim, dtype=torch.float64, device="cuda")
+    r = ed.lanczos_ground(s, "fp64", psi=psi)
+    Co = chi.chi_ab_z(m, nup, ndw, ro["psi"], ro["e0"], kind, 0, 1, Z, nsteps=150)
+    C01 = ed.chi_ab_z(s, psi, r["e0"], kind, 0, 1, Z, "fp64", nsteps=150)
+    C10 = ed.chi_ab_z(s, psi, r["e0"], kind, 1, 0, Z, "fp64", nsteps=150)
+    scale = max(1.0, np.abs(Co).max())
+    assert np.abs(C01 - Co).max() <= 1e-8 * scale
+    assert np.abs(C01 - C10).max() <= 1e-10 * scale
+    C11 = ed.chi_ab_z(s, psi, r["e0"], kind, 1, 1, Z, "fp64", nsteps=150)
+    C1, _ = ed.chi_z(s, psi, r["e0"], kind, 1, Z, "fp64", nsteps=150)
+    assert np.abs(C11 - C1).max() <= 1e-10 * max(1.0, np.abs(C1).max())
+    # FP32 chains from the polished state
+    psi2 = torch.empty(s.dim, dtype=torch.float64, device="cuda")
+    r2 = ed.lanczos_ground(s, "fp32_polish", psi=psi2)
+    C2 = ed.chi_ab_z(s, psi2, r2["e0"], kind, 0, 1, Z, "fp32_polish", nsteps=150)
+    assert np.abs(C2 - Co).max() <= 1e-5 * scale
+    with pytest.raises(ed.EDError):
+        ed.chi_ab_z(s, psi, r["e0"], "pair", 0, 1, Z, "fp64")
+    s.free()
+
+
+@pytest.mark.parametrize("kind", ("spin", "charge"))
+def test_inter_orbital_chi_vanishes_at_u0(ed, kind):
+    b = make_model(2, 3, U=0.0, Jh=0.0, seed=45)
+    m = _asym(ImpurityModel(norb=2, nbath=3, U=0.0, Ust=0.0, Jh=0.0, e_imp=b.e_imp,
+                            e_bath=b.e_bath, v_bath=b.v_bath), 45)
+    s = ed.Sector(m, 4, 3)
+    psi = torch.empty(s.dim, dtype=torch.float64, device="cuda")
+    r = ed.lanczos_ground(s, "fp64", psi=psi)
+    C01 = ed.chi_ab_z(s, psi, r["e0"], kind, 0, 1, Z, "fp64", nsteps=200)
+    C0, _ = ed.chi_z(s, psi, r["e0"], kind, 0, Z, "fp64", nsteps=200)
+    assert np.abs(C0).max() > 1e-2
+    assert np.abs(C01).max() < 1e-8
     s.free()
