@@ -16,6 +16,12 @@ Reading: the spin and charge functions use the connected operator
 O - <O> (for a hermitian O both terms then start from (O - <O>)|gs>, and the
 E_m = E0 component, which would make C(0) singular, is removed).
 
+Excitonic function (Sec. 6.8 names it among the susceptibilities).  Reading:
+the singlet inter-orbital particle-hole operator of an orbital pair a != b,
+O = sum_sigma (c^+_{a sigma} c_{b sigma} + c^+_{b sigma} c_{a sigma}),
+hermitian and real, keeping (N_up, N_dw); its connected function from two
+chains of (O - <O>)|gs> like the spin and charge functions.
+
 Inter-orbital functions (Sec. 6.8, the auxiliary-operator construction of
 non-diagonal correlation functions): C_ab(z) = <A (z - (H - E0))^-1 B> -
 <B (z + (H - E0))^-1 A> for A = O_a, B = O_b from the chains of O_a + O_b,
@@ -154,4 +160,71 @@ def lehmann_chi_ab_z(model, nup, ndw, kind, a, b, z):
     wa, wb = U.T @ pa, U.T @ pb
     d = E - E[0]
     w = wa * wb
+    return (w[None, :] * (1.0 / (z[:, None] - d[None, :]) - 1.0 / (z[:, None] + d[None, :]))).sum(1)
+
+
+def move_sign(I, between):
+    """(-1)^(occupied levels of string I in the mask `between`): the sign of
+    moving one electron between the two levels that bound the mask."""
+    return -1.0 if fock.popcount(I & between) & 1 else 1.0
+
+
+def exciton_matrix(model, nup, ndw, a, b):
+    """The excitonic operator O = sum_sigma (c^+_a c_b + c^+_b c_a) of the
+    impurity orbitals a != b on the sector (sector order), built string by
+    string: moving an electron between levels a and b of one spin string
+    takes the sign (-1)^(occupied levels strictly between them); the dw
+    operators' Jordan-Wigner signs from the up string cancel in pairs."""
+    import scipy.sparse as sp
+    s = fock.get_sector(model, nup, ndw)
+    la, lb = fock.level_of_impurity(model, a), fock.level_of_impurity(model, b)
+    lo, hi = min(la, lb), max(la, lb)
+    between = ((1 << hi) - 1) & ~((1 << (lo + 1)) - 1)
+
+    def moves(smap):
+        out = []
+        for i, I in enumerate(smap):
+            I = int(I)
+            for src, dst in ((lb, la), (la, lb)):
+                if (I >> src) & 1 and not (I >> dst) & 1:
+                    J = I ^ (1 << src) ^ (1 << dst)
+                    out.append((fock.binary_search(smap, J), i, move_sign(I, between)))
+        return out
+    rows, cols, vals = [], [], []
+    du, dd = s.dim_up, s.dim_dw
+    for j, i, sgn in moves(s.map_up):          # up moves: same dw string
+        for r in range(dd):
+            rows.append(r * du + j); cols.append(r * du + i); vals.append(sgn)
+    for j, i, sgn in moves(s.map_dw):          # dw moves: same up string
+        for c in range(du):
+            rows.append(j * du + c); cols.append(i * du + c); vals.append(sgn)
+    return sp.csr_matrix((vals, (rows, cols)), shape=(s.dim, s.dim))
+
+
+def chi_exciton_z(model, nup, ndw, psi, e0, a, b, z, nsteps=200):
+    """Excitonic C_O(z) of the orbital pair (a, b) from the two chains of the
+    connected (O - <O>)|gs> (bosonic sign, as chi_z)."""
+    z = np.asarray(z, dtype=np.complex128)
+    O = exciton_matrix(model, nup, ndw, a, b)
+    avg = float(psi @ (O @ psi)) / float(psi @ psi)
+    phi = O @ psi - avg * psi
+    nrm2 = float(phi @ phi)
+    if nrm2 == 0.0:
+        return np.zeros(z.shape, dtype=np.complex128)
+    sec = fock.get_sector(model, nup, ndw)
+    al, be = lanczos_chain(sec.matvec, phi, nsteps)
+    return nrm2 * gf.continued_fraction(al, be, e0 + z) + \
+        HOLE_TERM_SIGN * nrm2 * gf.continued_fraction(al, be, e0 - z)
+
+
+def lehmann_chi_exciton_z(model, nup, ndw, a, b, z):
+    """The exact T = 0 excitonic function from dense eigenvectors."""
+    z = np.asarray(z, dtype=np.complex128)
+    s0 = fock.get_sector(model, nup, ndw)
+    E, U = np.linalg.eigh(s0.hamiltonian().toarray())
+    gs = U[:, 0]
+    O = exciton_matrix(model, nup, ndw, a, b).toarray()
+    phi = O @ gs - (gs @ O @ gs) * gs
+    w = (U.T @ phi) ** 2
+    d = E - E[0]
     return (w[None, :] * (1.0 / (z[:, None] - d[None, :]) - 1.0 / (z[:, None] + d[None, :]))).sum(1)

@@ -15,7 +15,12 @@
   = the exact off-diagonal Lehmann sum; C_ab = C_ba; C_aa = the one-orbital
   function; C_ab = 0 at U = 0 with each orbital on its own bath (the
   particle-hole excitations of the two orbitals never mix), while each
-  orbital's own function does not vanish.
+  orbital's own function does not vanish;
+* excitonic function (singlet inter-orbital particle-hole operator) = the
+  exact Lehmann sum, and at U = 0 = the closed form from the one-body
+  eigenvectors (Wick: sum over particle-hole pairs of |<l|o|k>|^2, o the
+  one-body matrix of the operator), for a pair with a level between them
+  (the fermionic sign matters) and an adjacent pair.
 """
 import numpy as np
 import pytest
@@ -139,3 +144,49 @@ def test_inter_orbital_function_vanishes_at_u0(kind):
     C0 = chi.chi_z(m, 4, 3, r["psi"], r["e0"], kind, 0, Z, nsteps=200)
     assert np.abs(C0).max() > 1e-2
     assert np.abs(C01).max() < 1e-9
+
+
+def _exciton_u0_closed_form(m, nup, ndw, a, b, z):
+    """sum_sigma sum_{k occupied, l empty} |(U^T o U)_{lk}|^2
+    [1/(z - (e_l - e_k)) - 1/(z + (e_l - e_k))] with o the one-body matrix of
+    c^+_a c_b + c^+_b c_a (levels a, b are the impurity orbitals)."""
+    want = np.zeros(z.shape, dtype=np.complex128)
+    for spin, n in ((0, nup), (1, ndw)):
+        e, U = _one_body(m, spin)
+        o = np.zeros((len(e), len(e)))
+        la, lb = fock.level_of_impurity(m, a), fock.level_of_impurity(m, b)
+        o[la, lb] = o[lb, la] = 1.0
+        M = U.T @ o @ U
+        for k in range(n):
+            for l in range(n, len(e)):
+                d = e[l] - e[k]
+                want += M[l, k] ** 2 * (1 / (z - d) - 1 / (z + d))
+    return want
+
+
+@pytest.mark.parametrize("pair", [(0, 2), (0, 1)])
+def test_exciton_chains_equal_lehmann_sum(pair):
+    a, b = pair
+    m = _asym(make_model(3, 1, U=2.2, Jh=0.3, seed=46), 46)
+    fock._SECTOR_CACHE.clear()
+    s = fock.Sector(m, 3, 2)
+    r = lanczos.ground_state(s.matvec, s.dim)
+    C = chi.chi_exciton_z(m, 3, 2, r["psi"], r["e0"], a, b, Z, nsteps=150)
+    Cx = chi.lehmann_chi_exciton_z(m, 3, 2, a, b, Z)
+    assert np.abs(Cx).max() > 1e-3
+    assert np.abs(C - Cx).max() < 1e-10
+
+
+@pytest.mark.parametrize("pair", [(0, 2), (1, 2)])
+def test_exciton_u0_closed_form(pair):
+    a, b = pair
+    base = make_model(3, 2, U=0.0, Jh=0.0, seed=47)
+    m = _asym(ImpurityModel(norb=3, nbath=2, U=0.0, Ust=0.0, Jh=0.0, e_imp=base.e_imp,
+                            e_bath=base.e_bath, v_bath=base.v_bath), 47)
+    fock._SECTOR_CACHE.clear()
+    s = fock.Sector(m, 4, 5)
+    r = lanczos.ground_state(s.matvec, s.dim)
+    C = chi.chi_exciton_z(m, 4, 5, r["psi"], r["e0"], a, b, Z, nsteps=300)
+    want = _exciton_u0_closed_form(m, 4, 5, a, b, Z)
+    assert np.abs(want).max() > 1e-3
+    assert np.abs(C - want).max() < 1e-9

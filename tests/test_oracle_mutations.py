@@ -372,3 +372,40 @@ def test_wrong_inter_orbital_combination_is_caught(monkeypatch):
     assert err_lehmann() > 1e-3
     monkeypatch.setattr(chi, "AB_COEFFS", (0.5, -0.5, 0.5))
     assert size_u0() > 1e-3
+
+
+def test_dropped_sign_of_exciton_move_is_caught(monkeypatch):
+    """The excitonic operator built without the fermionic sign of moving an
+    electron past occupied levels no longer matches the U = 0 closed form
+    from the one-body eigenvectors for orbitals 0 and 2 (level 1 between)."""
+    from oracle import chi
+    from workloads import ImpurityModel
+    z = 1j * 2 * np.pi * np.arange(1, 20) / 10.0
+    base = make_model(3, 2, U=0.0, Jh=0.0, seed=47)
+    m = ImpurityModel(norb=3, nbath=2, U=0.0, Ust=0.0, Jh=0.0, e_imp=base.e_imp,
+                      e_bath=base.e_bath, v_bath=base.v_bath)
+    fock._SECTOR_CACHE.clear()
+    s = fock.Sector(m, 4, 5)
+    r = lanczos.ground_state(s.matvec, s.dim)
+    want = np.zeros(z.shape, dtype=np.complex128)
+    for spin, n in ((0, 4), (1, 5)):
+        h = np.diag(fock.level_energies(m, spin))
+        for a in range(3):
+            for nu in range(2):
+                i, j = fock.level_of_impurity(m, a), fock.level_of_bath(m, a, nu)
+                h[i, j] = h[j, i] = m.v_bath[spin, a, nu]
+        e, U = np.linalg.eigh(h)
+        o = np.zeros_like(h)
+        o[0, 2] = o[2, 0] = 1.0
+        M = U.T @ o @ U
+        for k in range(n):
+            for l in range(n, len(e)):
+                d = e[l] - e[k]
+                want += M[l, k] ** 2 * (1 / (z - d) - 1 / (z + d))
+
+    def err():
+        return np.abs(chi.chi_exciton_z(m, 4, 5, r["psi"], r["e0"], 0, 2, z, nsteps=300)
+                      - want).max()
+    assert err() < 1e-9
+    monkeypatch.setattr(chi, "move_sign", lambda I, between: 1.0)
+    assert err() > 1e-3
