@@ -345,7 +345,7 @@ ed_status ed_lanczos_ground_orbital(ed_sector s, const int32_t *nup_orb, const i
  * sectors).  d_psi, prec, host_z / host_C (nz complex values each) as for
  * ed_gf_lanczos_z; host_w (nullable) receives n+ and n-.  Synchronises
  * `stream`. */
-enum { ED_CHI_SPIN = 0, ED_CHI_CHARGE = 1, ED_CHI_PAIR = 2 };
+enum { ED_CHI_SPIN = 0, ED_CHI_CHARGE = 1, ED_CHI_PAIR = 2, ED_CHI_EXCITON = 3 };
 ed_status ed_chi_z(ed_sector s, ed_precision prec, const void *d_psi, double e0, int32_t kind,
                    int32_t orb, int32_t nsteps, const double *host_z, int32_t nz, double *host_C,
                    double *host_w, void *stream);
@@ -357,9 +357,14 @@ ed_status ed_chi_z(ed_sector s, ed_precision prec, const void *d_psi, double e0,
  * operator of one orbital, from the chains of O_a + O_b, O_a and O_b:
  * C_ab = [C(O_a + O_b) - C_aa - C_bb] / 2 (for these real operators and a
  * real symmetric H, C_ab = C_ba, so the paper's second auxiliary operator
- * A - iB is not needed); orb_a = orb_b gives ed_chi_z's C_aa.  Arguments,
- * precisions and outputs as ed_chi_z (no weights); ED_ERR_ARG for
- * ED_CHI_PAIR or an orbital out of range.  Synchronises `stream`. */
+ * A - iB is not needed); orb_a = orb_b gives ed_chi_z's C_aa.
+ * kind = ED_CHI_EXCITON: the excitonic function of the orbital pair
+ * (orb_a != orb_b), C_O with O = sum_sigma (c^+_{a sigma} c_{b sigma} +
+ * c^+_{b sigma} c_{a sigma}) (the singlet inter-orbital particle-hole
+ * operator, hermitian, same sector) as its connected O - <O>, from one chain
+ * as for spin and charge.  Arguments, precisions and outputs as ed_chi_z (no
+ * weights); ED_ERR_ARG for ED_CHI_PAIR, an orbital out of range or an
+ * excitonic pair with orb_a = orb_b.  Synchronises `stream`. */
 ed_status ed_chi_ab_z(ed_sector s, ed_precision prec, const void *d_psi, double e0, int32_t kind,
                       int32_t orb_a, int32_t orb_b, int32_t nsteps, const double *host_z,
                       int32_t nz, double *host_C, void *stream);

@@ -563,7 +563,7 @@ def lanczos_ground_orbital(sector: Sector, nup_orb, ndw_orb, precision="fp64", m
     return r.as_dict()
 
 
-CHI_KINDS = {"spin": 0, "charge": 1, "pair": 2}
+CHI_KINDS = {"spin": 0, "charge": 1, "pair": 2, "exciton": 3}
 
 
 def chi_z(sector: Sector, psi, e0, kind, orb, z, precision="fp64", nsteps=200, stream=None):
@@ -581,7 +581,8 @@ def chi_z(sector: Sector, psi, e0, kind, orb, z, precision="fp64", nsteps=200, s
 
 def chi_ab_z(sector: Sector, psi, e0, kind, orb_a, orb_b, z, precision="fp64", nsteps=200,
              stream=None):
-    """Inter-orbital spin or charge function C_ab(z) at T = 0 (ed_chi_ab_z)."""
+    """Inter-orbital spin or charge function C_ab(z) at T = 0, or the
+    excitonic function of the orbital pair (kind "exciton") (ed_chi_ab_z)."""
     zz = np.ascontiguousarray(np.asarray(z, dtype=np.complex128).reshape(-1))
     out = np.zeros(zz.size, dtype=np.complex128)
     _check(lib().ed_chi_ab_z(sector.h, _prec(precision), _psi_ptr(psi, precision), float(e0),

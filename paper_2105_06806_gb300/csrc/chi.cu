@@ -217,6 +217,119 @@ ed_status chi_impl(ed_sector s, ed_precision prec, const Ti *psi, double e0, int
   return ED_OK;
 }
 
+// ----------------------------------------------------------------- excitonic function
+//
+// O = sum_sigma (c^+_a c_b + c^+_b c_a) of an orbital pair: out = O x on the
+// padded block-major layout, each element gathering the two moves between
+// impurity levels a and b of its up string (same row) and of its dw string
+// (same column) from the move tables (entry (index << 1) | sign, or -1);
+// padding columns stay zero.  At most four terms of +-x, summed in FP64.
+template <typename T>
+__global__ void k_exciton_apply(const T *x, T *out, const int32_t *mup, const int32_t *mdw,
+                                const int32_t *padinv, int64_t stride, int64_t ddw, int k1,
+                                int k2) {
+  for (int64_t r = blockIdx.y; r < ddw; r += gridDim.y) {
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < stride;
+         c += (int64_t)gridDim.x * blockDim.x) {
+      double acc = 0.0;
+      if (padinv[c] >= 0) {
+        for (int q = 0; q < 2; ++q) {
+          const int k = q ? k2 : k1;
+          const int32_t eu = mup[(int64_t)k * stride + c];
+          if (eu >= 0) {
+            const double v = (double)x[r * stride + (eu >> 1)];
+            acc += (eu & 1) ? -v : v;
+          }
+          const int32_t ed = mdw[(int64_t)k * ddw + r];
+          if (ed >= 0) {
+            const double v = (double)x[(int64_t)(ed >> 1) * stride + c];
+            acc += (ed & 1) ? -v : v;
+          }
+        }
+      }
+      out[r * stride + c] = (T)acc;
+    }
+  }
+}
+
+// parts[cta] = sum x y, parts[CHI_PARTS + cta] = sum x x (FP64)
+template <typename T>
+__global__ void __launch_bounds__(CHI_THREADS) k_exciton_dots(const T *x, const T *y, int64_t n,
+                                                              double *parts) {
+  __shared__ double red[2][CHI_THREADS / 32];
+  double a = 0.0, b = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double xi = (double)x[i];
+    a += xi * (double)y[i];
+    b += xi * xi;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_down_sync(0xffffffffu, a, o);
+    b += __shfl_down_sync(0xffffffffu, b, o);
+  }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) {
+    red[0][wid] = a;
+    red[1][wid] = b;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double sa = 0.0, sb = 0.0;
+    for (int k = 0; k < CHI_THREADS / 32; ++k) {
+      sa += red[0][k];
+      sb += red[1][k];
+    }
+    parts[blockIdx.x] = sa;
+    parts[CHI_PARTS + blockIdx.x] = sb;
+  }
+}
+
+// phi = y - <O> x (the connected operator applied to psi)
+template <typename Ti, typename To>
+__global__ void k_exciton_phi(const Ti *x, const Ti *y, To *phi, int64_t n, const double *avg) {
+  const double o0 = avg[0];
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    phi[i] = (To)((double)y[i] - o0 * (double)x[i]);
+}
+
+template <typename Ti, typename To>
+ed_status exciton_impl(ed_sector s, const Ti *psi, double e0, int a, int b, int nsteps,
+                       const double2 *dz, int nz, double2 *dC, LanczosState *st, double *w,
+                       cudaStream_t cs) {
+  const int no = s->mp.norb;
+  const int64_t bn = s->bdim, stride = s->bstride, ddw = s->sp[1].dim;
+  Mem xb, ob, tabs, scratch, phi;
+  ED_TRY(xb.alloc((size_t)bn * sizeof(Ti), cs, "excitonic operator"));
+  ED_TRY(ob.alloc((size_t)bn * sizeof(Ti), cs, "excitonic operator"));
+  ED_TRY(tabs.alloc((size_t)no * no * (stride + ddw) * sizeof(int32_t), cs, "move tables"));
+  ED_TRY(scratch.alloc((2 * CHI_PARTS + 8) * sizeof(double), cs, "susceptibility partials"));
+  ED_TRY(phi.alloc((size_t)bn * sizeof(To), cs, "susceptibility start vector"));
+  int32_t *mup = (int32_t *)tabs.p, *mdw = mup + (size_t)no * no * stride;
+  double *parts = (double *)scratch.p, *avg = parts + 2 * CHI_PARTS;
+  ED_TRY(ed_move_tables(s, mup, mdw, cs));
+  ED_TRY(ed_permute_vec(s, sizeof(Ti) == 8 ? ED_FP64 : ED_FP32, true, psi, xb.p, cs));
+  const dim3 grid((unsigned)std::max<int64_t>(1, std::min<int64_t>((stride + 255) / 256, 64)),
+                  (unsigned)std::max<int64_t>(1, std::min<int64_t>(ddw, 65535)));
+  k_exciton_apply<Ti><<<grid, 256, 0, cs>>>((const Ti *)xb.p, (Ti *)ob.p, mup, mdw, s->padinv,
+                                            stride, ddw, b * no + a, a * no + b);
+  ED_LAUNCHED(1);
+  const unsigned g = (unsigned)std::max<int64_t>(
+      1, std::min<int64_t>((bn + 4 * CHI_THREADS - 1) / (4 * CHI_THREADS), CHI_PARTS));
+  k_exciton_dots<Ti><<<g, CHI_THREADS, 0, cs>>>((const Ti *)xb.p, (const Ti *)ob.p, bn, parts);
+  ED_LAUNCHED(1);
+  k_chi_avg<<<1, 32, 0, cs>>>(parts, (int)g, avg);
+  ED_LAUNCHED(1);
+  k_exciton_phi<Ti, To><<<g, CHI_THREADS, 0, cs>>>((const Ti *)xb.p, (const Ti *)ob.p,
+                                                   (To *)phi.p, bn, avg);
+  ED_LAUNCHED(1);
+  double wt = 0.0;
+  ED_TRY(chain_and_cfrac<To>(s, (const To *)phi.p, nsteps, e0, dz, nz, true, 0, dC, st, &wt, cs));
+  w[0] = w[1] = wt;
+  return ED_OK;
+}
+
 // The device buffers of a susceptibility call (the frequencies, the
 // accumulated C, one Lanczos state) around `run`, then C and the weights to
 // the host.
@@ -278,18 +391,32 @@ extern "C" ed_status ed_chi_z(ed_sector s, ed_precision prec, const void *d_psi,
 
 // Inter-orbital spin / charge function: the auxiliary-operator construction
 // of Sec. 6.8, C_ab = [C(O_a + O_b) - C_aa - C_bb] / 2 (real operators, real
-// symmetric H: C_ab = C_ba), three chains accumulated into one C.
+// symmetric H: C_ab = C_ba), three chains accumulated into one C.  The
+// excitonic kind: C_O of O = sum_sigma (c^+_a c_b + c^+_b c_a), one chain.
 extern "C" ed_status ed_chi_ab_z(ed_sector s, ed_precision prec, const void *d_psi, double e0,
                                  int32_t kind, int32_t orb_a, int32_t orb_b, int32_t nsteps,
                                  const double *host_z, int32_t nz, double *host_C, void *stream) {
   if (!s || !d_psi || !host_C || nz < 0 || (nz > 0 && !host_z)) return ED_ERR_ARG;
-  if (kind != ED_CHI_SPIN && kind != ED_CHI_CHARGE) return ED_ERR_ARG;
+  if (kind != ED_CHI_SPIN && kind != ED_CHI_CHARGE && kind != ED_CHI_EXCITON) return ED_ERR_ARG;
   const int norb = s->mp.norb;
   if (orb_a < 0 || orb_a >= norb || orb_b < 0 || orb_b >= norb) return ED_ERR_ARG;
+  if (kind == ED_CHI_EXCITON && orb_a == orb_b) return ED_ERR_ARG;
   if (prec != ED_FP64 && prec != ED_FP32 && prec != ED_FP32_POLISH) return ED_ERR_ARG;
   if (nsteps <= 0) nsteps = 200;
   if (nsteps > ED_MAX_LANCZOS) return ED_ERR_ARG;
   cudaStream_t cs = (cudaStream_t)stream;
+  if (kind == ED_CHI_EXCITON)
+    return chi_call(host_z, nz, host_C, nullptr, cs,
+                    [&](const double2 *dz, double2 *dC, LanczosState *st, double *w) {
+                      if (prec == ED_FP64)
+                        return exciton_impl<double, double>(s, (const double *)d_psi, e0, orb_a,
+                                                            orb_b, nsteps, dz, nz, dC, st, w, cs);
+                      if (prec == ED_FP32)
+                        return exciton_impl<float, float>(s, (const float *)d_psi, e0, orb_a,
+                                                          orb_b, nsteps, dz, nz, dC, st, w, cs);
+                      return exciton_impl<double, float>(s, (const double *)d_psi, e0, orb_a,
+                                                         orb_b, nsteps, dz, nz, dC, st, w, cs);
+                    });
   int wab[ED_MAX_NORB] = {0}, wa[ED_MAX_NORB] = {0}, wb[ED_MAX_NORB] = {0};
   wab[orb_a] += 1;
   wab[orb_b] += 1;  // a = b: 2 O_a, and the combination gives C_aa

@@ -320,6 +320,22 @@ ed_status ed_build_nd_tables(ed_sector s, cudaStream_t st) {
   return ED_OK;
 }
 
+ed_status ed_move_tables(ed_sector s, int32_t *up, int32_t *dw, cudaStream_t st) {
+  const int no = s->mp.norb;
+  const int64_t nu = s->bstride, nd = s->sp[1].dim;
+  if (nu > 0) {
+    k_nd_table<1><<<(unsigned)((nu + 255) / 256), 256, 0, st>>>(
+        s->bk[0].map, s->padinv, s->colpos, nu, no, ed_block_view(s, 0), up);
+    ED_LAUNCHED(1);
+  }
+  if (nd > 0) {
+    k_nd_table<1><<<(unsigned)((nd + 255) / 256), 256, 0, st>>>(
+        s->bk[1].map, nullptr, nullptr, nd, no, ed_block_view(s, 1), dw);
+    ED_LAUNCHED(1);
+  }
+  return ED_OK;
+}
+
 void ed_free_nd_tables(ed_sector s, cudaStream_t st) {
   for (int l = 0; l < 2; ++l) {
     ed_dfree(s->nd[l].up, st);

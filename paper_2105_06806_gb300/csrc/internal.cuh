@@ -363,6 +363,10 @@ __device__ __forceinline__ T ed_nd_terms(const HvTables<T> &tb, const T *v, int6
 
 ed_status ed_build_nd_tables(ed_sector s, cudaStream_t st);
 void ed_free_nd_tables(ed_sector s, cudaStream_t st);
+// The block-major move tables of both spins (the format of NdTables: entry
+// k = b * norb + a moves an electron from impurity level b to a) into caller
+// device memory: up norb^2 * bstride, dw norb^2 * D_dw int32.
+ed_status ed_move_tables(ed_sector s, int32_t *up, int32_t *dw, cudaStream_t st);
 // CTAs (= partial sums of the Lanczos and dot modes) of the H_nd kernel
 int64_t ed_nd_grid(int64_t ddw, int64_t ncols);
 // Adds the H_nd terms after the factorised product (modes of k_hv; ND_DOT:

@@ -5,7 +5,9 @@ Matsubara axis and the real axis at eta = 0.5; FP32 chains on the polished
 state <= 1e-5 (relative); the empty-atom pair function 1/(z - (2e + U));
 inter-orbital spin and charge functions (ed_chi_ab_z) against the oracle's
 auxiliary-operator construction, C_aa = ed_chi_z, C_ab = C_ba, and C_ab = 0
-at U = 0 with each orbital on its own bath."""
+at U = 0 with each orbital on its own bath; the excitonic function against
+the oracle (FP64 1e-8, FP32 + polish 1e-5) and, at U = 0, against the closed
+form from the one-body eigenvectors."""
 import numpy as np
 import pytest
 import torch
@@ -112,4 +114,62 @@ def test_inter_orbital_chi_vanishes_at_u0(ed, kind):
     C0, _ = ed.chi_z(s, psi, r["e0"], kind, 0, Z, "fp64", nsteps=200)
     assert np.abs(C0).max() > 1e-2
     assert np.abs(C01).max() < 1e-8
+    s.free()
+
+
+@pytest.mark.parametrize("case", ["norb3_ns9", "kanamori_ns9"])
+@pytest.mark.parametrize("pair", [(0, 2), (1, 2)])
+def test_exciton_chi_against_oracle(ed, case, pair):
+    a, b = pair
+    if case == "norb3_ns9":
+        m, nup, ndw = _asym(make_model(3, 2, U=2.3, Jh=0.35, seed=55), 55), 5, 4
+    else:
+        m, nup, ndw = CASES[case]
+    fock._SECTOR_CACHE.clear()
+    ref = fock.Sector(m, nup, ndw)
+    ro = lanczos.ground_state(ref.matvec, ref.dim)
+    Co = chi.chi_exciton_z(m, nup, ndw, ro["psi"], ro["e0"], a, b, Z, nsteps=150)
+    s = ed.Sector(m, nup, ndw)
+    psi = torch.empty(s.dim, dtype=torch.float64, device="cuda")
+    r = ed.lanczos_ground(s, "fp64", psi=psi)
+    C = ed.chi_ab_z(s, psi, r["e0"], "exciton", a, b, Z, "fp64", nsteps=150)
+    scale = max(1.0, np.abs(Co).max())
+    assert np.abs(Co).max() > 1e-3
+    assert np.abs(C - Co).max() <= 1e-8 * scale
+    Cba = ed.chi_ab_z(s, psi, r["e0"], "exciton", b, a, Z, "fp64", nsteps=150)
+    assert np.abs(Cba - C).max() <= 1e-10 * scale       # the same operator
+    psi2 = torch.empty(s.dim, dtype=torch.float64, device="cuda")
+    r2 = ed.lanczos_ground(s, "fp32_polish", psi=psi2)
+    C2 = ed.chi_ab_z(s, psi2, r2["e0"], "exciton", a, b, Z, "fp32_polish", nsteps=150)
+    assert np.abs(C2 - Co).max() <= 1e-5 * scale
+    with pytest.raises(ed.EDError):
+        ed.chi_ab_z(s, psi, r["e0"], "exciton", a, a, Z, "fp64")
+    s.free()
+
+
+def test_exciton_chi_u0_closed_form(ed):
+    base = make_model(3, 2, U=0.0, Jh=0.0, seed=47)
+    m = _asym(ImpurityModel(norb=3, nbath=2, U=0.0, Ust=0.0, Jh=0.0, e_imp=base.e_imp,
+                            e_bath=base.e_bath, v_bath=base.v_bath), 47)
+    nup, ndw, a, b = 4, 5, 0, 2
+    want = np.zeros(Z.shape, dtype=np.complex128)
+    for spin, n in ((0, nup), (1, ndw)):
+        h = np.diag(fock.level_energies(m, spin))
+        for o in range(3):
+            for nu in range(2):
+                i, j = fock.level_of_impurity(m, o), fock.level_of_bath(m, o, nu)
+                h[i, j] = h[j, i] = m.v_bath[spin, o, nu]
+        e, U = np.linalg.eigh(h)
+        op = np.zeros_like(h)
+        op[a, b] = op[b, a] = 1.0
+        M = U.T @ op @ U
+        for k in range(n):
+            for l in range(n, len(e)):
+                d = e[l] - e[k]
+                want += M[l, k] ** 2 * (1 / (Z - d) - 1 / (Z + d))
+    s = ed.Sector(m, nup, ndw)
+    psi = torch.empty(s.dim, dtype=torch.float64, device="cuda")
+    r = ed.lanczos_ground(s, "fp64", psi=psi)
+    C = ed.chi_ab_z(s, psi, r["e0"], "exciton", a, b, Z, "fp64", nsteps=300)
+    assert np.abs(C - want).max() <= 1e-8 * max(1.0, np.abs(want).max())
     s.free()
