@@ -16,6 +16,16 @@ Reading: the spin and charge functions use the connected operator
 O - <O> (for a hermitian O both terms then start from (O - <O>)|gs>, and the
 E_m = E0 component, which would make C(0) singular, is removed).
 
+Imaginary time (Sec. 6.8: the susceptibilities are also evaluated in
+imaginary time).  Reading: on [0, beta] at T = 0,
+C(tau) = n+ sum_m |a+_m|^2 exp(-tau (E+_m - E0))
+       + n- sum_m |a-_m|^2 exp(-(beta - tau)(E-_m - E0)),
+the first term from the O^+|gs> chain, the second from the O|gs> chain, with
+E_m and |a_m|^2 the eigenvalues of the chain's tridiagonal matrix and the
+squared first components of its eigenvectors; its bosonic Fourier transform
+int_0^beta exp(i nu_n tau) C(tau) dtau is -C(i nu_n) up to exp(-beta (E_m -
+E0)) terms, and for a hermitian operator C(tau) = C(beta - tau).
+
 Excitonic function (Sec. 6.8 names it among the susceptibilities).  Reading:
 the singlet inter-orbital particle-hole operator of an orbital pair a != b,
 O = sum_sigma (c^+_{a sigma} c_{b sigma} + c^+_{b sigma} c_{a sigma}),
@@ -228,3 +238,50 @@ def lehmann_chi_exciton_z(model, nup, ndw, a, b, z):
     w = (U.T @ phi) ** 2
     d = E - E[0]
     return (w[None, :] * (1.0 / (z[:, None] - d[None, :]) - 1.0 / (z[:, None] + d[None, :]))).sum(1)
+
+
+def tau_argument(tau, beta, create):
+    """The time a term of C(tau) decays over: tau for the O^+|gs> chain,
+    beta - tau for the O|gs> chain (see the module text)."""
+    return tau if create > 0 else beta - tau
+
+
+def chi_tau(model, nup, ndw, psi, e0, kind, orb, tau, beta, nsteps=200):
+    """C(tau) for tau in [0, beta] (see the module text) from the chains of
+    chi_z: each chain's poles and weights from the eigenvalues and first
+    eigenvector components of its tridiagonal matrix (scipy's tridiagonal
+    eigensolver)."""
+    from scipy.linalg import eigh_tridiagonal
+    tau = np.asarray(tau, dtype=np.float64)
+    C = np.zeros(tau.shape)
+    for phi, (n2u, n2d), create in start_vectors(model, nup, ndw, psi, kind, orb):
+        nrm2 = float(phi @ phi)
+        if nrm2 == 0.0:
+            continue
+        sec = fock.get_sector(model, n2u, n2d)
+        a, b = lanczos_chain(sec.matvec, phi, nsteps)
+        lam, Z = eigh_tridiagonal(a, b[1:len(a)])
+        w = Z[0, :] ** 2
+        d = lam - e0
+        t = tau_argument(tau, beta, create)
+        C += nrm2 * (w[None, :] * np.exp(-t[:, None] * d[None, :])).sum(1)
+    return C
+
+
+def lehmann_chi_tau(model, nup, ndw, kind, orb, tau, beta):
+    """The exact C(tau) from dense eigenvectors: sum_m |<m|O^+|0>|^2
+    exp(-tau (E_m - E0)) + |<m|O|0>|^2 exp(-(beta - tau)(E_m - E0))."""
+    tau = np.asarray(tau, dtype=np.float64)
+    s0 = fock.get_sector(model, nup, ndw)
+    E, U = np.linalg.eigh(s0.hamiltonian().toarray())
+    e0, gs = E[0], U[:, 0]
+    C = np.zeros(tau.shape)
+    for phi, (n2u, n2d), create in start_vectors(model, nup, ndw, gs, kind, orb):
+        if not np.any(phi):
+            continue
+        s1 = fock.get_sector(model, n2u, n2d)
+        E1, U1 = np.linalg.eigh(s1.hamiltonian().toarray())
+        w = (U1.T @ phi) ** 2
+        t = tau_argument(tau, beta, create)
+        C += (w[None, :] * np.exp(-t[:, None] * (E1 - e0)[None, :])).sum(1)
+    return C

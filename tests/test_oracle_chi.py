@@ -20,7 +20,11 @@
   exact Lehmann sum, and at U = 0 = the closed form from the one-body
   eigenvectors (Wick: sum over particle-hole pairs of |<l|o|k>|^2, o the
   one-body matrix of the operator), for a pair with a level between them
-  (the fermionic sign matters) and an adjacent pair.
+  (the fermionic sign matters) and an adjacent pair;
+* imaginary time: C(tau) from the chains' poles and weights = the exact
+  Lehmann sum in tau; its bosonic Fourier transform = -C(i nu_n) of chi_z (an
+  independent route: the continued fraction); C(tau) = C(beta - tau) for the
+  hermitian spin and charge operators.
 """
 import numpy as np
 import pytest
@@ -190,3 +194,24 @@ def test_exciton_u0_closed_form(pair):
     want = _exciton_u0_closed_form(m, 4, 5, a, b, Z)
     assert np.abs(want).max() > 1e-3
     assert np.abs(C - want).max() < 1e-9
+
+
+TAU_BETA = 40.0
+TAU = np.linspace(0.0, TAU_BETA, 8001)
+
+
+@pytest.mark.parametrize("kind", chi.KINDS)
+def test_chi_tau_lehmann_and_fourier(kind):
+    m = _asym(make_model(2, 2, U=2.4, Jh=0.4, seed=44), 44)
+    fock._SECTOR_CACHE.clear()
+    s = fock.Sector(m, 3, 2)
+    r = lanczos.ground_state(s.matvec, s.dim)
+    C = chi.chi_tau(m, 3, 2, r["psi"], r["e0"], kind, 1, TAU, TAU_BETA, nsteps=120)
+    Cx = chi.lehmann_chi_tau(m, 3, 2, kind, 1, TAU, TAU_BETA)
+    assert np.abs(C - Cx).max() < 1e-10 * max(1.0, np.abs(Cx).max())
+    nu = 2 * np.pi * np.arange(1, 8) / TAU_BETA
+    ft = np.array([np.trapezoid(np.exp(1j * v * TAU) * C, TAU) for v in nu])
+    Cz = chi.chi_z(m, 3, 2, r["psi"], r["e0"], kind, 1, 1j * nu, nsteps=120)
+    assert np.abs(ft + Cz).max() < 2e-5
+    if kind in ("spin", "charge"):
+        assert np.abs(C - C[::-1]).max() < 1e-12

@@ -409,3 +409,27 @@ def test_dropped_sign_of_exciton_move_is_caught(monkeypatch):
     assert err() < 1e-9
     monkeypatch.setattr(chi, "move_sign", lambda I, between: 1.0)
     assert err() > 1e-3
+
+
+def test_swapped_imaginary_time_terms_are_caught(monkeypatch):
+    """C(tau) with the O^+|gs> and O|gs> chains decaying over the wrong
+    times: its Fourier transform no longer equals -C(i nu_n) of the continued
+    fraction (pair function, whose two terms differ)."""
+    from oracle import chi
+    beta = 40.0
+    tau = np.linspace(0.0, beta, 8001)
+    m = make_model(2, 2, U=2.4, Jh=0.4, seed=44)
+    fock._SECTOR_CACHE.clear()
+    s = fock.Sector(m, 3, 2)
+    r = lanczos.ground_state(s.matvec, s.dim)
+    nu = 2 * np.pi * np.arange(1, 8) / beta
+    Cz = chi.chi_z(m, 3, 2, r["psi"], r["e0"], "pair", 1, 1j * nu, nsteps=120)
+
+    def err():
+        C = chi.chi_tau(m, 3, 2, r["psi"], r["e0"], "pair", 1, tau, beta, nsteps=120)
+        ft = np.array([np.trapezoid(np.exp(1j * v * tau) * C, tau) for v in nu])
+        return np.abs(ft + Cz).max()
+    assert err() < 2e-5
+    monkeypatch.setattr(chi, "tau_argument",
+                        lambda t, b, create: b - t if create > 0 else t)
+    assert err() > 1e-3
