@@ -350,6 +350,23 @@ ed_status ed_chi_z(ed_sector s, ed_precision prec, const void *d_psi, double e0,
                    int32_t orb, int32_t nsteps, const double *host_z, int32_t nz, double *host_C,
                    double *host_w, void *stream);
 
+/* Susceptibility in imaginary time at T = 0 (Sec. 6.8 evaluates the
+ * susceptibilities on the imaginary-time axis as well): for tau in [0, beta],
+ *   C(tau) = n+ sum_m w+_m exp(-tau (E+_m - e0))
+ *          + n- sum_m w-_m exp(-(beta - tau)(E-_m - e0)),
+ * from the two chains of ed_chi_z (the O^+ psi chain decays over tau, the
+ * O psi chain over beta - tau), E_m and w_m the eigenvalues of each chain's
+ * tridiagonal matrix and the squared first components of its eigenvectors
+ * (computed on the host by Jacobi rotations, at most ED_MAX_LANCZOS
+ * steps).  Its bosonic Fourier transform is -C(i nu_n) of ed_chi_z up to
+ * exp(-beta (E_m - e0)) terms; for spin and charge C(tau) = C(beta - tau).
+ * kind, orb, prec, nsteps as ed_chi_z; host_tau: ntau times in [0, beta]
+ * (ED_ERR_ARG otherwise, or for beta <= 0); host_C receives ntau doubles.
+ * Synchronises `stream`. */
+ed_status ed_chi_tau(ed_sector s, ed_precision prec, const void *d_psi, double e0, int32_t kind,
+                     int32_t orb, int32_t nsteps, double beta, const double *host_tau,
+                     int32_t ntau, double *host_C, void *stream);
+
 /* Inter-orbital spin or charge function (Sec. 6.8, the auxiliary-operator
  * construction of non-diagonal correlation functions):
  *   C_ab(z) = <A (z - (H - E0))^-1 B> - <B (z + (H - E0))^-1 A>,

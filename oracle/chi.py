@@ -16,8 +16,8 @@ Reading: the spin and charge functions use the connected operator
 O - <O> (for a hermitian O both terms then start from (O - <O>)|gs>, and the
 E_m = E0 component, which would make C(0) singular, is removed).
 
-Imaginary time (Sec. 6.8: the susceptibilities are also evaluated in
-imaginary time).  Reading: on [0, beta] at T = 0,
+Imaginary time (Sec. 6.8 evaluates the susceptibilities on the
+imaginary-time axis as well).  Reading: on [0, beta] at T = 0,
 C(tau) = n+ sum_m |a+_m|^2 exp(-tau (E+_m - E0))
        + n- sum_m |a-_m|^2 exp(-(beta - tau)(E-_m - E0)),
 the first term from the O^+|gs> chain, the second from the O|gs> chain, with

@@ -31,7 +31,7 @@ EXPORTED = [
     "ed_sector_permute", "ed_lanczos_ground", "ed_gf_lanczos", "ed_gf_lanczos_z", "ed_sigma",
     "ed_observables", "ed_solve", "ed_eph_matvec", "ed_eph_lanczos_ground",
     "ed_eph_gf_lanczos_z", "ed_lanczos_states", "ed_espace_truncate", "ed_gf_thermal_z",
-    "ed_chi_z", "ed_chi_ab_z", "ed_orbital_sector_dims", "ed_lanczos_ground_orbital",
+    "ed_chi_z", "ed_chi_ab_z", "ed_chi_tau", "ed_orbital_sector_dims", "ed_lanczos_ground_orbital",
     "ed_server_create", "ed_submit", "ed_poll", "ed_wait", "ed_server_destroy",
     "ed_server_inject_alloc_failure", "ed_batch_stats", "ed_residual_noalloc", "ed_status_string",
     "ed_last_error",
@@ -194,6 +194,8 @@ def lib():
                                 i32, vp, i32, vp, vp, vp],
             "ed_chi_z": [vp, C.c_int, vp, C.c_double, i32, i32, i32, vp, i32, vp, vp, vp],
             "ed_chi_ab_z": [vp, C.c_int, vp, C.c_double, i32, i32, i32, i32, vp, i32, vp, vp],
+            "ed_chi_tau": [vp, C.c_int, vp, C.c_double, i32, i32, i32, C.c_double, vp, i32, vp,
+                           vp],
             "ed_orbital_sector_dims": [vp, vp, vp, C.POINTER(i64), C.POINTER(i64)],
             "ed_lanczos_ground_orbital": [vp, vp, vp, C.POINTER(ed_lanczos_opts),
                                           C.POINTER(ed_lanczos_result), vp, vp],
@@ -577,6 +579,19 @@ def chi_z(sector: Sector, psi, e0, kind, orb, z, precision="fp64", nsteps=200, s
                           int(zz.size), C.c_void_p(out.ctypes.data), C.c_void_p(w.ctypes.data),
                           C.c_void_p(_stream_ptr(stream))), "ed_chi_z")
     return out, (float(w[0]), float(w[1]))
+
+
+def chi_tau(sector: Sector, psi, e0, kind, orb, tau, beta, precision="fp64", nsteps=200,
+            stream=None):
+    """Susceptibility C(tau) at T = 0 for tau in [0, beta] (ed_chi_tau)."""
+    tt = np.ascontiguousarray(np.asarray(tau, dtype=np.float64).reshape(-1))
+    out = np.zeros(tt.size, dtype=np.float64)
+    _check(lib().ed_chi_tau(sector.h, _prec(precision), _psi_ptr(psi, precision), float(e0),
+                            CHI_KINDS[kind], int(orb), int(nsteps), float(beta),
+                            C.c_void_p(tt.ctypes.data), int(tt.size),
+                            C.c_void_p(out.ctypes.data), C.c_void_p(_stream_ptr(stream))),
+           "ed_chi_tau")
+    return out
 
 
 def chi_ab_z(sector: Sector, psi, e0, kind, orb_a, orb_b, z, precision="fp64", nsteps=200,

@@ -124,11 +124,95 @@ struct Mem {
   }
 };
 
+// Imaginary-time output of a susceptibility call: C(tau) at ntau host times
+// in [0, beta], accumulated on the host.
+struct TauOut {
+  const double *tau;
+  int ntau;
+  double beta;
+  double *C;
+};
+
+// Eigenvalues lam and squared first eigenvector components w of the
+// symmetric tridiagonal T_k (a[0..k-1], b[1..k-1]) by cyclic Jacobi rotations
+// on its dense form: each rotation J (cos c, sin s in the plane p, q) zeroes
+// the element (p, q) of J^T T J; only the first row of the accumulated
+// rotations is kept, since the weights are its squares.  Sweeps until the
+// off-diagonal part is below 1e-28 of the diagonal's squared norm.
+void tridiag_poles(const double *a, const double *b, int k, std::vector<double> &lam,
+                   std::vector<double> &w) {
+  std::vector<double> A((size_t)k * k, 0.0), v(k, 0.0);
+  for (int i = 0; i < k; ++i) {
+    A[(size_t)i * k + i] = a[i];
+    if (i > 0) A[(size_t)i * k + i - 1] = A[(size_t)(i - 1) * k + i] = b[i];
+  }
+  v[0] = 1.0;
+  for (int sweep = 0; sweep < 100; ++sweep) {
+    double off = 0.0, dia = 0.0;
+    for (int p = 0; p < k; ++p) {
+      dia += A[(size_t)p * k + p] * A[(size_t)p * k + p];
+      for (int q = p + 1; q < k; ++q) off += A[(size_t)p * k + q] * A[(size_t)p * k + q];
+    }
+    if (off <= 1e-28 * dia || off == 0.0) break;
+    for (int p = 0; p + 1 < k; ++p)
+      for (int q = p + 1; q < k; ++q) {
+        const double apq = A[(size_t)p * k + q];
+        if (apq == 0.0) continue;
+        const double app = A[(size_t)p * k + p], aqq = A[(size_t)q * k + q];
+        const double theta = (aqq - app) / (2.0 * apq);
+        const double t = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+        const double c = 1.0 / sqrt(t * t + 1.0), sn = t * c;
+        for (int r = 0; r < k; ++r) {
+          if (r == p || r == q) continue;
+          const double arp = A[(size_t)r * k + p], arq = A[(size_t)r * k + q];
+          A[(size_t)r * k + p] = A[(size_t)p * k + r] = c * arp - sn * arq;
+          A[(size_t)r * k + q] = A[(size_t)q * k + r] = sn * arp + c * arq;
+        }
+        A[(size_t)p * k + p] = app - t * apq;
+        A[(size_t)q * k + q] = aqq + t * apq;
+        A[(size_t)p * k + q] = A[(size_t)q * k + p] = 0.0;
+        const double vp = v[p], vq = v[q];
+        v[p] = c * vp - sn * vq;
+        v[q] = sn * vp + c * vq;
+      }
+  }
+  lam.resize(k);
+  w.resize(k);
+  for (int i = 0; i < k; ++i) {
+    lam[i] = A[(size_t)i * k + i];
+    w[i] = v[i] * v[i];
+  }
+}
+
+// C(tau) += sgn-terms of the chain held in st (k steps): weight * sum_m w_m
+// exp(-t (lam_m - e0)), t = tau for the O^+ chain (sgn +1), beta - tau for
+// the O chain (sgn -1)
+ed_status tau_accumulate(const LanczosState *st, int k, double weight, double e0, bool both,
+                         int which, const TauOut &to, cudaStream_t cs) {
+  std::vector<double> a(k), b(k);
+  ED_TRY_CUDA(cudaMemcpyAsync(a.data(), st->alpha, k * sizeof(double), cudaMemcpyDeviceToHost, cs));
+  ED_TRY_CUDA(cudaMemcpyAsync(b.data(), st->beta, k * sizeof(double), cudaMemcpyDeviceToHost, cs));
+  ED_TRY_CUDA(cudaStreamSynchronize(cs));
+  std::vector<double> lam, w;
+  tridiag_poles(a.data(), b.data(), k, lam, w);
+  for (int sg = +1; sg >= -1; sg -= 2) {
+    if (!both && which != sg) continue;
+    for (int i = 0; i < to.ntau; ++i) {
+      const double t = sg > 0 ? to.tau[i] : to.beta - to.tau[i];
+      double acc = 0.0;
+      for (int m = 0; m < k; ++m) acc += w[m] * exp(-t * (lam[m] - e0));
+      to.C[i] += weight * acc;
+    }
+  }
+  return ED_OK;
+}
+
 // chain on sector nb from phi (block-major), then C += sgn-term (see ed_chi_z)
 template <typename T>
 ed_status chain_and_cfrac(ed_sector nb, const T *phi, int nsteps, double e0, const double2 *dz,
                           int nz, bool both, int which, double2 *dC, LanczosState *st,
-                          double *weight, cudaStream_t cs, double coef = 1.0) {
+                          double *weight, cudaStream_t cs, double coef = 1.0,
+                          const TauOut *tout = nullptr) {
   ED_TRY(ed_build_items(nb, 1, (int)sizeof(T)));
   // FP32 chains run on H - e0, with the one-body diagonal tables shifted in
   // FP64 before their rounding (as the Green's-function chains)
@@ -150,6 +234,7 @@ ed_status chain_and_cfrac(ed_sector nb, const T *phi, int nsteps, double e0, con
   *weight = run.weight;
   if (run.weight <= 0.0 || run.k <= 0) return ED_OK;
   e0 -= sigma;
+  if (tout) return tau_accumulate(st, run.k, coef * run.weight, e0, both, which, *tout, cs);
   // n+ [(e0 + z - T)^-1]_00 (sgn +1) and + n- [(e0 - z - T)^-1]_00: the
   // launcher adds sgn * weight * [(e0 + sgn z - T)^-1]_00, so the second
   // term takes sgn = -1 with weight -n-
@@ -163,7 +248,8 @@ ed_status chain_and_cfrac(ed_sector nb, const T *phi, int nsteps, double e0, con
 template <typename Ti, typename To>
 ed_status chi_impl(ed_sector s, ed_precision prec, const Ti *psi, double e0, int kind, int orb,
                    int nsteps, const double2 *dz, int nz, double2 *dC, LanczosState *st,
-                   double *w, cudaStream_t cs, const int *wts = nullptr, double coef = 1.0) {
+                   double *w, cudaStream_t cs, const int *wts = nullptr, double coef = 1.0,
+                   const TauOut *tout = nullptr) {
   if (kind == ED_CHI_SPIN || kind == ED_CHI_CHARGE) {
     int one[ED_MAX_NORB] = {0};
     one[orb] = 1;
@@ -188,7 +274,7 @@ ed_status chi_impl(ed_sector s, ed_precision prec, const Ti *psi, double e0, int
     ED_LAUNCHED(1);
     double wt = 0.0;
     ED_TRY(chain_and_cfrac<To>(s, (const To *)phi.p, nsteps, e0, dz, nz, true, 0, dC, st, &wt, cs,
-                               coef));
+                               coef, tout));
     w[0] = w[1] = wt;
     return ED_OK;
   }
@@ -210,7 +296,7 @@ ed_status chi_impl(ed_sector s, ed_precision prec, const Ti *psi, double e0, int
     ED_TRY((ed_apply_op_launch<To, To>(s1, s2, (const To *)b.p, (To *)c.p, orb, second, term, cs)));
     double wt = 0.0;
     ED_TRY(chain_and_cfrac<To>(s2, (const To *)c.p, nsteps, e0, dz, nz, false, term, dC, st, &wt,
-                               cs));
+                               cs, 1.0, tout));
     w[term > 0 ? 0 : 1] = wt;
   }
   (void)prec;
@@ -360,15 +446,16 @@ ed_status chi_call(const double *host_z, int32_t nz, double *host_C, double *hos
 // chi_impl in the precisions of `prec`
 ed_status chi_prec(ed_sector s, ed_precision prec, const void *d_psi, double e0, int kind, int orb,
                    int nsteps, const double2 *dz, int nz, double2 *dC, LanczosState *st,
-                   double *w, cudaStream_t cs, const int *wts = nullptr, double coef = 1.0) {
+                   double *w, cudaStream_t cs, const int *wts = nullptr, double coef = 1.0,
+                   const TauOut *tout = nullptr) {
   if (prec == ED_FP64)
     return chi_impl<double, double>(s, prec, (const double *)d_psi, e0, kind, orb, nsteps, dz, nz,
-                                    dC, st, w, cs, wts, coef);
+                                    dC, st, w, cs, wts, coef, tout);
   if (prec == ED_FP32)
     return chi_impl<float, float>(s, prec, (const float *)d_psi, e0, kind, orb, nsteps, dz, nz, dC,
-                                  st, w, cs, wts, coef);
+                                  st, w, cs, wts, coef, tout);
   return chi_impl<double, float>(s, prec, (const double *)d_psi, e0, kind, orb, nsteps, dz, nz, dC,
-                                 st, w, cs, wts, coef);
+                                 st, w, cs, wts, coef, tout);
 }
 
 }  // namespace
@@ -386,6 +473,30 @@ extern "C" ed_status ed_chi_z(ed_sector s, ed_precision prec, const void *d_psi,
   return chi_call(host_z, nz, host_C, host_w, cs,
                   [&](const double2 *dz, double2 *dC, LanczosState *st, double *w) {
                     return chi_prec(s, prec, d_psi, e0, kind, orb, nsteps, dz, nz, dC, st, w, cs);
+                  });
+}
+
+// Imaginary time: C(tau) from each chain's poles and weights (tau_accumulate)
+extern "C" ed_status ed_chi_tau(ed_sector s, ed_precision prec, const void *d_psi, double e0,
+                                int32_t kind, int32_t orb, int32_t nsteps, double beta,
+                                const double *host_tau, int32_t ntau, double *host_C,
+                                void *stream) {
+  if (!s || !d_psi || ntau < 0 || (ntau > 0 && (!host_tau || !host_C))) return ED_ERR_ARG;
+  if (kind != ED_CHI_SPIN && kind != ED_CHI_CHARGE && kind != ED_CHI_PAIR) return ED_ERR_ARG;
+  if (orb < 0 || orb >= s->mp.norb || !(beta > 0.0)) return ED_ERR_ARG;
+  for (int i = 0; i < ntau; ++i)
+    if (!(host_tau[i] >= 0.0 && host_tau[i] <= beta)) return ED_ERR_ARG;
+  if (prec != ED_FP64 && prec != ED_FP32 && prec != ED_FP32_POLISH) return ED_ERR_ARG;
+  if (nsteps <= 0) nsteps = 200;
+  if (nsteps > ED_MAX_LANCZOS) return ED_ERR_ARG;
+  cudaStream_t cs = (cudaStream_t)stream;
+  for (int i = 0; i < ntau; ++i) host_C[i] = 0.0;
+  const TauOut to{host_tau, ntau, beta, host_C};
+  double unused[2];
+  return chi_call(nullptr, 0, unused, nullptr, cs,
+                  [&](const double2 *dz, double2 *dC, LanczosState *st, double *w) {
+                    return chi_prec(s, prec, d_psi, e0, kind, orb, nsteps, dz, 0, dC, st, w, cs,
+                                    nullptr, 1.0, &to);
                   });
 }
 

@@ -7,7 +7,9 @@ inter-orbital spin and charge functions (ed_chi_ab_z) against the oracle's
 auxiliary-operator construction, C_aa = ed_chi_z, C_ab = C_ba, and C_ab = 0
 at U = 0 with each orbital on its own bath; the excitonic function against
 the oracle (FP64 1e-8, FP32 + polish 1e-5) and, at U = 0, against the closed
-form from the one-body eigenvectors."""
+form from the one-body eigenvectors; C(tau) in imaginary time (ed_chi_tau)
+against the oracle's poles-and-weights evaluation (FP64 1e-8, FP32 + polish
+1e-5, relative) and C(tau) = C(beta - tau) for spin and charge."""
 import numpy as np
 import pytest
 import torch
@@ -172,4 +174,31 @@ def test_exciton_chi_u0_closed_form(ed):
     r = ed.lanczos_ground(s, "fp64", psi=psi)
     C = ed.chi_ab_z(s, psi, r["e0"], "exciton", a, b, Z, "fp64", nsteps=300)
     assert np.abs(C - want).max() <= 1e-8 * max(1.0, np.abs(want).max())
+    s.free()
+
+
+@pytest.mark.parametrize("case", ["norb2_ns8", "kanamori_ns9"])
+@pytest.mark.parametrize("kind", chi.KINDS)
+def test_chi_tau_against_oracle(ed, case, kind):
+    m, nup, ndw = CASES[case]
+    beta = 30.0
+    tau = np.linspace(0.0, beta, 301)
+    fock._SECTOR_CACHE.clear()
+    ref = fock.Sector(m, nup, ndw)
+    ro = lanczos.ground_state(ref.matvec, ref.dim)
+    Co = chi.chi_tau(m, nup, ndw, ro["psi"], ro["e0"], kind, 0, tau, beta, nsteps=120)
+    s = ed.Sector(m, nup, ndw)
+    psi = torch.empty(s.dim, dtype=torch.float64, device="cuda")
+    r = ed.lanczos_ground(s, "fp64", psi=psi)
+    C = ed.chi_tau(s, psi, r["e0"], kind, 0, tau, beta, "fp64", nsteps=120)
+    scale = max(1.0, np.abs(Co).max())
+    assert np.abs(C - Co).max() <= 1e-8 * scale
+    if kind != "pair":
+        assert np.abs(C - C[::-1]).max() <= 1e-10 * scale
+    psi2 = torch.empty(s.dim, dtype=torch.float64, device="cuda")
+    r2 = ed.lanczos_ground(s, "fp32_polish", psi=psi2)
+    C2 = ed.chi_tau(s, psi2, r2["e0"], kind, 0, tau, beta, "fp32_polish", nsteps=120)
+    assert np.abs(C2 - Co).max() <= 1e-5 * scale
+    with pytest.raises(ed.EDError):
+        ed.chi_tau(s, psi, r["e0"], kind, 0, np.array([beta + 1.0]), beta, "fp64")
     s.free()
