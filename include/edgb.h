@@ -221,8 +221,9 @@ typedef struct {
   int32_t polish_steps;  /* FP64 Lanczos steps of ED_FP32_POLISH (0: 4)          */
   int32_t want_vector;   /* 1: psi and its FP64 residual                         */
   int32_t basis_mib;     /* Krylov basis kept on the device during the first
-                            pass, so that psi needs no second pass: 0 = up to
-                            40% of the free device memory, > 0 = at most this
+                            pass, so that psi needs no second pass (or one
+                            resumed after the stored vectors): 0 = up to 60%
+                            of the available device memory, > 0 = at most this
                             many MiB, -1 = none (always the second pass)      */
   int32_t reserved;      /* 0                                                    */
 } ed_lanczos_opts;

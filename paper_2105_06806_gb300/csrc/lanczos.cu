@@ -1060,7 +1060,7 @@ static ed_status lanczos_solve(ed_sector s, int maxit, double tol, uint64_t seed
       bs.budget = (size_t)basis_mib << 20;
     } else {
       size_t avail = 0;
-      bs.budget = ed_device_available(&avail) == ED_OK ? (size_t)(0.4 * (double)avail) : 0;
+      bs.budget = ed_device_available(&avail) == ED_OK ? (size_t)(0.6 * (double)avail) : 0;
     }
   }
 
